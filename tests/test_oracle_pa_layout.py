@@ -1,0 +1,55 @@
+"""Pins for the power-amplifier model and for Eq. 1 / Fig. 2."""
+import json
+import os
+
+import numpy as np
+
+from oracle import pa, paper_layout as PL
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_saleh_small_signal_and_peak_p12():
+    aa, ba, ap, bp = 2.1587, 1.1517, 4.0033, 9.1040
+    r = np.array([1e-6, 1e-4])
+    np.testing.assert_allclose(pa.saleh_am(r, aa, ba) / r, aa, rtol=1e-7)   # A(r) ~ alpha r
+    np.testing.assert_allclose(pa.saleh_pm(r, ap, bp) / r ** 2, ap, rtol=1e-7)
+    grid = np.linspace(0.01, 3, 300001)
+    rpk = grid[np.argmax(pa.saleh_am(grid, aa, ba))]
+    assert abs(rpk - 1 / np.sqrt(ba)) < 1e-4                                # peak at 1/sqrt(beta)
+    assert abs(pa.saleh_am(1 / np.sqrt(ba), aa, ba) - aa / (2 * np.sqrt(ba))) < 1e-12
+    x = np.array([1e-5 + 0j, 0, 0, 0])
+    y = pa.pa(x)
+    np.testing.assert_allclose(y[:3] / 1e-5, aa * np.array([1.0, 0.1, -0.05]), rtol=1e-6)
+    assert abs(pa.small_signal_gain() - aa * 1.05) < 1e-12
+
+
+def test_eq1_reproduces_table1_p13():
+    g = json.load(open(os.path.join(GOLD, "table1_buffer_memory.json")))
+    S, r = g["motion_token_bytes"], g["motion_gpu_rate"]
+    n_delay = g["motion_channels_with_delay"]
+    n_plain = len(g["motion_channels"]) - n_delay
+    total = n_plain * PL.eq1_capacity_bytes(S, r, False) + n_delay * PL.eq1_capacity_bytes(S, r, True)
+    assert total == 3456000
+    assert round(total / 1e6, 2) == g["prop_heterog_MB"]
+
+
+def test_fig2_access_pattern():
+    g = json.load(open(os.path.join(GOLD, "fig2_access_pattern.json")))
+    r = g["rate"]
+    assert PL.eq1_capacity_tokens(r, True) == g["slots"]
+    assert [PL.write_slots(k, r) for k in range(4)] == g["writes"]
+    assert [PL.read_slots(k, r) for k in range(4)] == g["reads"]
+
+
+def test_triple_buffer_is_a_fifo():
+    """Alternating writes and reads through the Fig. 2 layout deliver D, then the
+    written tokens in order (the slot 3r -> 0 copy carries the overlap)."""
+    for r in (1, 2, 4, 5):
+        tb = PL.TripleBuffer(r, "D")
+        got, nxt = [], 0
+        for _ in range(9):
+            tb.write(list(range(nxt, nxt + r)))
+            nxt += r
+            got += tb.read()
+        assert got == ["D"] + list(range(9 * r - 1))
