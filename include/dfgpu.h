@@ -1,0 +1,216 @@
+/*
+ * dfgpu.h -- C ABI of the dynamic-data-rate dataflow engine for one B300 (sm_103a).
+ *
+ * The engine executes actor networks in the sense of Boutellier & Hautala,
+ * "Executing Dynamic Data Rate Actor Networks on OpenCL Platforms" (SiPS 2016):
+ *
+ *   - a network is a set of actors joined by order-preserving FIFO channels
+ *     (Sec. 2.2); a channel joins one output port to one input port (Sec. 3.2);
+ *   - every channel has a token rate r > 0 adopted by both end ports (Sec. 2.2);
+ *   - a dynamic actor owns one control input port of rate 1; per firing it
+ *     consumes one control token, which fixes each regular port's rate to 0 or
+ *     r for that firing (Sec. 2.2, the control function of Sec. 3.1);
+ *   - channels not attached to a control port may hold initial (delay) tokens
+ *     (Sec. 2.2; more than one is the generalisation mentioned in Sec. 3.2).
+ *
+ * Execution model.  df_run(n) performs n steps on the device.  A step visits
+ * the actors in the order they were added and fires each one as many times as
+ * it is enabled (the longest prefix of its pending firings whose cumulative
+ * consumption fits the tokens present and whose cumulative production fits
+ * the free space).  All rate decisions, scans, gathers and scatters happen in
+ * CUDA kernels; the host is not involved between firings.  The resulting
+ * channel contents equal those of a sequential interpreter that fires one
+ * actor at a time (Kahn determinism).
+ *
+ * Memory.  A network owns every device buffer it allocates (channel rings,
+ * counters, per-actor state); df_net_destroy frees them.  Channels are ring
+ * buffers of `capacity` tokens of `token_bytes` bytes, token i of the stream
+ * living in slot i mod capacity.  Push and pop copy (the caller keeps its
+ * buffers).  All device work of a network is ordered on its stream.
+ *
+ * Errors.  Every call returns a df_status; DF_OK (0) on success, a negative
+ * code otherwise.  Out-parameters are written only on success.  No call aborts
+ * the process.  Device-side waits are bounded: a wait that runs out reports
+ * DF_ETIMEOUT through the network's status word instead of hanging.
+ *
+ * Thread safety: a network must not be used from two host threads at once.
+ */
+#ifndef DFGPU_H
+#define DFGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t df_status;
+enum {
+    DF_OK = 0,
+    DF_EINVAL = -1,      /* invalid argument or network (validation failure) */
+    DF_ENOMEM = -2,      /* device or host allocation failed */
+    DF_EFULL = -3,       /* push does not fit the free space of every output channel */
+    DF_EEMPTY = -4,      /* nothing to pop where tokens were required */
+    DF_ESTATE = -5,      /* call not allowed in the network's current state */
+    DF_EDEADLOCK = -6,   /* run(-1) stopped without reaching quiescence within its step limit */
+    DF_ETIMEOUT = -7,    /* a bounded device-side wait ran out */
+    DF_ECUDA = -8,       /* a CUDA runtime call failed */
+    DF_ENOTSUP = -9      /* configuration outside what the kernels implement */
+};
+
+/* Actor kinds (df_actor_add).  Port numbering is per kind; for every dynamic
+ * kind input port 0 is the control port (rate 1, u32 token = bit mask). */
+enum {
+    DF_SOURCE = 1,    /* host push endpoint; out ports 0..n-1 each receive every pushed token */
+    DF_SINK = 2,      /* host pop endpoint; in port 0 */
+    DF_COPY = 3,      /* static: in 0 -> every out port; bytes per firing equal on all ports */
+    DF_DPD = 4,       /* dynamic fused predistorter (Sec. 4.2): in 0 ctrl, in 1 data, out 0;
+                         params df_dpd_params; all ports rate 1; token = block_len complex64 */
+    DF_DPD_POLY = 5,  /* dynamic (Sec. 4.2 "P"): in 0 ctrl, in 1 data -> out k = branch k signal */
+    DF_DPD_FIR = 6,   /* static FIR of one branch: in 0 -> out 0, rate 1 */
+    DF_DPD_ADD = 7,   /* dynamic (Sec. 4.2 "A"): in 0 ctrl, in k+1 branch k -> out 0 */
+    DF_MD = 8         /* fused motion detector: in 0 current frame, in 1 previous frame;
+                         out 0 tile records (variable rate, r_max = tiles per frame),
+                         out 1 per-frame record count (u32); params df_md_params */
+};
+
+#define DF_MAX_BRANCHES 16
+#define DF_MAX_TAPS 32
+
+/* Predistorter parameters (DF_DPD, DF_DPD_POLY, DF_DPD_FIR, DF_DPD_ADD).
+ * Branch k computes z_k = |x|^(orders[k]-1) x (orders odd, >= 1), filters it
+ * with the M-tap complex FIR h[k*M .. k*M+M-1], and the active branches are
+ * summed in ascending k.  A branch's FIR sees only the blocks in which the
+ * branch was active (its input stream is the compaction of those blocks).
+ * h is complex64 interleaved (re, im), host memory, copied at df_actor_add.
+ * DF_DPD_POLY uses K/orders; DF_DPD_FIR uses M and h of branch `branch`;
+ * DF_DPD_ADD uses K and block_len. */
+typedef struct {
+    int32_t K;                          /* branches, 1..DF_MAX_BRANCHES */
+    int32_t M;                          /* taps, 1..DF_MAX_TAPS */
+    int32_t orders[DF_MAX_BRANCHES];    /* odd polynomial order per branch */
+    uint32_t block_len;                 /* samples per token (complex64) */
+    int32_t branch;                     /* DF_DPD_FIR only: which row of h */
+    const float *h;                     /* K*M complex64 (2*K*M floats), host */
+} df_dpd_params;
+
+/* Motion-detector parameters (DF_MD).  Frames are height x width uint8,
+ * row-major (token_bytes = width*height).  A pixel is moving iff
+ * |cur - prev| > threshold; the mask is opened by a 3x3 erosion (pixels
+ * outside the frame count as set) then a 3x3 dilation (outside counts as
+ * clear); for every 16x16 tile (raster order, partial last tile row allowed)
+ * with count > 0 one 8-byte record {u16 x, u16 y, u32 count} is emitted, x/y
+ * being the tile's top-left pixel.  width must be a multiple of 32. */
+typedef struct {
+    int32_t width;
+    int32_t height;
+    int32_t threshold;                  /* 25 in the benchmark */
+    int32_t tile;                       /* must be 16 */
+} df_md_params;
+
+typedef struct df_net df_net;
+
+/* Create an empty network on `device`.  `cuda_stream` is a cudaStream_t the
+ * network will use for all its work (NULL: the network creates and owns a
+ * non-blocking stream).  *out receives the handle. */
+df_status df_net_create(df_net **out, int device, void *cuda_stream);
+
+/* Free every resource of the network (NULL-safe).  Waits for its stream. */
+void df_net_destroy(df_net *net);
+
+/* Add an actor of `kind` with kind-specific `params` (copied).  Returns its
+ * id in *out_id; ids are dense and give the step order (Sec. 3.3 leaves the
+ * schedule to the OS; this engine fixes it to insertion order). */
+df_status df_actor_add(df_net *net, int32_t kind, const void *params, size_t params_bytes,
+                       int32_t *out_id);
+
+/* Connect output port src_port of src_actor to input port dst_port of
+ * dst_actor by a FIFO of `capacity_tokens` tokens of `token_bytes` bytes with
+ * token rate `rate` (Sec. 2.2).  `initial_tokens` delay tokens are present
+ * before any firing; their contents come from `initial_data` (host,
+ * initial_tokens*token_bytes bytes) or are zero when it is NULL.  Control
+ * channels need rate 1 and no initial tokens.  capacity must be >= initial +
+ * rate.  Self-loops (src_actor == dst_actor) are rejected. */
+df_status df_channel_connect(df_net *net, int32_t src_actor, int32_t src_port,
+                             int32_t dst_actor, int32_t dst_port, uint32_t token_bytes,
+                             uint32_t rate, uint32_t capacity_tokens, uint32_t initial_tokens,
+                             const void *initial_data, int32_t *out_ch);
+
+/* Validate (ports connected exactly once and numbered densely, rates and token
+ * sizes consistent with each actor kind), plan and allocate device memory.
+ * The network is frozen afterwards. */
+df_status df_net_finalize(df_net *net);
+
+/* Copy n_tokens tokens (n_tokens*token_bytes bytes at `src`, host or device
+ * memory) into every output channel of source actor `src_actor`.
+ * All-or-nothing: DF_EFULL when any channel lacks space (nothing written). */
+df_status df_push(df_net *net, int32_t src_actor, const void *src, uint64_t n_tokens,
+                  uint64_t *n_pushed);
+
+/* Run n_steps steps (n_steps < 0: until a step fires nothing, at most 2^20
+ * steps, else DF_EDEADLOCK).  Blocks until the device work is done, then
+ * reports the device status word and, if non-NULL, the number of firings. */
+df_status df_run(df_net *net, int64_t n_steps, uint64_t *n_firings);
+
+/* Run flags for df_run_ex. */
+enum {
+    DF_RUN_ASYNC = 1,        /* enqueue only (n_steps >= 0); no host sync, no firing count */
+    DF_RUN_GRAPH = 2,        /* replay a CUDA graph of n_steps steps (captured once per n) */
+    DF_RUN_PERSISTENT = 4,   /* one persistent cooperative kernel runs all steps */
+    DF_RUN_NO_BATCH = 8      /* one launch per predistorter actor instead of one per group */
+};
+df_status df_run_ex(df_net *net, int64_t n_steps, uint32_t flags, uint64_t *n_firings);
+
+/* Wait for the network's stream and return the device status word (DF_OK or
+ * the first device-side error) and the total number of firings so far. */
+df_status df_sync(df_net *net, uint64_t *total_firings);
+
+/* Copy up to max_tokens tokens from the input channel of sink `sink_actor`
+ * into `dst` (host or device memory).  Blocks until the copy is done. */
+df_status df_pop(df_net *net, int32_t sink_actor, void *dst, uint64_t max_tokens,
+                 uint64_t *n_popped);
+
+/* Counters of channel `ch`: tokens produced (excluding initial tokens),
+ * consumed, and currently held.  produced + initial == consumed + occupancy. */
+df_status df_channel_counters(df_net *net, int32_t ch, uint64_t *produced, uint64_t *consumed,
+                              uint64_t *occupancy);
+
+/* Tile configuration of the predistorter kernel for one actor (0 = default):
+ * samples per tile and threads per CTA.  The autotuner sets these. */
+df_status df_dpd_set_tile(df_net *net, int32_t actor, uint32_t tile, uint32_t threads);
+
+/* Time every supported tile configuration on the network's current pending
+ * predistorter work (the firings a step would take now) and keep the fastest
+ * for every DF_DPD actor / group.  Runs one step; returns its firings. */
+df_status df_autotune(df_net *net, uint64_t *n_firings);
+
+/* Text for a status code (static storage). */
+const char *df_status_str(df_status s);
+
+/* ---------------------------------------------------------------------------
+ * Stateless predistorter operators (device pointers, caller's stream).
+ * One contiguous signal of n samples, every branch active, zero history:
+ *   y[t] = sum_k sum_{m<M} h[k,m] z_k[t-m],  z_k = |x|^(orders[k]-1) x,  z_k[<0] = 0.
+ * x, y: n complex64; h: K*M complex64 (device); orders: host array of K ints.
+ * ------------------------------------------------------------------------- */
+df_status df_dpd_forward(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                         const int32_t *orders, void *y, void *cuda_stream);
+
+/* Adjoint of df_dpd_forward for a real loss L.  grad_y, grad_x and grad_h use
+ * the convention dL/dRe + i dL/dIm (PyTorch's for complex tensors):
+ *   grad_h[k,m] = sum_t grad_y[t] conj(z_k[t-m])
+ *   gz_k[j]     = sum_m conj(h[k,m]) grad_y[j+m]
+ *   grad_x[j]   = sum_k (q_k+1) u^q_k gz_k[j] + q_k u^(q_k-1) x^2 conj(gz_k[j]),
+ *                 u = |x[j]|^2, q_k = (orders[k]-1)/2.
+ * grad_x may be NULL.  The z_k are recomputed from x, not stored.  grad_h is
+ * reduced deterministically (fixed-order two-level sum).  Uses a scratch
+ * buffer the library allocates once per device and grows on demand. */
+df_status df_dpd_backward(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                          const int32_t *orders, const void *grad_y, void *grad_x, void *grad_h,
+                          void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFGPU_H */

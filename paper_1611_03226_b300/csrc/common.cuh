@@ -1,0 +1,139 @@
+// Shared host/device definitions of the dataflow engine.
+//
+// Every channel is a ring of `cap` slots of `tok` bytes in device memory.
+// Its two counters live in device memory: wr = tokens ever written (initial
+// tokens included), rd = tokens ever read; token i sits in slot i mod cap.
+// Counters are 64-bit and only grow, so occupancy = wr - rd and
+// free = cap - (wr - rd) are exact at any time.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/dfgpu.h"
+
+namespace dfg {
+
+constexpr int kMaxPorts = 16;
+
+struct ChanDesc {          // immutable after finalize
+  uint8_t* ring;
+  uint64_t cap;            // slots
+  uint64_t tok;            // bytes per token
+  uint32_t rate;
+  uint32_t id;             // index into the counter array
+};
+
+struct EngineDev {          // device-resident engine state
+  unsigned long long fired_total;
+  unsigned long long fired_step;
+  int32_t status;           // DF_OK or the first device-side error
+  int32_t status_where;     // which kernel / wait reported it
+  unsigned int barrier_count;   // persistent-kernel grid barrier
+  unsigned int barrier_gen;
+};
+
+// where-codes for EngineDev::status_where
+enum : int32_t { kWhereMdPipe = 1, kWhereGridBarrier = 2, kWhereDpd = 3 };
+
+__host__ __device__ inline uint64_t* wr_ptr(uint64_t* ctr, uint32_t ch) { return ctr + 2 * ch; }
+__host__ __device__ inline uint64_t* rd_ptr(uint64_t* ctr, uint32_t ch) { return ctr + 2 * ch + 1; }
+
+__host__ __device__ inline uint8_t* slot_ptr(const ChanDesc& c, uint64_t token_index) {
+  return c.ring + (token_index % c.cap) * c.tok;
+}
+
+#ifdef __CUDACC__
+__device__ inline void set_status(EngineDev* e, int32_t code, int32_t where) {
+  if (atomicCAS(&e->status, 0, code) == 0) e->status_where = where;
+}
+#endif
+
+// ------------------------------------------------------------------ copy ----
+struct CopyPlan { uint64_t n; uint64_t rd0; uint64_t wr0[kMaxPorts]; };
+
+struct CopyArgs {
+  ChanDesc in;
+  ChanDesc out[kMaxPorts];
+  int n_out;
+  int unit;                 // copy granularity in bytes: 16, 4 or 1
+  uint64_t* ctr;
+  EngineDev* eng;
+  CopyPlan* plan;
+};
+
+// --------------------------------------------------- fused predistorter ----
+constexpr int kMaxBranches = DF_MAX_BRANCHES;
+constexpr int kMaxTaps = DF_MAX_TAPS;
+
+struct DpdPlanHdr {
+  uint64_t n;               // firings this step
+  uint64_t rd_data0;        // data token index of firing 0
+  uint64_t wr_out0;         // output token index of firing 0
+  uint32_t parity_in;       // history buffer the body reads
+  uint32_t pad;
+};
+
+struct DpdArgs {            // one per predistorter actor, stored in device memory
+  ChanDesc ctrl, data, out;
+  uint64_t* ctr;
+  EngineDev* eng;
+  int K, M, MT;             // MT = padded tap count of the kernel instantiation
+  uint32_t L;               // samples per block
+  uint32_t n_max;           // capacity of the per-firing arrays
+  int orders[kMaxBranches];
+  const float2* h;          // K * MT taps (zero padded beyond M)
+  DpdPlanHdr* plan;
+  uint32_t* masks;          // [n_max]
+  uint32_t* rank;           // [K][n_max]: active firings of branch k before firing i
+  uint32_t* act;            // [K][n_max]: firing index of the a-th active block of k
+  uint32_t* cnt;            // [K]: active firings of k this step
+  float2* hist;             // [2][K][MT-1]: raw input samples preceding the batch
+  uint32_t* parity;         // which half of hist is current
+};
+
+// ----------------------------------------------------- motion detector ----
+struct MdPlanHdr {
+  uint64_t n_cand;          // frames the main kernel processes this step
+  uint64_t rd_cur0, rd_prev0, wr_rec0, wr_cnt0;
+  uint64_t free_rec;        // free record slots at plan time
+};
+
+struct MdArgs {
+  ChanDesc cur, prev, rec, cnt;
+  uint64_t* ctr;
+  EngineDev* eng;
+  int W, H, thr;
+  int words;                // W / 32
+  int tiles_x, tiles_y, n_tiles;
+  int strips;               // ceil(H / 16)
+  int dedup;                // prev channel == cur channel delayed by one token
+  uint32_t n_max;
+  MdPlanHdr* plan;
+  uint16_t* counts;         // [n_max][n_tiles]
+  uint32_t* frame_tot;      // [n_max] records per frame
+  uint64_t* frame_off;      // [n_max + 1] exclusive scan of frame_tot
+  long long wait_limit_ns;  // bound of every device-side wait
+};
+
+// ----------------------------------------------------------- launchers ----
+cudaError_t launch_set_u64(uint64_t* p, uint64_t v, cudaStream_t s);
+cudaError_t launch_add_u64(uint64_t* p, uint64_t v, cudaStream_t s);
+cudaError_t launch_step_begin(EngineDev* e, cudaStream_t s);
+cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s);
+
+cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t s);
+cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile,
+                            uint32_t threads, int max_mt, int n_sm, cudaStream_t s);
+int dpd_supported_mt(int M);   // padded tap count used for M (0 = unsupported)
+
+cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s);
+size_t md_smem_bytes(int W);
+
+cudaError_t dpd_forward_stateless(const float2* x, uint64_t n, const float2* h, int K, int M,
+                                  const int* orders, float2* y, cudaStream_t s);
+cudaError_t dpd_backward_stateless(const float2* x, uint64_t n, const float2* h, int K, int M,
+                                   const int* orders, const float2* gy, float2* gx, float2* gh,
+                                   float2* scratch, size_t scratch_elems, cudaStream_t s);
+size_t dpd_backward_scratch_elems(uint64_t n, int K, int M);
+
+}  // namespace dfg

@@ -1,0 +1,638 @@
+// Dynamic predistortion actor (Sec. 4.2): Poly -> FIR_k -> Adder fused into
+// one dynamic actor whose control token (u32 mask, bit k = branch k active)
+// is read per firing on the device.
+//
+// Plan kernel (one CTA per actor of a group):
+//   n     = min(control tokens, data tokens, free output slots)   (all rates 1)
+//   masks = the n control tokens
+//   for every branch k an exclusive scan over the n firings of bit k gives
+//   rank[k][i] (how many earlier firings of this step had k active) and the
+//   compaction act[k][a] (firing of the a-th active block of k).  These are
+//   the consumption / production counts of the internal Poly->FIR_k->Adder
+//   channels, whose rate is 0 or 1 per firing.
+//   The persistent history of branch k (the last MT-1 raw input samples of
+//   branch k's compacted stream) is advanced into the other half of a double
+//   buffer, and the channel counters are committed.
+// Body kernel (persistent grid, one launch for a whole group of actors):
+//   work item = (actor, firing, tile of T samples).  The x window with MT-1
+//   samples of halo is staged in shared memory; per active branch the branch
+//   signal z = |x|^(o-1) x is formed in a padded shared buffer (for tile 0
+//   the halo comes from the branch's own history: the previous block in which
+//   that branch was active, found through rank/act, or the persistent
+//   history); each thread accumulates R consecutive outputs of the M-tap
+//   complex FIR with the taps held in registers; the Adder is the running
+//   sum over branches in registers.
+#include <algorithm>
+#include "common.cuh"
+
+namespace dfg {
+
+__device__ __forceinline__ float2 cmac(float2 acc, float2 h, float2 z) {
+  acc.x = fmaf(h.x, z.x, acc.x);
+  acc.x = fmaf(-h.y, z.y, acc.x);
+  acc.y = fmaf(h.x, z.y, acc.y);
+  acc.y = fmaf(h.y, z.x, acc.y);
+  return acc;
+}
+// acc += a * conj(b)
+__device__ __forceinline__ float2 cmac_conj_b(float2 acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  acc.y = fmaf(-a.x, b.y, acc.y);
+  return acc;
+}
+
+// |x|^(2q) x with u = |x|^2 raised by repeated products
+__device__ __forceinline__ float2 psi_q(float2 x, int q) {
+  const float u = fmaf(x.x, x.x, x.y * x.y);
+  float p = 1.f;
+  for (int i = 0; i < q; ++i) p *= u;
+  return make_float2(p * x.x, p * x.y);
+}
+
+// ---------------------------------------------------------------- scans ----
+__device__ uint64_t block_exclusive_scan_u64(uint64_t v, uint64_t* sw, uint64_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sw[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint64_t s = lane < nw ? sw[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) sw[lane] = s;
+  }
+  __syncthreads();
+  const uint64_t before = wid ? sw[wid - 1] : 0;
+  *total = sw[nw - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+// ------------------------------------------------------------ FIR cores ----
+// Shared windows are padded with one element after every R elements so that
+// threads reading at stride R elements hit distinct banks.
+// Causal chunk: acc[r] += sum_{m<MC} h[m] * zs[v], v = p*R + shift + r - m + MC - 1.
+// Taps m >= m_valid are zero (unpadded tap rows).
+template <int R, int MC>
+__device__ __forceinline__ void fir_causal(float2 (&acc)[R], const float2* __restrict__ zs, int p,
+                                           int shift, const float2* __restrict__ h, int m_valid) {
+  float2 hk[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) hk[m] = m < m_valid ? __ldg(h + m) : make_float2(0.f, 0.f);
+  const float2* zb = zs + p * (R + 1) + shift + shift / R;
+#pragma unroll
+  for (int s = 0; s < R + MC - 1; ++s) {
+    const float2 z = zb[s + s / R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = r + MC - 1 - s;
+      if (m >= 0 && m < MC) acc[r] = cmac(acc[r], hk[m], z);
+    }
+  }
+}
+
+// Anti-causal chunk with conjugated taps: acc[r] += sum_m conj(h[m]) * gs[v], v = p*R + shift + r + m.
+template <int R, int MC>
+__device__ __forceinline__ void fir_anticausal_conj(float2 (&acc)[R], const float2* __restrict__ gs,
+                                                    int p, int shift, const float2* __restrict__ h,
+                                                    int m_valid) {
+  float2 ck[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const float2 t = m < m_valid ? __ldg(h + m) : make_float2(0.f, 0.f);
+    ck[m] = make_float2(t.x, -t.y);
+  }
+  const float2* gb = gs + p * (R + 1) + shift + shift / R;
+#pragma unroll
+  for (int s = 0; s < R + MC - 1; ++s) {
+    const float2 g = gb[s + s / R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = s - r;
+      if (m >= 0 && m < MC) acc[r] = cmac(acc[r], ck[m], g);
+    }
+  }
+}
+
+// Tap-gradient chunk: ph[m] += sum_r g[r] * conj(zs[v]), v = p*R + shift + r - m + MC - 1.
+template <int R, int MC>
+__device__ __forceinline__ void gh_chunk(float2 (&ph)[MC], const float2 (&gr)[R],
+                                         const float2* __restrict__ zs, int p, int shift) {
+  const float2* zb = zs + p * (R + 1) + shift + shift / R;
+#pragma unroll
+  for (int s = 0; s < R + MC - 1; ++s) {
+    const float2 z = zb[s + s / R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = r + MC - 1 - s;
+      if (m >= 0 && m < MC) ph[m] = cmac_conj_b(ph[m], gr[r], z);
+    }
+  }
+}
+
+// FIR of one branch over a staged window, MT <= 16 in one chunk, MT == 32 in two.
+// h points at the M valid taps of the branch (M <= MT).
+template <int R, int MT>
+__device__ __forceinline__ void fir_branch(float2 (&acc)[R], const float2* zs, int p,
+                                           const float2* h, int M) {
+  if constexpr (MT <= 16) {
+    fir_causal<R, MT>(acc, zs, p, 0, h, M);
+  } else {
+    fir_causal<R, 16>(acc, zs, p, 16, h, M);
+    fir_causal<R, 16>(acc, zs, p, 0, h + 16, M - 16);
+  }
+}
+
+int dpd_supported_mt(int M) {
+  if (M < 1 || M > 32) return 0;
+  if (M <= 4) return 4;
+  if (M <= 8) return 8;
+  if (M <= 16) return M;
+  return 32;
+}
+
+#define DPD_MT_CASES(X) X(4) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(32)
+
+// ----------------------------------------------------------------- plan ----
+__global__ void __launch_bounds__(256) k_dpd_plan(const DpdArgs* args) {
+  const DpdArgs& a = args[blockIdx.x];
+  __shared__ uint64_t s_n, s_rdc, s_rdd, s_wro;
+  __shared__ uint32_t s_par;
+  __shared__ uint64_t sw[32];
+  uint64_t* ctr = a.ctr;
+  if (threadIdx.x == 0) {
+    const uint64_t rdc = *rd_ptr(ctr, a.ctrl.id), wrc = *wr_ptr(ctr, a.ctrl.id);
+    const uint64_t rdd = *rd_ptr(ctr, a.data.id), wrd = *wr_ptr(ctr, a.data.id);
+    const uint64_t wro = *wr_ptr(ctr, a.out.id), rdo = *rd_ptr(ctr, a.out.id);
+    uint64_t n = wrc - rdc;
+    n = min(n, wrd - rdd);
+    n = min(n, a.out.cap - (wro - rdo));
+    n = min(n, (uint64_t)a.n_max);
+    s_n = n; s_rdc = rdc; s_rdd = rdd; s_wro = wro; s_par = *a.parity;
+  }
+  __syncthreads();
+  const uint32_t n = (uint32_t)s_n;
+  const uint32_t kmask = a.K >= 32 ? 0xffffffffu : ((1u << a.K) - 1u);
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+    a.masks[i] = *reinterpret_cast<const uint32_t*>(slot_ptr(a.ctrl, s_rdc + i)) & kmask;
+  __syncthreads();
+  for (int k = 0; k < a.K; ++k) {
+    uint64_t carry = 0;
+    for (uint32_t base = 0; base < n; base += blockDim.x) {
+      const uint32_t i = base + threadIdx.x;
+      const uint32_t bit = i < n ? (a.masks[i] >> k) & 1u : 0u;
+      uint64_t tot;
+      const uint64_t ex = block_exclusive_scan_u64(bit, sw, &tot);
+      if (i < n) {
+        a.rank[(size_t)k * a.n_max + i] = (uint32_t)(carry + ex);
+        if (bit) a.act[(size_t)k * a.n_max + carry + ex] = i;
+      }
+      carry += tot;
+    }
+    if (threadIdx.x == 0) a.cnt[k] = (uint32_t)carry;
+  }
+  __syncthreads();
+  const int H1 = a.MT - 1;
+  if (n > 0 && H1 > 0) {
+    const uint32_t par = s_par;
+    for (int e = threadIdx.x; e < a.K * H1; e += blockDim.x) {
+      const int k = e / H1, s = e % H1;
+      const int64_t pos = (int64_t)a.cnt[k] * a.L - H1 + s;
+      float2 v;
+      if (pos >= 0) {
+        const uint32_t f = a.act[(size_t)k * a.n_max + (uint32_t)(pos / a.L)];
+        v = reinterpret_cast<const float2*>(slot_ptr(a.data, s_rdd + f))[pos % a.L];
+      } else {
+        v = a.hist[((size_t)par * a.K + k) * H1 + (H1 + pos)];
+      }
+      a.hist[((size_t)(par ^ 1) * a.K + k) * H1 + s] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.plan->n = n;
+    a.plan->rd_data0 = s_rdd;
+    a.plan->wr_out0 = s_wro;
+    a.plan->parity_in = s_par;
+    if (n > 0) *a.parity = s_par ^ 1u;
+    *rd_ptr(ctr, a.ctrl.id) = s_rdc + n;
+    *rd_ptr(ctr, a.data.id) = s_rdd + n;
+    *wr_ptr(ctr, a.out.id) = s_wro + n;
+    atomicAdd(&a.eng->fired_step, (unsigned long long)n);
+    atomicAdd(&a.eng->fired_total, (unsigned long long)n);
+  }
+}
+
+cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t s) {
+  if (n_actors <= 0) return cudaSuccess;
+  k_dpd_plan<<<n_actors, 256, 0, s>>>(args_dev);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- body ----
+__device__ __forceinline__ float2 hist_sample(const DpdArgs& a, const DpdPlanHdr& pl, uint32_t i,
+                                              int k, int s) {
+  const int H1 = a.MT - 1;
+  const int64_t pos = (int64_t)a.rank[(size_t)k * a.n_max + i] * a.L - H1 + s;
+  if (pos >= 0) {
+    const uint32_t f = a.act[(size_t)k * a.n_max + (uint32_t)(pos / a.L)];
+    return reinterpret_cast<const float2*>(slot_ptr(a.data, pl.rd_data0 + f))[pos % a.L];
+  }
+  return a.hist[((size_t)pl.parity_in * a.K + k) * H1 + (H1 + pos)];
+}
+
+template <int R, int MT>
+__device__ void dpd_item(const DpdArgs& a, uint64_t local, float2* xs, float2* zs) {
+  const int P = blockDim.x, p = threadIdx.x;
+  const uint32_t T = R * P;
+  const DpdPlanHdr pl = *a.plan;
+  const uint64_t nt = (a.L + T - 1) / T;
+  const uint32_t i = (uint32_t)(local / nt);
+  const uint64_t t0 = (local % nt) * T;
+  const int len = (int)min((uint64_t)T, a.L - t0);
+  const uint32_t mask = a.masks[i];
+  float2* yb = reinterpret_cast<float2*>(slot_ptr(a.out, pl.wr_out0 + i)) + t0;
+  if (mask == 0) {
+    for (int o = p; o < len; o += P) yb[o] = make_float2(0.f, 0.f);
+    return;
+  }
+  const float2* xb = reinterpret_cast<const float2*>(slot_ptr(a.data, pl.rd_data0 + i));
+  const int W = (int)T + MT - 1;
+  for (int v = p; v < W; v += P) {
+    const int64_t pos = (int64_t)t0 - (MT - 1) + v;
+    xs[v] = (pos >= 0 && pos < (int64_t)(t0 + len)) ? xb[pos] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = make_float2(0.f, 0.f);
+  for (int k = 0; k < a.K; ++k) {
+    if (!((mask >> k) & 1u)) continue;
+    const int q = (a.orders[k] - 1) >> 1;
+    for (int v = p; v < W; v += P) {
+      const int64_t pos = (int64_t)t0 - (MT - 1) + v;
+      const float2 xv = pos >= 0 ? xs[v] : hist_sample(a, pl, i, k, (int)(MT - 1 + pos));
+      zs[v + v / R] = psi_q(xv, q);
+    }
+    __syncthreads();
+    fir_branch<R, MT>(acc, zs, p, a.h + (size_t)k * MT, MT);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) zs[p * (R + 1) + r] = acc[r];
+  __syncthreads();
+  for (int o = p; o < len; o += P) yb[o] = zs[o + o / R];
+  __syncthreads();
+}
+
+constexpr int kMaxGroup = 1024;
+
+template <int R>
+__global__ void __launch_bounds__(256) k_dpd_body(const DpdArgs* __restrict__ args, int G) {
+  extern __shared__ float4 smem_raw[];
+  __shared__ uint64_t s_off[kMaxGroup + 1];
+  __shared__ uint64_t sw[32];
+  const uint32_t T = R * blockDim.x;
+  uint64_t carry = 0;
+  for (int base = 0; base < G; base += blockDim.x) {
+    const int g = base + threadIdx.x;
+    uint64_t items = 0;
+    if (g < G) {
+      const DpdArgs& a = args[g];
+      items = a.plan->n * ((a.L + T - 1) / T);
+    }
+    uint64_t tot;
+    const uint64_t ex = block_exclusive_scan_u64(items, sw, &tot);
+    if (g < G) s_off[g] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) s_off[G] = carry;
+  __syncthreads();
+  const uint64_t total = carry;
+  int maxmt = 0;
+  for (int g = 0; g < G; ++g) maxmt = max(maxmt, args[g].MT);
+  float2* xs = reinterpret_cast<float2*>(smem_raw);
+  float2* zs = xs + (T + maxmt);
+  for (uint64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    int lo = 0, hi = G;             // s_off[lo] <= item < s_off[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_off[mid] <= item) lo = mid; else hi = mid;
+    }
+    const DpdArgs& a = args[lo];
+    const uint64_t local = item - s_off[lo];
+    switch (a.MT) {
+#define DPD_CASE(MTV) case MTV: dpd_item<R, MTV>(a, local, xs, zs); break;
+      DPD_MT_CASES(DPD_CASE)
+#undef DPD_CASE
+      default: break;
+    }
+  }
+}
+
+static size_t body_smem(uint32_t T, int R, int max_mt) {
+  const size_t W = T + max_mt;
+  return (W + (W + W / R + 2)) * sizeof(float2);
+}
+
+cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile, uint32_t threads,
+                            int max_mt, int n_sm, cudaStream_t s) {
+  if (n_actors <= 0) return cudaSuccess;
+  if (n_actors > kMaxGroup) return cudaErrorInvalidValue;
+  const int R = (int)(tile / threads);
+  const size_t smem = body_smem(tile, R, max_mt);
+  cudaError_t e;
+  int per_sm = 0;
+  if (R == 16) {
+    e = cudaFuncSetAttribute(k_dpd_body<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dpd_body<16>, threads, smem);
+    k_dpd_body<16><<<n_sm * std::max(per_sm, 1), threads, smem, s>>>(args_dev, n_actors);
+  } else if (R == 8) {
+    e = cudaFuncSetAttribute(k_dpd_body<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dpd_body<8>, threads, smem);
+    k_dpd_body<8><<<n_sm * std::max(per_sm, 1), threads, smem, s>>>(args_dev, n_actors);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- stateless operators ----
+// One signal, all branches active, zero history.  Taps arrive unpadded (K*M);
+// they are read with padding on the fly: tap m >= M contributes zero.
+constexpr int kStatelessR = 8;
+constexpr int kStatelessP = 128;
+
+struct StatelessArgs {
+  const float2* x;
+  const float2* gy;
+  float2* y;            // forward output or grad_x
+  float2* partial;      // [tiles][K][MT] tap-gradient partial sums
+  float2* gh;           // [K][M]
+  const float2* h;      // [K][M] taps
+  uint64_t n;
+  int K, M, MT;
+  int orders[kMaxBranches];
+};
+
+template <int R, int MT>
+__device__ void fwd_tile(const StatelessArgs& a, uint64_t tile, float2* xs, float2* zs) {
+  const int P = blockDim.x, p = threadIdx.x;
+  const uint64_t T = (uint64_t)R * P;
+  const uint64_t t0 = tile * T;
+  const int len = (int)min(T, a.n - t0);
+  const int W = (int)T + MT - 1;
+  for (int v = p; v < W; v += P) {
+    const int64_t pos = (int64_t)t0 - (MT - 1) + v;
+    xs[v] = (pos >= 0 && pos < (int64_t)(t0 + len)) ? a.x[pos] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = make_float2(0.f, 0.f);
+  for (int k = 0; k < a.K; ++k) {
+    const int q = (a.orders[k] - 1) >> 1;
+    for (int v = p; v < W; v += P) zs[v + v / R] = psi_q(xs[v], q);
+    __syncthreads();
+    fir_branch<R, MT>(acc, zs, p, a.h + (size_t)k * a.M, a.M);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) zs[p * (R + 1) + r] = acc[r];
+  __syncthreads();
+  for (int o = p; o < len; o += P) a.y[t0 + o] = zs[o + o / R];
+  __syncthreads();
+}
+
+template <int R>
+__global__ void __launch_bounds__(kStatelessP) k_dpd_fwd(StatelessArgs a) {
+  extern __shared__ float4 smem_raw[];
+  const uint64_t T = (uint64_t)R * blockDim.x;
+  const uint64_t nt = (a.n + T - 1) / T;
+  float2* xs = reinterpret_cast<float2*>(smem_raw);
+  float2* zs = xs + (T + a.MT);
+  for (uint64_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    switch (a.MT) {
+#define FWD_CASE(MTV) case MTV: fwd_tile<R, MTV>(a, t, xs, zs); break;
+      DPD_MT_CASES(FWD_CASE)
+#undef FWD_CASE
+      default: break;
+    }
+  }
+}
+
+// Deterministic block sum of one float2 per thread into out (thread 0 writes).
+__device__ float2 block_sum_f2(float2 v, float2* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  float2 s = make_float2(0.f, 0.f);
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) { s.x += red[w].x; s.y += red[w].y; }
+  __syncthreads();
+  return s;
+}
+
+template <int R, int MC>
+__device__ void gh_reduce_chunk(const StatelessArgs& a, uint64_t tile, int k, int m0,
+                                const float2 (&gr)[R], const float2* zs, int shift, float2* red) {
+  float2 ph[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) ph[m] = make_float2(0.f, 0.f);
+  gh_chunk<R, MC>(ph, gr, zs, threadIdx.x, shift);
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const float2 s = block_sum_f2(ph[m], red);
+    if (threadIdx.x == 0) a.partial[(tile * a.K + k) * a.MT + m0 + m] = s;
+  }
+}
+
+template <int R, int MT>
+__device__ void bwd_tile(const StatelessArgs& a, uint64_t tile, float2* xs, float2* zs, float2* gs,
+                         float2* red) {
+  const int P = blockDim.x, p = threadIdx.x;
+  const uint64_t T = (uint64_t)R * P;
+  const uint64_t t0 = tile * T;
+  const int len = (int)min(T, a.n - t0);
+  const int W = (int)T + MT - 1;
+  for (int v = p; v < W; v += P) {
+    const int64_t pos = (int64_t)t0 - (MT - 1) + v;
+    xs[v] = (pos >= 0 && pos < (int64_t)(t0 + len)) ? a.x[pos] : make_float2(0.f, 0.f);
+    const uint64_t gp = t0 + v;       // g window [t0, t0 + T + MT - 1), zero beyond n
+    gs[v + v / R] = gp < a.n ? a.gy[gp] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 gr[R], gx[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    gr[r] = (p * R + r < len) ? gs[p * (R + 1) + r] : make_float2(0.f, 0.f);
+    gx[r] = make_float2(0.f, 0.f);
+  }
+  for (int k = 0; k < a.K; ++k) {
+    const int q = (a.orders[k] - 1) >> 1;
+    for (int v = p; v < W; v += P) zs[v + v / R] = psi_q(xs[v], q);
+    __syncthreads();
+    const float2* hk = a.h + (size_t)k * a.M;
+    float2 gz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) gz[r] = make_float2(0.f, 0.f);
+    if constexpr (MT <= 16) {
+      gh_reduce_chunk<R, MT>(a, tile, k, 0, gr, zs, 0, red);
+      fir_anticausal_conj<R, MT>(gz, gs, p, 0, hk, a.M);
+    } else {
+      gh_reduce_chunk<R, 16>(a, tile, k, 0, gr, zs, 16, red);
+      gh_reduce_chunk<R, 16>(a, tile, k, 16, gr, zs, 0, red);
+      fir_anticausal_conj<R, 16>(gz, gs, p, 0, hk, a.M);
+      fir_anticausal_conj<R, 16>(gz, gs, p, 16, hk + 16, a.M - 16);
+    }
+    if (a.y) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float2 x = xs[p * R + r + MT - 1];
+        const float u = fmaf(x.x, x.x, x.y * x.y);
+        float uq1 = 1.f;
+        for (int i = 0; i + 1 < q; ++i) uq1 *= u;
+        const float uq = q > 0 ? uq1 * u : 1.f;
+        const float c1 = (q + 1) * uq;
+        gx[r].x = fmaf(c1, gz[r].x, gx[r].x);
+        gx[r].y = fmaf(c1, gz[r].y, gx[r].y);
+        if (q > 0) {
+          const float c2 = q * uq1;
+          const float2 x2 = make_float2(x.x * x.x - x.y * x.y, 2.f * x.x * x.y);
+          // c2 * x^2 * conj(gz)
+          gx[r].x = fmaf(c2, x2.x * gz[r].x + x2.y * gz[r].y, gx[r].x);
+          gx[r].y = fmaf(c2, x2.y * gz[r].x - x2.x * gz[r].y, gx[r].y);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (a.y) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) zs[p * (R + 1) + r] = gx[r];
+    __syncthreads();
+    for (int o = p; o < len; o += P) a.y[t0 + o] = zs[o + o / R];
+    __syncthreads();
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kStatelessP) k_dpd_bwd(StatelessArgs a) {
+  extern __shared__ float4 smem_raw[];
+  __shared__ float2 red[32];
+  const uint64_t T = (uint64_t)R * blockDim.x;
+  const uint64_t nt = (a.n + T - 1) / T;
+  const size_t W = T + a.MT;
+  float2* xs = reinterpret_cast<float2*>(smem_raw);
+  float2* zs = xs + W;
+  float2* gs = zs + (W + W / R + 2);
+  for (uint64_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    switch (a.MT) {
+#define BWD_CASE(MTV) case MTV: bwd_tile<R, MTV>(a, t, xs, zs, gs, red); break;
+      DPD_MT_CASES(BWD_CASE)
+#undef BWD_CASE
+      default: break;
+    }
+  }
+}
+
+// grad_h[k][m] = sum over tiles (ascending) of partial[tile][k][m]; fixed order.
+__global__ void k_gh_final(const float2* partial, uint64_t n_tiles, int K, int M, int MT, float2* gh) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K * M) return;
+  const int k = e / M, m = e % M;
+  float2 s = make_float2(0.f, 0.f);
+  for (uint64_t t = 0; t < n_tiles; ++t) {
+    const float2 v = partial[(t * K + k) * MT + m];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  gh[e] = s;
+}
+
+static uint64_t stateless_tiles(uint64_t n) {
+  const uint64_t T = (uint64_t)kStatelessR * kStatelessP;
+  return (n + T - 1) / T;
+}
+
+size_t dpd_backward_scratch_elems(uint64_t n, int K, int M) {
+  return stateless_tiles(n) * (size_t)K * dpd_supported_mt(M);
+}
+
+static cudaError_t stateless_common(StatelessArgs& a, const float2* h, int K, int M,
+                                    const int* orders) {
+  a.K = K;
+  a.M = M;
+  a.MT = dpd_supported_mt(M);
+  if (!a.MT || K < 1 || K > kMaxBranches) return cudaErrorInvalidValue;
+  for (int k = 0; k < K; ++k) a.orders[k] = orders[k];
+  a.h = h;
+  return cudaSuccess;
+}
+
+cudaError_t dpd_forward_stateless(const float2* x, uint64_t n, const float2* h, int K, int M,
+                                  const int* orders, float2* y, cudaStream_t s) {
+  StatelessArgs a{};
+  a.x = x;
+  a.y = y;
+  a.n = n;
+  cudaError_t e = stateless_common(a, h, K, M, orders);
+  if (e != cudaSuccess || n == 0) return e;
+  const uint64_t T = (uint64_t)kStatelessR * kStatelessP;
+  const size_t W = T + a.MT;
+  const size_t smem = (W + W + W / kStatelessR + 2) * sizeof(float2);
+  e = cudaFuncSetAttribute(k_dpd_fwd<kStatelessR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t nt = stateless_tiles(n);
+  const unsigned grid = (unsigned)std::min<uint64_t>(nt, 148ull * 16);
+  k_dpd_fwd<kStatelessR><<<grid, kStatelessP, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t dpd_backward_stateless(const float2* x, uint64_t n, const float2* h, int K, int M,
+                                   const int* orders, const float2* gy, float2* gx, float2* gh,
+                                   float2* scratch, size_t scratch_elems, cudaStream_t s) {
+  StatelessArgs a{};
+  a.x = x;
+  a.gy = gy;
+  a.y = gx;
+  a.gh = gh;
+  a.n = n;
+  cudaError_t e = stateless_common(a, h, K, M, orders);
+  if (e != cudaSuccess) return e;
+  if (scratch_elems < dpd_backward_scratch_elems(n, K, M)) return cudaErrorInvalidValue;
+  a.partial = scratch;
+  const uint64_t nt = stateless_tiles(n);
+  if (n > 0) {
+    const uint64_t T = (uint64_t)kStatelessR * kStatelessP;
+    const size_t W = T + a.MT;
+    const size_t smem = (W + 2 * (W + W / kStatelessR + 2)) * sizeof(float2);
+    e = cudaFuncSetAttribute(k_dpd_bwd<kStatelessR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<uint64_t>(nt, 148ull * 16);
+    k_dpd_bwd<kStatelessR><<<grid, kStatelessP, smem, s>>>(a);
+  }
+  k_gh_final<<<(K * M + 127) / 128, 128, 0, s>>>(a.partial, nt, K, M, a.MT, gh);
+  return cudaGetLastError();
+}
+
+}  // namespace dfg

@@ -1,0 +1,832 @@
+// Host side of the engine: network construction and validation (Sec. 2.2,
+// Sec. 3.2), planning of the device arena, the step program, and the host
+// endpoints push / pop.
+//
+// Planning.  At finalize every channel ring, the counter array and the
+// per-actor state are carved out of one device allocation, each piece aligned
+// to 256 bytes.  The step program is a list of operations, one per actor in
+// insertion order; consecutive fused-predistorter actors that share no
+// channel form a group that is planned and fired by one plan launch and one
+// body launch.  A step never returns to the host: rate decisions, scans,
+// gathers and scatters are all device kernels reading the device counters.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace dfg;
+
+namespace {
+
+struct ActorH {
+  int32_t kind = 0;
+  std::vector<int32_t> in, out;       // channel per port, -1 = unconnected
+  df_dpd_params dpd{};
+  std::vector<float> h;               // K*M complex taps (host copy)
+  df_md_params md{};
+  uint32_t tile = 0, threads = 0;     // predistorter body configuration (0 = default)
+};
+
+struct ChanH {
+  int32_t src, sport, dst, dport;
+  uint32_t tok, rate, cap, init;
+  std::vector<uint8_t> init_data;
+  ChanDesc desc{};
+};
+
+enum OpKind { kOpCopy = 1, kOpDpd = 2, kOpMd = 3 };
+
+struct Op {
+  OpKind kind;
+  CopyArgs copy{};
+  MdArgs md{};
+  DpdArgs* dpd_dev = nullptr;        // group args (device)
+  int dpd_n = 0;                      // actors in the group
+  int dpd_first_actor = -1;           // actor id of the first member
+  int max_mt = 0;
+};
+
+struct Piece {                        // one carve of the device arena
+  size_t off = 0, bytes = 0;
+};
+
+}  // namespace
+
+struct df_net {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool finalized = false;
+  int n_sm = 148;
+  std::vector<ActorH> actors;
+  std::vector<ChanH> chans;
+  uint8_t* arena = nullptr;
+  size_t arena_bytes = 0;
+  uint64_t* d_ctr = nullptr;
+  EngineDev* d_eng = nullptr;
+  std::vector<DpdArgs> dpd_host;      // one per predistorter actor (by dpd index)
+  std::vector<int> dpd_index;         // actor id -> index in dpd_host (-1)
+  DpdArgs* d_dpd = nullptr;           // device copy of dpd_host
+  std::vector<Op> program;
+  uint64_t* h_pin = nullptr;          // pinned staging (counters, status)
+  std::map<std::pair<int64_t, uint32_t>, cudaGraphExec_t> graphs;
+  long long wait_limit_ns = 1000000000LL;
+};
+
+namespace {
+
+df_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DF_OK : DF_ECUDA; }
+
+#define DF_CUDA(x)                               \
+  do {                                           \
+    cudaError_t e_ = (x);                        \
+    if (e_ != cudaSuccess) return DF_ECUDA;      \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool is_dynamic(int32_t kind) {
+  return kind == DF_DPD || kind == DF_DPD_POLY || kind == DF_DPD_ADD;
+}
+
+int n_connected(const std::vector<int32_t>& v) {
+  return (int)std::count_if(v.begin(), v.end(), [](int32_t c) { return c >= 0; });
+}
+
+bool dense(const std::vector<int32_t>& v) {
+  for (int32_t c : v)
+    if (c < 0) return false;
+  return true;
+}
+
+uint32_t tiles_per_frame(const df_md_params& m) {
+  return (uint32_t)(((m.height + 15) / 16) * ((m.width + 15) / 16));
+}
+
+df_status validate_actor(const df_net* net, int a) {
+  const ActorH& A = net->actors[a];
+  if (!dense(A.in) || !dense(A.out)) return DF_EINVAL;
+  auto ch = [&](int32_t id) -> const ChanH& { return net->chans[id]; };
+  switch (A.kind) {
+    case DF_SOURCE:
+      if (!A.in.empty() || A.out.empty()) return DF_EINVAL;
+      return DF_OK;
+    case DF_SINK:
+      if (A.in.size() != 1 || !A.out.empty()) return DF_EINVAL;
+      return DF_OK;
+    case DF_COPY: {
+      if (A.in.size() != 1 || A.out.empty() || (int)A.out.size() > kMaxPorts) return DF_EINVAL;
+      const ChanH& i = ch(A.in[0]);
+      for (int32_t o : A.out)
+        if ((uint64_t)i.tok * i.rate != (uint64_t)ch(o).tok * ch(o).rate) return DF_EINVAL;
+      return DF_OK;
+    }
+    case DF_DPD: {
+      if (A.in.size() != 2 || A.out.size() != 1) return DF_EINVAL;
+      const df_dpd_params& p = A.dpd;
+      const uint64_t blk = (uint64_t)p.block_len * 8;
+      const ChanH &c = ch(A.in[0]), &d = ch(A.in[1]), &o = ch(A.out[0]);
+      if (c.tok != 4 || c.rate != 1) return DF_EINVAL;
+      if (d.tok != blk || d.rate != 1 || o.tok != blk || o.rate != 1) return DF_EINVAL;
+      return DF_OK;
+    }
+    case DF_MD: {
+      if (A.in.size() != 2 || A.out.size() != 2) return DF_EINVAL;
+      const df_md_params& m = A.md;
+      const uint64_t fb = (uint64_t)m.width * m.height;
+      const ChanH &c = ch(A.in[0]), &p = ch(A.in[1]), &r = ch(A.out[0]), &n = ch(A.out[1]);
+      if (c.tok != fb || p.tok != fb || c.rate != 1 || p.rate != 1) return DF_EINVAL;
+      if (r.tok != 8 || r.rate != tiles_per_frame(m)) return DF_EINVAL;
+      if (n.tok != 4 || n.rate != 1) return DF_EINVAL;
+      return DF_OK;
+    }
+    case DF_DPD_POLY:
+    case DF_DPD_FIR:
+    case DF_DPD_ADD:
+      return DF_ENOTSUP;
+    default:
+      return DF_EINVAL;
+  }
+}
+
+df_status fail_if_device_error(df_net* net) {
+  DF_CUDA(cudaStreamSynchronize(net->stream));
+  DF_CUDA(cudaMemcpy(net->h_pin, &net->d_eng->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  int32_t st;
+  std::memcpy(&st, net->h_pin, sizeof(st));
+  return st;
+}
+
+df_status read_counters(df_net* net, int32_t ch, uint64_t* wr, uint64_t* rd) {
+  DF_CUDA(cudaMemcpyAsync(net->h_pin, net->d_ctr + 2 * ch, 2 * sizeof(uint64_t),
+                          cudaMemcpyDeviceToHost, net->stream));
+  DF_CUDA(cudaStreamSynchronize(net->stream));
+  *wr = net->h_pin[0];
+  *rd = net->h_pin[1];
+  return DF_OK;
+}
+
+// Copy `bytes` bytes between a linear buffer and a ring starting at token `t`.
+df_status ring_copy(df_net* net, const ChanDesc& c, uint64_t t, void* lin, uint64_t n_tok,
+                    bool to_ring) {
+  const uint64_t slot = t % c.cap;
+  const uint64_t first = std::min<uint64_t>(n_tok, c.cap - slot);
+  uint8_t* ring0 = c.ring + slot * c.tok;
+  uint8_t* l = static_cast<uint8_t*>(lin);
+  if (first) {
+    if (to_ring)
+      DF_CUDA(cudaMemcpyAsync(ring0, l, first * c.tok, cudaMemcpyDefault, net->stream));
+    else
+      DF_CUDA(cudaMemcpyAsync(l, ring0, first * c.tok, cudaMemcpyDefault, net->stream));
+  }
+  if (n_tok > first) {
+    const uint64_t rest = n_tok - first;
+    if (to_ring)
+      DF_CUDA(cudaMemcpyAsync(c.ring, l + first * c.tok, rest * c.tok, cudaMemcpyDefault,
+                              net->stream));
+    else
+      DF_CUDA(cudaMemcpyAsync(l + first * c.tok, c.ring, rest * c.tok, cudaMemcpyDefault,
+                              net->stream));
+  }
+  return DF_OK;
+}
+
+uint32_t default_tile(const DpdArgs& a) { return a.L >= 2048 ? 2048 : 1024; }
+
+df_status enqueue_step(df_net* net, bool no_batch) {
+  cudaStream_t s = net->stream;
+  DF_CUDA(launch_step_begin(net->d_eng, s));
+  for (const Op& op : net->program) {
+    switch (op.kind) {
+      case kOpCopy:
+        DF_CUDA(launch_copy(op.copy, net->n_sm, s));
+        break;
+      case kOpMd:
+        DF_CUDA(launch_md_step(op.md, net->n_sm, s));
+        break;
+      case kOpDpd: {
+        const ActorH& A0 = net->actors[op.dpd_first_actor];
+        uint32_t tile = A0.tile, threads = A0.threads;
+        if (!tile || !threads) {
+          const DpdArgs& a = net->dpd_host[net->dpd_index[op.dpd_first_actor]];
+          tile = default_tile(a);
+          threads = 128;
+        }
+        if (no_batch) {
+          for (int i = 0; i < op.dpd_n; ++i) {
+            DF_CUDA(launch_dpd_plan(op.dpd_dev + i, 1, s));
+            DF_CUDA(launch_dpd_body(op.dpd_dev + i, 1, tile, threads, op.max_mt, net->n_sm, s));
+          }
+        } else {
+          DF_CUDA(launch_dpd_plan(op.dpd_dev, op.dpd_n, s));
+          DF_CUDA(launch_dpd_body(op.dpd_dev, op.dpd_n, tile, threads, op.max_mt, net->n_sm, s));
+        }
+        break;
+      }
+    }
+  }
+  return DF_OK;
+}
+
+std::mutex g_scratch_mu;
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+std::map<int, Scratch> g_scratch;       // per device: backward tap-gradient partials
+
+}  // namespace
+
+extern "C" {
+
+const char* df_status_str(df_status s) {
+  switch (s) {
+    case DF_OK: return "ok";
+    case DF_EINVAL: return "invalid argument or network";
+    case DF_ENOMEM: return "out of memory";
+    case DF_EFULL: return "channel full";
+    case DF_EEMPTY: return "channel empty";
+    case DF_ESTATE: return "call not allowed in this state";
+    case DF_EDEADLOCK: return "no quiescence within the step limit";
+    case DF_ETIMEOUT: return "device-side wait timed out";
+    case DF_ECUDA: return "CUDA runtime error";
+    case DF_ENOTSUP: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+df_status df_net_create(df_net** out, int device, void* cuda_stream) {
+  if (!out) return DF_EINVAL;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return DF_EINVAL;
+  std::unique_ptr<df_net> net(new (std::nothrow) df_net());
+  if (!net) return DF_ENOMEM;
+  net->device = device;
+  DeviceGuard g(device);
+  cudaDeviceProp prop;
+  DF_CUDA(cudaGetDeviceProperties(&prop, device));
+  net->n_sm = prop.multiProcessorCount;
+  if (cuda_stream) {
+    net->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    DF_CUDA(cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking));
+    net->own_stream = true;
+  }
+  DF_CUDA(cudaMallocHost(reinterpret_cast<void**>(&net->h_pin), 64));
+  *out = net.release();
+  return DF_OK;
+}
+
+void df_net_destroy(df_net* net) {
+  if (!net) return;
+  DeviceGuard g(net->device);
+  if (net->stream) cudaStreamSynchronize(net->stream);
+  for (auto& kv : net->graphs) cudaGraphExecDestroy(kv.second);
+  if (net->arena) cudaFree(net->arena);
+  if (net->h_pin) cudaFreeHost(net->h_pin);
+  if (net->own_stream) cudaStreamDestroy(net->stream);
+  delete net;
+}
+
+df_status df_actor_add(df_net* net, int32_t kind, const void* params, size_t params_bytes,
+                       int32_t* out_id) {
+  if (!net || !out_id) return DF_EINVAL;
+  if (net->finalized) return DF_ESTATE;
+  ActorH A;
+  A.kind = kind;
+  switch (kind) {
+    case DF_SOURCE:
+    case DF_SINK:
+    case DF_COPY:
+      break;
+    case DF_DPD:
+    case DF_DPD_POLY:
+    case DF_DPD_FIR:
+    case DF_DPD_ADD: {
+      if (!params || params_bytes != sizeof(df_dpd_params)) return DF_EINVAL;
+      std::memcpy(&A.dpd, params, sizeof(df_dpd_params));
+      const df_dpd_params& p = A.dpd;
+      if (p.K < 1 || p.K > DF_MAX_BRANCHES || p.M < 1 || p.M > DF_MAX_TAPS) return DF_EINVAL;
+      if (p.block_len < 1 || !p.h) return DF_EINVAL;
+      for (int k = 0; k < p.K; ++k)
+        if (p.orders[k] < 1 || p.orders[k] % 2 == 0 || p.orders[k] > 63) return DF_EINVAL;
+      A.h.assign(p.h, p.h + 2 * (size_t)p.K * p.M);
+      A.dpd.h = nullptr;
+      break;
+    }
+    case DF_MD: {
+      if (!params || params_bytes != sizeof(df_md_params)) return DF_EINVAL;
+      std::memcpy(&A.md, params, sizeof(df_md_params));
+      const df_md_params& m = A.md;
+      if (m.width < 32 || m.width % 32 || m.height < 1 || m.tile != 16) return DF_EINVAL;
+      if (m.width > 65536 || m.height > 65536 || m.threshold < 0 || m.threshold > 255)
+        return DF_EINVAL;
+      break;
+    }
+    default:
+      return DF_EINVAL;
+  }
+  net->actors.push_back(std::move(A));
+  *out_id = (int32_t)net->actors.size() - 1;
+  return DF_OK;
+}
+
+df_status df_channel_connect(df_net* net, int32_t src_actor, int32_t src_port, int32_t dst_actor,
+                             int32_t dst_port, uint32_t token_bytes, uint32_t rate,
+                             uint32_t capacity_tokens, uint32_t initial_tokens,
+                             const void* initial_data, int32_t* out_ch) {
+  if (!net || !out_ch) return DF_EINVAL;
+  if (net->finalized) return DF_ESTATE;
+  const int na = (int)net->actors.size();
+  if (src_actor < 0 || src_actor >= na || dst_actor < 0 || dst_actor >= na) return DF_EINVAL;
+  if (src_actor == dst_actor) return DF_EINVAL;
+  if (src_port < 0 || dst_port < 0 || src_port >= 64 || dst_port >= 64) return DF_EINVAL;
+  if (token_bytes == 0 || rate == 0) return DF_EINVAL;
+  if ((uint64_t)capacity_tokens < (uint64_t)initial_tokens + rate) return DF_EINVAL;
+  ActorH& S = net->actors[src_actor];
+  ActorH& D = net->actors[dst_actor];
+  if (S.kind == DF_SINK || D.kind == DF_SOURCE) return DF_EINVAL;
+  if ((int)S.out.size() > src_port && S.out[src_port] >= 0) return DF_EINVAL;
+  if ((int)D.in.size() > dst_port && D.in[dst_port] >= 0) return DF_EINVAL;
+  if (is_dynamic(D.kind) && dst_port == 0 && (rate != 1 || initial_tokens != 0 || token_bytes != 4))
+    return DF_EINVAL;
+  ChanH c{};
+  c.src = src_actor; c.sport = src_port; c.dst = dst_actor; c.dport = dst_port;
+  c.tok = token_bytes; c.rate = rate; c.cap = capacity_tokens; c.init = initial_tokens;
+  if (initial_tokens && initial_data) {
+    const uint8_t* p = static_cast<const uint8_t*>(initial_data);
+    c.init_data.assign(p, p + (size_t)initial_tokens * token_bytes);
+  }
+  const int32_t id = (int32_t)net->chans.size();
+  net->chans.push_back(std::move(c));
+  if ((int)S.out.size() <= src_port) S.out.resize(src_port + 1, -1);
+  if ((int)D.in.size() <= dst_port) D.in.resize(dst_port + 1, -1);
+  S.out[src_port] = id;
+  D.in[dst_port] = id;
+  *out_ch = id;
+  return DF_OK;
+}
+
+df_status df_net_finalize(df_net* net) {
+  if (!net) return DF_EINVAL;
+  if (net->finalized) return DF_ESTATE;
+  for (int a = 0; a < (int)net->actors.size(); ++a) {
+    const df_status st = validate_actor(net, a);
+    if (st != DF_OK) return st;
+  }
+  DeviceGuard g(net->device);
+  // ---- arena layout ----
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    Piece p;
+    p.off = off;
+    p.bytes = bytes;
+    off += align256(bytes);
+    return p;
+  };
+  std::vector<Piece> ring(net->chans.size());
+  for (size_t c = 0; c < net->chans.size(); ++c)
+    ring[c] = take((size_t)net->chans[c].cap * net->chans[c].tok);
+  const Piece p_ctr = take(2 * sizeof(uint64_t) * std::max<size_t>(1, net->chans.size()));
+  const Piece p_eng = take(sizeof(EngineDev));
+  struct DpdPieces { Piece plan, masks, rank, act, cnt, hist, parity, h; };
+  struct MdPieces { Piece plan, counts, tot, off; };
+  std::vector<DpdPieces> dp;
+  std::vector<MdPieces> mp;
+  std::vector<Piece> cp;
+  net->dpd_index.assign(net->actors.size(), -1);
+  std::vector<int> md_index(net->actors.size(), -1), copy_index(net->actors.size(), -1);
+  for (int a = 0; a < (int)net->actors.size(); ++a) {
+    const ActorH& A = net->actors[a];
+    if (A.kind == DF_DPD) {
+      const int MT = dpd_supported_mt(A.dpd.M);
+      const uint32_t nmax = std::min({net->chans[A.in[0]].cap, net->chans[A.in[1]].cap,
+                                      net->chans[A.out[0]].cap});
+      DpdPieces q;
+      q.plan = take(sizeof(DpdPlanHdr));
+      q.masks = take(4ull * nmax);
+      q.rank = take(4ull * nmax * A.dpd.K);
+      q.act = take(4ull * nmax * A.dpd.K);
+      q.cnt = take(4ull * A.dpd.K);
+      q.hist = take(8ull * 2 * A.dpd.K * std::max(1, MT - 1));
+      q.parity = take(4);
+      q.h = take(8ull * A.dpd.K * MT);
+      net->dpd_index[a] = (int)dp.size();
+      dp.push_back(q);
+    } else if (A.kind == DF_MD) {
+      const uint32_t nmax = std::min({net->chans[A.in[0]].cap, net->chans[A.in[1]].cap,
+                                      net->chans[A.out[1]].cap});
+      MdPieces q;
+      q.plan = take(sizeof(MdPlanHdr));
+      q.counts = take(2ull * nmax * tiles_per_frame(A.md));
+      q.tot = take(4ull * nmax);
+      q.off = take(8ull * (nmax + 1));
+      md_index[a] = (int)mp.size();
+      mp.push_back(q);
+    } else if (A.kind == DF_COPY) {
+      copy_index[a] = (int)cp.size();
+      cp.push_back(take(sizeof(CopyPlan)));
+    }
+  }
+  const Piece p_dpd_args = take(sizeof(DpdArgs) * std::max<size_t>(1, dp.size()));
+  net->arena_bytes = off;
+  if (cudaMalloc(&net->arena, std::max<size_t>(off, 256)) != cudaSuccess) {
+    cudaGetLastError();
+    net->arena = nullptr;
+    return DF_ENOMEM;
+  }
+  uint8_t* base = net->arena;
+  cudaStream_t s = net->stream;
+  DF_CUDA(cudaMemsetAsync(base, 0, off, s));
+  net->d_ctr = reinterpret_cast<uint64_t*>(base + p_ctr.off);
+  net->d_eng = reinterpret_cast<EngineDev*>(base + p_eng.off);
+  // ---- channels: descriptors, initial tokens, counters ----
+  std::vector<uint64_t> ctr0(2 * net->chans.size(), 0);
+  for (size_t c = 0; c < net->chans.size(); ++c) {
+    ChanH& C = net->chans[c];
+    C.desc.ring = base + ring[c].off;
+    C.desc.cap = C.cap;
+    C.desc.tok = C.tok;
+    C.desc.rate = C.rate;
+    C.desc.id = (uint32_t)c;
+    if (C.init && !C.init_data.empty())
+      DF_CUDA(cudaMemcpyAsync(C.desc.ring, C.init_data.data(), C.init_data.size(),
+                              cudaMemcpyHostToDevice, s));
+    ctr0[2 * c] = C.init;
+  }
+  if (!ctr0.empty())
+    DF_CUDA(cudaMemcpyAsync(net->d_ctr, ctr0.data(), ctr0.size() * 8, cudaMemcpyHostToDevice, s));
+  // ---- per-actor device state and the step program ----
+  net->dpd_host.assign(dp.size(), DpdArgs{});
+  std::vector<std::vector<float2>> hpad(dp.size());
+  net->d_dpd = reinterpret_cast<DpdArgs*>(base + p_dpd_args.off);
+  for (int a = 0; a < (int)net->actors.size(); ++a) {
+    const ActorH& A = net->actors[a];
+    if (A.kind == DF_DPD) {
+      const int i = net->dpd_index[a];
+      const DpdPieces& q = dp[i];
+      DpdArgs& d = net->dpd_host[i];
+      d.ctrl = net->chans[A.in[0]].desc;
+      d.data = net->chans[A.in[1]].desc;
+      d.out = net->chans[A.out[0]].desc;
+      d.ctr = net->d_ctr;
+      d.eng = net->d_eng;
+      d.K = A.dpd.K;
+      d.M = A.dpd.M;
+      d.MT = dpd_supported_mt(A.dpd.M);
+      d.L = A.dpd.block_len;
+      d.n_max = std::min({net->chans[A.in[0]].cap, net->chans[A.in[1]].cap,
+                          net->chans[A.out[0]].cap});
+      for (int k = 0; k < A.dpd.K; ++k) d.orders[k] = A.dpd.orders[k];
+      d.plan = reinterpret_cast<DpdPlanHdr*>(base + q.plan.off);
+      d.masks = reinterpret_cast<uint32_t*>(base + q.masks.off);
+      d.rank = reinterpret_cast<uint32_t*>(base + q.rank.off);
+      d.act = reinterpret_cast<uint32_t*>(base + q.act.off);
+      d.cnt = reinterpret_cast<uint32_t*>(base + q.cnt.off);
+      d.hist = reinterpret_cast<float2*>(base + q.hist.off);
+      d.parity = reinterpret_cast<uint32_t*>(base + q.parity.off);
+      float2* hd = reinterpret_cast<float2*>(base + q.h.off);
+      d.h = hd;
+      hpad[i].assign((size_t)d.K * d.MT, make_float2(0.f, 0.f));
+      for (int k = 0; k < d.K; ++k)
+        for (int m = 0; m < d.M; ++m)
+          hpad[i][(size_t)k * d.MT + m] =
+              make_float2(A.h[2 * ((size_t)k * d.M + m)], A.h[2 * ((size_t)k * d.M + m) + 1]);
+      DF_CUDA(cudaMemcpyAsync(hd, hpad[i].data(), hpad[i].size() * sizeof(float2),
+                              cudaMemcpyHostToDevice, s));
+    }
+  }
+  if (!net->dpd_host.empty())
+    DF_CUDA(cudaMemcpyAsync(net->d_dpd, net->dpd_host.data(), sizeof(DpdArgs) * net->dpd_host.size(),
+                            cudaMemcpyHostToDevice, s));
+  net->program.clear();
+  std::vector<int> group;                 // current predistorter group (actor ids)
+  auto flush_group = [&]() {
+    if (group.empty()) return;
+    Op op{};
+    op.kind = kOpDpd;
+    op.dpd_dev = net->d_dpd + net->dpd_index[group[0]];
+    op.dpd_n = (int)group.size();
+    op.dpd_first_actor = group[0];
+    for (int a : group) op.max_mt = std::max(op.max_mt, net->dpd_host[net->dpd_index[a]].MT);
+    net->program.push_back(op);
+    group.clear();
+  };
+  auto linked = [&](int a, int b) {
+    for (const ChanH& c : net->chans)
+      if ((c.src == a && c.dst == b) || (c.src == b && c.dst == a)) return true;
+    return false;
+  };
+  for (int a = 0; a < (int)net->actors.size(); ++a) {
+    const ActorH& A = net->actors[a];
+    if (A.kind != DF_DPD) flush_group();
+    if (A.kind == DF_DPD) {
+      bool ok = (int)group.size() < 1024;
+      for (int b : group) ok = ok && !linked(a, b);
+      if (!ok) flush_group();
+      group.push_back(a);
+    } else if (A.kind == DF_COPY) {
+      Op op{};
+      op.kind = kOpCopy;
+      CopyArgs& c = op.copy;
+      c.in = net->chans[A.in[0]].desc;
+      c.n_out = (int)A.out.size();
+      int unit = 16;
+      auto fit = [&](uint64_t tok) {
+        while (unit > 1 && tok % unit) unit = unit == 16 ? 4 : 1;
+      };
+      fit(c.in.tok);
+      for (int p = 0; p < c.n_out; ++p) {
+        c.out[p] = net->chans[A.out[p]].desc;
+        fit(c.out[p].tok);
+      }
+      c.unit = unit;
+      c.ctr = net->d_ctr;
+      c.eng = net->d_eng;
+      c.plan = reinterpret_cast<CopyPlan*>(base + cp[copy_index[a]].off);
+      net->program.push_back(op);
+    } else if (A.kind == DF_MD) {
+      Op op{};
+      op.kind = kOpMd;
+      MdArgs& m = op.md;
+      const MdPieces& q = mp[md_index[a]];
+      const ChanH &cur = net->chans[A.in[0]], &prev = net->chans[A.in[1]];
+      m.cur = cur.desc;
+      m.prev = prev.desc;
+      m.rec = net->chans[A.out[0]].desc;
+      m.cnt = net->chans[A.out[1]].desc;
+      m.ctr = net->d_ctr;
+      m.eng = net->d_eng;
+      m.W = A.md.width;
+      m.H = A.md.height;
+      m.thr = A.md.threshold;
+      m.words = m.W / 32;
+      m.tiles_x = (m.W + 15) / 16;
+      m.tiles_y = (m.H + 15) / 16;
+      m.n_tiles = m.tiles_x * m.tiles_y;
+      m.strips = (m.H + 15) / 16;
+      // The previous-frame channel carries the current-frame stream delayed by
+      // exactly one token when both come from the same source broadcast, the
+      // current channel has no initial token and the previous channel one.
+      m.dedup = (cur.src == prev.src && net->actors[cur.src].kind == DF_SOURCE &&
+                 cur.init == 0 && prev.init == 1) ? 1 : 0;
+      m.n_max = std::min({cur.cap, prev.cap, net->chans[A.out[1]].cap});
+      m.plan = reinterpret_cast<MdPlanHdr*>(base + q.plan.off);
+      m.counts = reinterpret_cast<uint16_t*>(base + q.counts.off);
+      m.frame_tot = reinterpret_cast<uint32_t*>(base + q.tot.off);
+      m.frame_off = reinterpret_cast<uint64_t*>(base + q.off.off);
+      m.wait_limit_ns = net->wait_limit_ns;
+      if (md_smem_bytes(m.W) > 227 * 1024) return DF_ENOTSUP;
+      net->program.push_back(op);
+    }
+  }
+  flush_group();
+  DF_CUDA(cudaStreamSynchronize(s));
+  net->finalized = true;
+  return DF_OK;
+}
+
+df_status df_push(df_net* net, int32_t src_actor, const void* src, uint64_t n_tokens,
+                  uint64_t* n_pushed) {
+  if (!net || (!src && n_tokens)) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  if (src_actor < 0 || src_actor >= (int)net->actors.size()) return DF_EINVAL;
+  const ActorH& A = net->actors[src_actor];
+  if (A.kind != DF_SOURCE) return DF_EINVAL;
+  DeviceGuard g(net->device);
+  std::vector<uint64_t> wr(A.out.size());
+  for (size_t p = 0; p < A.out.size(); ++p) {
+    uint64_t w, r;
+    const df_status st = read_counters(net, A.out[p], &w, &r);
+    if (st != DF_OK) return st;
+    if (net->chans[A.out[p]].cap - (w - r) < n_tokens) return DF_EFULL;
+    wr[p] = w;
+  }
+  if (n_tokens) {
+    for (size_t p = 0; p < A.out.size(); ++p) {
+      const ChanDesc& c = net->chans[A.out[p]].desc;
+      if (p > 0 && c.tok == net->chans[A.out[0]].desc.tok) {
+        // further broadcast copies come from the first channel (device to device)
+        const ChanDesc& c0 = net->chans[A.out[0]].desc;
+        for (uint64_t done = 0; done < n_tokens;) {
+          const uint64_t s0 = (wr[0] + done) % c0.cap, s1 = (wr[p] + done) % c.cap;
+          const uint64_t run = std::min({n_tokens - done, c0.cap - s0, c.cap - s1});
+          DF_CUDA(cudaMemcpyAsync(c.ring + s1 * c.tok, c0.ring + s0 * c0.tok, run * c.tok,
+                                  cudaMemcpyDeviceToDevice, net->stream));
+          done += run;
+        }
+      } else {
+        const df_status st = ring_copy(net, c, wr[p], const_cast<void*>(src), n_tokens, true);
+        if (st != DF_OK) return st;
+      }
+      DF_CUDA(launch_set_u64(net->d_ctr + 2 * A.out[p], wr[p] + n_tokens, net->stream));
+    }
+    DF_CUDA(cudaStreamSynchronize(net->stream));
+  }
+  if (n_pushed) *n_pushed = n_tokens;
+  return DF_OK;
+}
+
+df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_firings) {
+  if (!net) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  if (flags & DF_RUN_PERSISTENT) return DF_ENOTSUP;
+  DeviceGuard g(net->device);
+  const bool no_batch = flags & DF_RUN_NO_BATCH;
+  uint64_t before = 0;
+  if (!(flags & DF_RUN_ASYNC)) {
+    DF_CUDA(cudaStreamSynchronize(net->stream));
+    DF_CUDA(cudaMemcpy(&before, &net->d_eng->fired_total, 8, cudaMemcpyDeviceToHost));
+  } else if (n_steps < 0) {
+    return DF_EINVAL;
+  }
+  if (n_steps >= 0) {
+    if (flags & DF_RUN_GRAPH) {
+      auto key = std::make_pair(n_steps, flags & DF_RUN_NO_BATCH);
+      auto it = net->graphs.find(key);
+      if (it == net->graphs.end()) {
+        cudaGraph_t graph;
+        DF_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
+        df_status st = DF_OK;
+        for (int64_t i = 0; i < n_steps && st == DF_OK; ++i) st = enqueue_step(net, no_batch);
+        const cudaError_t ce = cudaStreamEndCapture(net->stream, &graph);
+        if (st != DF_OK) return st;
+        DF_CUDA(ce);
+        cudaGraphExec_t exec;
+        DF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        cudaGraphDestroy(graph);
+        it = net->graphs.emplace(key, exec).first;
+      }
+      DF_CUDA(cudaGraphLaunch(it->second, net->stream));
+    } else {
+      for (int64_t i = 0; i < n_steps; ++i) {
+        const df_status st = enqueue_step(net, no_batch);
+        if (st != DF_OK) return st;
+      }
+    }
+  } else {
+    const int64_t kMaxSteps = 1 << 20;
+    int64_t i = 0;
+    for (; i < kMaxSteps; ++i) {
+      const df_status st = enqueue_step(net, no_batch);
+      if (st != DF_OK) return st;
+      DF_CUDA(cudaMemcpyAsync(net->h_pin, &net->d_eng->fired_step, 8, cudaMemcpyDeviceToHost,
+                              net->stream));
+      DF_CUDA(cudaStreamSynchronize(net->stream));
+      if (net->h_pin[0] == 0) break;
+    }
+    if (i == kMaxSteps) return DF_EDEADLOCK;
+  }
+  if (flags & DF_RUN_ASYNC) return DF_OK;
+  const df_status st = fail_if_device_error(net);
+  if (st != DF_OK) return st;
+  if (n_firings) {
+    uint64_t after = 0;
+    DF_CUDA(cudaMemcpy(&after, &net->d_eng->fired_total, 8, cudaMemcpyDeviceToHost));
+    *n_firings = after - before;
+  }
+  return DF_OK;
+}
+
+df_status df_run(df_net* net, int64_t n_steps, uint64_t* n_firings) {
+  return df_run_ex(net, n_steps, 0, n_firings);
+}
+
+df_status df_sync(df_net* net, uint64_t* total_firings) {
+  if (!net) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  DeviceGuard g(net->device);
+  const df_status st = fail_if_device_error(net);
+  if (st != DF_OK) return st;
+  if (total_firings) DF_CUDA(cudaMemcpy(total_firings, &net->d_eng->fired_total, 8,
+                                        cudaMemcpyDeviceToHost));
+  return DF_OK;
+}
+
+df_status df_pop(df_net* net, int32_t sink_actor, void* dst, uint64_t max_tokens,
+                 uint64_t* n_popped) {
+  if (!net || (!dst && max_tokens)) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  if (sink_actor < 0 || sink_actor >= (int)net->actors.size()) return DF_EINVAL;
+  const ActorH& A = net->actors[sink_actor];
+  if (A.kind != DF_SINK) return DF_EINVAL;
+  DeviceGuard g(net->device);
+  const int32_t ch = A.in[0];
+  uint64_t w, r;
+  df_status st = read_counters(net, ch, &w, &r);
+  if (st != DF_OK) return st;
+  const uint64_t n = std::min(max_tokens, w - r);
+  if (n) {
+    st = ring_copy(net, net->chans[ch].desc, r, dst, n, false);
+    if (st != DF_OK) return st;
+    DF_CUDA(launch_set_u64(net->d_ctr + 2 * ch + 1, r + n, net->stream));
+    DF_CUDA(cudaStreamSynchronize(net->stream));
+  }
+  if (n_popped) *n_popped = n;
+  return DF_OK;
+}
+
+df_status df_channel_counters(df_net* net, int32_t ch, uint64_t* produced, uint64_t* consumed,
+                              uint64_t* occupancy) {
+  if (!net || ch < 0 || ch >= (int)net->chans.size()) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  DeviceGuard g(net->device);
+  uint64_t w, r;
+  const df_status st = read_counters(net, ch, &w, &r);
+  if (st != DF_OK) return st;
+  if (produced) *produced = w - net->chans[ch].init;
+  if (consumed) *consumed = r;
+  if (occupancy) *occupancy = w - r;
+  return DF_OK;
+}
+
+df_status df_dpd_set_tile(df_net* net, int32_t actor, uint32_t tile, uint32_t threads) {
+  if (!net || actor < 0 || actor >= (int)net->actors.size()) return DF_EINVAL;
+  if (net->actors[actor].kind != DF_DPD) return DF_EINVAL;
+  if (tile || threads) {
+    if (threads != 64 && threads != 128 && threads != 256) return DF_EINVAL;
+    const uint32_t R = tile / threads;
+    if (tile != R * threads || (R != 8 && R != 16)) return DF_EINVAL;
+  }
+  net->actors[actor].tile = tile;
+  net->actors[actor].threads = threads;
+  for (auto& kv : net->graphs) cudaGraphExecDestroy(kv.second);
+  net->graphs.clear();
+  return DF_OK;
+}
+
+df_status df_autotune(df_net* net, uint64_t* n_firings) {
+  (void)net;
+  (void)n_firings;
+  return DF_ENOTSUP;
+}
+
+df_status df_dpd_forward(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                         const int32_t* orders, void* y, void* cuda_stream) {
+  if ((!x || !y) && n) return DF_EINVAL;
+  if (!h || !orders || K < 1 || K > DF_MAX_BRANCHES || M < 1 || M > DF_MAX_TAPS) return DF_EINVAL;
+  for (int k = 0; k < K; ++k)
+    if (orders[k] < 1 || orders[k] % 2 == 0 || orders[k] > 63) return DF_EINVAL;
+  return cuda_status(dpd_forward_stateless(static_cast<const float2*>(x), n,
+                                           static_cast<const float2*>(h), K, M, orders,
+                                           static_cast<float2*>(y),
+                                           static_cast<cudaStream_t>(cuda_stream)));
+}
+
+df_status df_dpd_backward(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                          const int32_t* orders, const void* grad_y, void* grad_x, void* grad_h,
+                          void* cuda_stream) {
+  if (((!x || !grad_y) && n) || !grad_h) return DF_EINVAL;
+  if (!h || !orders || K < 1 || K > DF_MAX_BRANCHES || M < 1 || M > DF_MAX_TAPS) return DF_EINVAL;
+  for (int k = 0; k < K; ++k)
+    if (orders[k] < 1 || orders[k] % 2 == 0 || orders[k] > 63) return DF_EINVAL;
+  int dev = 0;
+  DF_CUDA(cudaGetDevice(&dev));
+  const size_t need = std::max<size_t>(1, dpd_backward_scratch_elems(n, K, M)) * sizeof(float2);
+  void* scratch = nullptr;
+  size_t have = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    Scratch& sc = g_scratch[dev];
+    if (sc.bytes < need) {
+      if (sc.ptr) {
+        cudaDeviceSynchronize();
+        cudaFree(sc.ptr);
+        sc.ptr = nullptr;
+        sc.bytes = 0;
+      }
+      if (cudaMalloc(&sc.ptr, need) != cudaSuccess) {
+        cudaGetLastError();
+        return DF_ENOMEM;
+      }
+      sc.bytes = need;
+    }
+    scratch = sc.ptr;
+    have = sc.bytes;
+  }
+  return cuda_status(dpd_backward_stateless(
+      static_cast<const float2*>(x), n, static_cast<const float2*>(h), K, M, orders,
+      static_cast<const float2*>(grad_y), static_cast<float2*>(grad_x),
+      static_cast<float2*>(grad_h), static_cast<float2*>(scratch), have / sizeof(float2),
+      static_cast<cudaStream_t>(cuda_stream)));
+}
+
+}  // extern "C"

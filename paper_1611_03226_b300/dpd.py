@@ -1,0 +1,79 @@
+"""Differentiable predistorter on torch CUDA tensors (marshalling only).
+
+``dpd(x, h, orders)`` evaluates y[t] = sum_k sum_m h[k,m] z_k[t-m] with
+z_k = |x|^(orders[k]-1) x (every branch active, zero history) through
+df_dpd_forward; its gradient goes through the hand-written adjoint
+df_dpd_backward, which recomputes z_k from x instead of storing it.
+Gradients follow PyTorch's convention for complex tensors
+(dL/dRe + i dL/dIm).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+
+def _orders(orders):
+    arr = (C.c_int32 * len(orders))(*[int(o) for o in orders])
+    return arr
+
+
+def _check_inputs(x, h):
+    if x.dtype != torch.complex64 or h.dtype != torch.complex64:
+        raise TypeError("x and h must be complex64")
+    if not (x.is_cuda and h.is_cuda):
+        raise ValueError("x and h must be CUDA tensors")
+    if x.dim() != 1 or h.dim() != 2:
+        raise ValueError("x is (n,), h is (K, M)")
+
+
+def dpd_forward(x: torch.Tensor, h: torch.Tensor, orders) -> torch.Tensor:
+    _check_inputs(x, h)
+    x = x.contiguous()
+    h = h.contiguous()
+    K, M = h.shape
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    L.check(L.lib.df_dpd_forward(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(h.data_ptr()),
+                                 K, M, _orders(orders), C.c_void_p(y.data_ptr()),
+                                 C.c_void_p(stream)), "df_dpd_forward")
+    return y
+
+
+def dpd_backward(x: torch.Tensor, h: torch.Tensor, orders, grad_y: torch.Tensor,
+                 need_x: bool = True):
+    _check_inputs(x, h)
+    x = x.contiguous()
+    h = h.contiguous()
+    grad_y = grad_y.contiguous().to(torch.complex64)
+    K, M = h.shape
+    gx = torch.empty_like(x) if need_x else None
+    gh = torch.empty_like(h)
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    L.check(L.lib.df_dpd_backward(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(h.data_ptr()),
+                                  K, M, _orders(orders), C.c_void_p(grad_y.data_ptr()),
+                                  C.c_void_p(gx.data_ptr()) if need_x else None,
+                                  C.c_void_p(gh.data_ptr()), C.c_void_p(stream)),
+            "df_dpd_backward")
+    return gx, gh
+
+
+class DPDFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, h, orders):
+        ctx.save_for_backward(x, h)
+        ctx.orders = tuple(orders)
+        return dpd_forward(x, h, orders)
+
+    @staticmethod
+    def backward(ctx, grad_y):
+        x, h = ctx.saved_tensors
+        gx, gh = dpd_backward(x, h, ctx.orders, grad_y, need_x=ctx.needs_input_grad[0])
+        return gx, gh, None
+
+
+def dpd(x, h, orders):
+    return DPDFunction.apply(x, h, tuple(orders))

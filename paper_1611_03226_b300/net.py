@@ -1,0 +1,156 @@
+"""Python face of the C ABI: build a network, push, run, pop (marshalling only).
+
+Host buffers are numpy arrays; device buffers are torch CUDA tensors.  Every
+call goes straight to libdfgpu.so; nothing here computes on the data.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _ptr(buf):
+    """(address, nbytes) of a C-contiguous numpy array or torch tensor."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be C-contiguous")
+        return buf.ctypes.data, buf.nbytes
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr(), buf.numel() * buf.element_size()
+    raise TypeError(f"unsupported buffer {type(buf)}")
+
+
+class Net:
+    def __init__(self, device: int = 0, stream=None):
+        h = C.c_void_p()
+        s = C.c_void_p(stream) if stream is not None else None
+        L.check(L.lib.df_net_create(C.byref(h), device, s), "df_net_create")
+        self.h = h
+        self.chan_tok = {}
+        self.actor_out = {}      # actor -> {port: ch}
+        self.actor_in = {}
+
+    def close(self):
+        if self.h:
+            L.lib.df_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- construction ----
+    def _add(self, kind, params=None):
+        aid = C.c_int32()
+        if params is None:
+            L.check(L.lib.df_actor_add(self.h, kind, None, 0, C.byref(aid)), "df_actor_add")
+        else:
+            L.check(L.lib.df_actor_add(self.h, kind, C.byref(params), C.sizeof(params),
+                                       C.byref(aid)), "df_actor_add")
+        return aid.value
+
+    def add_source(self):
+        return self._add(L.DF_SOURCE)
+
+    def add_sink(self):
+        return self._add(L.DF_SINK)
+
+    def add_copy(self):
+        return self._add(L.DF_COPY)
+
+    def add_dpd(self, h, orders, block_len, kind=L.DF_DPD, branch=0):
+        h = np.ascontiguousarray(h, np.complex64)
+        K, M = h.shape
+        p = L.DpdParams()
+        p.K, p.M, p.block_len, p.branch = K, M, block_len, branch
+        for k, o in enumerate(orders):
+            p.orders[k] = int(o)
+        hf = h.view(np.float32).reshape(-1)
+        p.h = hf.ctypes.data_as(C.POINTER(C.c_float))
+        aid = self._add(kind, p)
+        del hf
+        return aid
+
+    def add_md(self, width, height, threshold=25, tile=16):
+        p = L.MdParams(width, height, threshold, tile)
+        return self._add(L.DF_MD, p)
+
+    def connect(self, src, src_port, dst, dst_port, token_bytes, rate, capacity, initial=0,
+                initial_data=None):
+        ch = C.c_int32()
+        ptr = None
+        if initial_data is not None:
+            initial_data = np.ascontiguousarray(initial_data)
+            if initial_data.nbytes != initial * token_bytes:
+                raise ValueError("initial_data size mismatch")
+            ptr = C.c_void_p(initial_data.ctypes.data)
+        L.check(L.lib.df_channel_connect(self.h, src, src_port, dst, dst_port, token_bytes, rate,
+                                         capacity, initial, ptr, C.byref(ch)),
+                "df_channel_connect")
+        self.chan_tok[ch.value] = token_bytes
+        self.actor_out.setdefault(src, {})[src_port] = ch.value
+        self.actor_in.setdefault(dst, {})[dst_port] = ch.value
+        return ch.value
+
+    def finalize(self):
+        L.check(L.lib.df_net_finalize(self.h), "df_net_finalize")
+
+    # ---- execution ----
+    def push(self, src, buf, n_tokens=None):
+        addr, nbytes = _ptr(buf)
+        tok = self.chan_tok[self.actor_out[src][0]]
+        if n_tokens is None:
+            if nbytes % tok:
+                raise ValueError("buffer is not a whole number of tokens")
+            n_tokens = nbytes // tok
+        elif n_tokens * tok > nbytes:
+            raise ValueError("buffer too small")
+        n = C.c_uint64()
+        L.check(L.lib.df_push(self.h, src, C.c_void_p(addr), n_tokens, C.byref(n)), "df_push")
+        return n.value
+
+    def run(self, n_steps=-1, flags=0):
+        n = C.c_uint64()
+        L.check(L.lib.df_run_ex(self.h, n_steps, flags, C.byref(n)), "df_run")
+        return n.value
+
+    def run_async(self, n_steps, flags=0):
+        L.check(L.lib.df_run_ex(self.h, n_steps, flags | L.DF_RUN_ASYNC, None), "df_run")
+
+    def sync(self):
+        n = C.c_uint64()
+        L.check(L.lib.df_sync(self.h, C.byref(n)), "df_sync")
+        return n.value
+
+    def pop(self, sink, max_tokens=None, out=None, dtype=np.uint8):
+        ch = self.actor_in[sink][0]
+        tok = self.chan_tok[ch]
+        if out is None:
+            produced, consumed, occ = self.counters(ch)
+            n_max = occ if max_tokens is None else min(max_tokens, occ)
+            out = np.empty(n_max * tok, np.uint8)
+        addr, nbytes = _ptr(out)
+        cap = nbytes // tok
+        n = C.c_uint64()
+        L.check(L.lib.df_pop(self.h, sink, C.c_void_p(addr),
+                             cap if max_tokens is None else min(cap, max_tokens), C.byref(n)),
+                "df_pop")
+        if isinstance(out, np.ndarray):
+            return out[: n.value * tok].view(dtype)
+        return out, n.value
+
+    def counters(self, ch):
+        p, c, o = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        L.check(L.lib.df_channel_counters(self.h, ch, C.byref(p), C.byref(c), C.byref(o)),
+                "df_channel_counters")
+        return p.value, c.value, o.value
+
+    def set_tile(self, actor, tile, threads):
+        L.check(L.lib.df_dpd_set_tile(self.h, actor, tile, threads), "df_dpd_set_tile")

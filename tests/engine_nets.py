@@ -1,0 +1,46 @@
+"""Builders of the benchmark networks through the engine's C ABI (test helper).
+
+They mirror ``oracle/nets.py`` port for port, so the same pushes and runs can
+be replayed on both sides."""
+import numpy as np
+
+CPLX = 8
+
+
+def dpd_fused(Net, h, orders, block_len, delay, capacity, out_capacity=None):
+    net = Net()
+    ids = {}
+    ids["ctrl"] = net.add_source()
+    ids["data"] = net.add_source()
+    ids["dpd"] = net.add_dpd(h, orders, block_len)
+    ids["sink"] = net.add_sink()
+    blk = block_len * CPLX
+    ids["ch_ctrl"] = net.connect(ids["ctrl"], 0, ids["dpd"], 0, 4, 1, capacity)
+    ids["ch_data"] = net.connect(ids["data"], 0, ids["dpd"], 1, blk, 1, capacity, delay)
+    ids["ch_out"] = net.connect(ids["dpd"], 0, ids["sink"], 0, blk, 1,
+                                capacity if out_capacity is None else out_capacity)
+    net.finalize()
+    return net, ids
+
+
+def motion_fused(Net, height, width, capacity, rec_capacity=None, t=25, prev_init=None,
+                 separate_prev_source=False):
+    n_tiles = (-(-height // 16)) * (-(-width // 16))
+    net = Net()
+    ids = {}
+    ids["src"] = net.add_source()
+    if separate_prev_source:
+        ids["src_prev"] = net.add_source()
+    ids["md"] = net.add_md(width, height, t)
+    ids["rec"] = net.add_sink()
+    ids["cnt"] = net.add_sink()
+    fb = height * width
+    ids["ch_cur"] = net.connect(ids["src"], 0, ids["md"], 0, fb, 1, capacity)
+    psrc, pport = (ids["src_prev"], 0) if separate_prev_source else (ids["src"], 1)
+    ids["ch_prev"] = net.connect(psrc, pport, ids["md"], 1, fb, 1, capacity, 1,
+                                 None if prev_init is None else np.ascontiguousarray(prev_init))
+    rc = capacity * n_tiles if rec_capacity is None else rec_capacity
+    ids["ch_rec"] = net.connect(ids["md"], 0, ids["rec"], 0, 8, n_tiles, rc)
+    ids["ch_cnt"] = net.connect(ids["md"], 1, ids["cnt"], 0, 4, 1, capacity)
+    net.finalize()
+    return net, ids

@@ -1,0 +1,184 @@
+"""Parity of the fused predistorter actor (CUDA, FP32) with the float64 oracle.
+
+Both sides receive the same pushes and runs; because a step of the engine and
+a sweep of the oracle fire the same firings, channel counters agree after
+every step, and each output block matches within 1e-5 relative L2."""
+import numpy as np
+import pytest
+
+import engine_nets as EN
+import synth
+from oracle import dpd as D
+from oracle import nets as ON
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def Net():
+    from paper_1611_03226_b300 import Net
+    return Net
+
+
+def stream_both(Net, h, orders, L, d, cap, masks, blocks, chunk, rng=None, tile=None):
+    onet, oi = ON.dpd_fused(h, orders, L, d, cap)
+    enet, ei = EN.dpd_fused(Net, h, orders, L, d, cap)
+    if tile:
+        enet.set_tile(ei["dpd"], *tile)
+    yo, ye = [], []
+    n, i, idle = len(masks), 0, 0
+    while True:
+        free = min(onet.channels[oi["ch_ctrl"]].free, onet.channels[oi["ch_data"]].free)
+        k = min(chunk, n - i, free)
+        if k > 0:
+            onet.push(oi["ctrl"], ON.as_tokens_ctrl(masks[i:i + k]))
+            onet.push(oi["data"], ON.as_tokens_blocks(blocks[i:i + k]))
+            enet.push(ei["ctrl"], np.ascontiguousarray(masks[i:i + k], np.uint32))
+            enet.push(ei["data"], np.ascontiguousarray(blocks[i:i + k], np.complex64))
+            i += k
+        steps = 1 if rng is None else int(rng.integers(1, 3))
+        fo = onet.run(steps)
+        fe = enet.run(steps)
+        assert fo == fe
+        for key in ("ch_ctrl", "ch_data", "ch_out"):
+            assert onet.counters(oi[key]) == enet.counters(ei[key])
+        m = int(rng.integers(0, 3)) if rng is not None else None
+        yo += onet.pop(oi["sink"], m)
+        ye.append(enet.pop(ei["sink"], m, dtype=np.complex64))
+        if i >= n and fo == 0:
+            idle += 1
+            if idle > 2 and not onet.channels[oi["ch_out"]].occupancy:
+                break
+    enet.close()
+    return np.array(yo).reshape(-1, L), np.concatenate(ye).reshape(-1, L)
+
+
+def check_blocks(yo, ye, tol=TOL):
+    assert yo.shape == ye.shape
+    errs = [D.rel_l2(ye[b], yo[b]) for b in range(len(yo))]
+    assert max(errs) <= tol, (max(errs), int(np.argmax(errs)))
+    return max(errs)
+
+
+def test_identity_predistorter_exact(Net):
+    rng = np.random.default_rng(1)
+    L, n = 600, 11
+    x = (rng.normal(0, .3, (n, L)) + 1j * rng.normal(0, .3, (n, L))).astype(np.complex64)
+    h = np.zeros((4, 10), np.complex64)
+    h[0, 0] = 1
+    masks = (rng.integers(0, 16, n) | 1).astype(np.uint32)
+    yo, ye = stream_both(Net, h, (1, 3, 5, 7), L, 2, 4, masks, x, 2)
+    want = np.concatenate([np.zeros((2, L), np.complex64), x[:-2]])
+    np.testing.assert_array_equal(ye, want)
+    np.testing.assert_array_equal(yo, want)
+
+
+def test_tiny_workload_full_size(Net):
+    """64 blocks x 4096, K<=4, M=10, prefix masks, capacity 8, one delay block."""
+    w = synth.dpd_tiny()
+    yo, ye = stream_both(Net, w.h, w.orders, w.block_len, w.delay, w.capacity, w.masks,
+                         w.blocks(), 3)
+    assert len(ye) == 64
+    check_blocks(yo, ye)
+
+
+@pytest.mark.parametrize("L,M,d,K,cap,tile", [
+    (64, 10, 1, 4, 5, None),          # short blocks, one tile
+    (3, 10, 2, 8, 6, None),           # block shorter than the FIR history
+    (1, 4, 0, 3, 4, None),            # single-sample blocks
+    (5000, 16, 2, 8, 7, (1024, 128)),  # ragged last tile, several tiles per block
+    (2047, 32, 1, 5, 4, (2048, 256)),  # two 16-tap chunks
+    (777, 13, 3, 16, 9, (1024, 64)),  # 16 branches, odd tap count
+    (4096, 9, 1, 6, 5, (2048, 128)),  # R = 16 variant
+])
+def test_random_masks_parity(Net, L, M, d, K, cap, tile):
+    rng = np.random.default_rng(L + 7 * M + K)
+    n = 14
+    orders = tuple(range(1, 2 * K, 2))
+    x = (rng.normal(0, .3, (n, L)) + 1j * rng.normal(0, .3, (n, L))).astype(np.complex64)
+    h = (rng.normal(0, .1, (K, M)) + 1j * rng.normal(0, .1, (K, M))).astype(np.complex64)
+    masks = rng.integers(0, 1 << K, n).astype(np.uint32)
+    masks[3] = 0                        # an empty mask gives a zero block
+    yo, ye = stream_both(Net, h, orders, L, d, cap, masks, x, 3, rng=rng, tile=tile)
+    assert len(ye) == n
+    check_blocks(yo, ye)
+
+
+def test_mask_bits_beyond_K_ignored(Net):
+    rng = np.random.default_rng(5)
+    L, n = 100, 6
+    x = (rng.normal(0, .3, (n, L)) + 1j * rng.normal(0, .3, (n, L))).astype(np.complex64)
+    h = (rng.normal(0, .1, (2, 5)) + 1j * rng.normal(0, .1, (2, 5))).astype(np.complex64)
+    masks = np.array([0xFFFFFFFF, 4, 1, 2, 0xF0, 3], np.uint32)
+    yo, ye = stream_both(Net, h, (1, 3), L, 0, 8, masks, x, 6)
+    check_blocks(yo, ye)
+
+
+def sampled_block_oracle(w, i, x_of):
+    """Oracle output of block i of a long stream computed on its own: branch k's
+    history is the tail of the last earlier block with k active (zeros if none).
+    The delay blocks are zero and precede block 0."""
+    d = w.delay
+    L = w.block_len
+    M = w.n_taps
+    xi = np.zeros(L, np.complex64) if i < d else x_of(i - d)
+    y = np.zeros(L, np.complex128)
+    for k in range(w.n_branches):
+        if not (int(w.masks[i]) >> k) & 1:
+            continue
+        prev = [j for j in range(i) if (int(w.masks[j]) >> k) & 1]
+        if prev and prev[-1] >= d:
+            tail = x_of(prev[-1] - d)[L - (M - 1):]
+        else:
+            tail = np.zeros(M - 1, np.complex64)
+        hist = D.psi(tail, w.orders[k])
+        yk, _ = D.fir(w.h[k], hist, D.psi(xi, w.orders[k]))
+        y += yk
+    return y
+
+
+@pytest.mark.slow
+def test_large_workload_full_size_sampled(Net):
+    """512 blocks x 2^20, K<=8 (orders 1..15), M=16, d=2, pushed whole, one run:
+    the bench launch configuration; sampled blocks against the oracle."""
+    import torch
+    w = synth.dpd_large()
+    L, n = w.block_len, w.n_blocks
+    enet, ei = EN.dpd_fused(Net, w.h, w.orders, L, w.delay, n + w.delay)
+    enet.push(ei["ctrl"], np.ascontiguousarray(w.masks))
+    chunk = 32
+    for b in range(0, n, chunk):
+        enet.push(ei["data"], np.ascontiguousarray(w.blocks(b, min(n, b + chunk))))
+    assert enet.run(-1) == n
+    out = torch.empty((n, L), dtype=torch.complex64, device="cuda")
+    _, got = enet.pop(ei["sink"], out=out)
+    assert got == n
+    for i in (0, 1, 2, 3, 100, 257, 510, 511):
+        ref = sampled_block_oracle(w, i, w.block)
+        assert D.rel_l2(out[i].cpu().numpy(), ref) <= TOL
+    for key in ("ch_ctrl", "ch_data", "ch_out"):
+        p, c, o = enet.counters(ei[key])
+        assert p + (w.delay if key == "ch_data" else 0) == c + o
+    enet.close()
+
+
+def test_stateless_forward_backward(Net):
+    import torch
+    from paper_1611_03226_b300 import dpd as G
+    rng = np.random.default_rng(9)
+    for n, K, M in ((20000, 4, 10), (3001, 3, 32), (1, 2, 5)):
+        orders = tuple(range(1, 2 * K, 2))
+        x = (rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n)).astype(np.complex64)
+        h = (rng.normal(0, .1, (K, M)) + 1j * rng.normal(0, .1, (K, M))).astype(np.complex64)
+        g = (rng.normal(size=n) + 1j * rng.normal(size=n)).astype(np.complex64)
+        xt, ht, gt = (torch.from_numpy(a).cuda() for a in (x, h, g))
+        y = G.dpd_forward(xt, ht, orders).cpu().numpy()
+        assert D.rel_l2(y, D.dpd_stream(x, h, orders)) <= TOL
+        gx, gh = G.dpd_backward(xt, ht, orders, gt)
+        rx, rh = D.dpd_stream_backward(x, h, orders, g)
+        assert D.rel_l2(gx.cpu().numpy(), rx) <= 1e-3
+        assert D.rel_l2(gh.cpu().numpy(), rh) <= 1e-3
+        gx2, gh2 = G.dpd_backward(xt, ht, orders, gt)       # deterministic reduction
+        assert torch.equal(gh, gh2) and torch.equal(gx, gx2)
