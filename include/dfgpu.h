@@ -185,8 +185,25 @@ df_status df_dpd_set_tile(df_net *net, int32_t actor, uint32_t tile, uint32_t th
  * for every DF_DPD actor / group.  Runs one step; returns its firings. */
 df_status df_autotune(df_net *net, uint64_t *n_firings);
 
+/* Kernel timing.  While enabled, every non-graph step records CUDA events on
+ * the network's stream around the kernels named below; df_profile_get waits
+ * for the stream and returns their summed device time (ms) and launch count
+ * since the last enable.  Graph replays (DF_RUN_GRAPH) are not timed. */
+enum {
+    DF_PROF_STEP = 0,        /* one whole step (every launch of the step) */
+    DF_PROF_DPD_BODY = 1,    /* predistorter body launches */
+    DF_PROF_MD_MAIN = 2,     /* motion-detector streaming kernel */
+    DF_PROF_COPY_BODY = 3    /* copy-actor body launches */
+};
+df_status df_profile_enable(df_net *net, int32_t on);
+df_status df_profile_get(df_net *net, int32_t what, double *total_ms, uint64_t *launches);
+
 /* Text for a status code (static storage). */
 const char *df_status_str(df_status s);
+
+/* The failing CUDA call and its error string behind the calling thread's most
+ * recent DF_ECUDA (empty if none); valid until the thread's next failure. */
+const char *df_last_error(void);
 
 /* ---------------------------------------------------------------------------
  * Stateless predistorter operators (device pointers, caller's stream).

@@ -16,6 +16,7 @@ DF_EDEADLOCK, DF_ETIMEOUT, DF_ECUDA, DF_ENOTSUP = -6, -7, -8, -9
 DF_SOURCE, DF_SINK, DF_COPY, DF_DPD, DF_DPD_POLY, DF_DPD_FIR, DF_DPD_ADD, DF_MD = range(1, 9)
 DF_RUN_ASYNC, DF_RUN_GRAPH, DF_RUN_PERSISTENT, DF_RUN_NO_BATCH = 1, 2, 4, 8
 DF_MAX_BRANCHES, DF_MAX_TAPS = 16, 32
+DF_PROF_STEP, DF_PROF_DPD_BODY, DF_PROF_MD_MAIN, DF_PROF_COPY_BODY = 0, 1, 2, 3
 
 
 class DpdParams(C.Structure):
@@ -31,7 +32,8 @@ class MdParams(C.Structure):
 class DfError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {status_str(status)} ({status})")
+        detail = f" [{lib.df_last_error().decode()}]" if status == DF_ECUDA else ""
+        super().__init__(f"{what}: {status_str(status)} ({status}){detail}")
 
 
 _P = C.c_void_p
@@ -53,6 +55,9 @@ _PROTOS = {
     "df_dpd_set_tile": (C.c_int32, [_P, C.c_int32, C.c_uint32, C.c_uint32]),
     "df_autotune": (C.c_int32, [_P, C.POINTER(C.c_uint64)]),
     "df_status_str": (C.c_char_p, [C.c_int32]),
+    "df_last_error": (C.c_char_p, []),
+    "df_profile_enable": (C.c_int32, [_P, C.c_int32]),
+    "df_profile_get": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     "df_dpd_forward": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
                                    C.POINTER(C.c_int32), _P, _P]),
     "df_dpd_backward": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,

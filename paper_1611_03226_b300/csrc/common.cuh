@@ -69,6 +69,8 @@ struct DpdPlanHdr {
   uint64_t n;               // firings this step
   uint64_t rd_data0;        // data token index of firing 0
   uint64_t wr_out0;         // output token index of firing 0
+  uint64_t slot_data0;      // rd_data0 mod data capacity
+  uint64_t slot_out0;       // wr_out0 mod output capacity
   uint32_t parity_in;       // history buffer the body reads
   uint32_t pad;
 };
@@ -119,14 +121,18 @@ struct MdArgs {
 cudaError_t launch_set_u64(uint64_t* p, uint64_t v, cudaStream_t s);
 cudaError_t launch_add_u64(uint64_t* p, uint64_t v, cudaStream_t s);
 cudaError_t launch_step_begin(EngineDev* e, cudaStream_t s);
-cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s);
+cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                        cudaEvent_t ev1 = nullptr);
 
 cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t s);
 cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile,
                             uint32_t threads, int max_mt, int n_sm, cudaStream_t s);
 int dpd_supported_mt(int M);   // padded tap count used for M (0 = unsupported)
+cudaError_t dpd_prepare();     // one-time kernel attributes (outside graph capture)
 
-cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s);
+cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                           cudaEvent_t ev1 = nullptr);
+cudaError_t md_prepare(int W);     // one-time kernel attributes (outside graph capture)
 size_t md_smem_bytes(int W);
 
 cudaError_t dpd_forward_stateless(const float2* x, uint64_t n, const float2* h, int K, int M,

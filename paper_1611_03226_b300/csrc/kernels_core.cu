@@ -80,9 +80,12 @@ __global__ void k_copy_body(CopyArgs a) {
   else copy_units<uint8_t>(a, pl);
 }
 
-cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s) {
+cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0,
+                        cudaEvent_t ev1) {
   k_copy_plan<<<1, 1, 0, s>>>(a);
+  if (ev0) cudaEventRecord(ev0, s);
   k_copy_body<<<n_sm * 4, 256, 0, s>>>(a);
+  if (ev1) cudaEventRecord(ev1, s);
   return cudaGetLastError();
 }
 

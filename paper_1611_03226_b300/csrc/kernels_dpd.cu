@@ -82,13 +82,15 @@ __device__ uint64_t block_exclusive_scan_u64(uint64_t v, uint64_t* sw, uint64_t*
 // Shared windows are padded with one element after every R elements so that
 // threads reading at stride R elements hit distinct banks.
 // Causal chunk: acc[r] += sum_{m<MC} h[m] * zs[v], v = p*R + shift + r - m + MC - 1.
-// Taps m >= m_valid are zero (unpadded tap rows).
+// Taps m >= m_valid are zero (unpadded tap rows).  The complex product is
+// issued as two passes over the R outputs (real tap part, then imaginary tap
+// part) so consecutive FMAs update different accumulators.
 template <int R, int MC>
 __device__ __forceinline__ void fir_causal(float2 (&acc)[R], const float2* __restrict__ zs, int p,
                                            int shift, const float2* __restrict__ h, int m_valid) {
   float2 hk[MC];
 #pragma unroll
-  for (int m = 0; m < MC; ++m) hk[m] = m < m_valid ? __ldg(h + m) : make_float2(0.f, 0.f);
+  for (int m = 0; m < MC; ++m) hk[m] = m < m_valid ? h[m] : make_float2(0.f, 0.f);
   const float2* zb = zs + p * (R + 1) + shift + shift / R;
 #pragma unroll
   for (int s = 0; s < R + MC - 1; ++s) {
@@ -96,7 +98,18 @@ __device__ __forceinline__ void fir_causal(float2 (&acc)[R], const float2* __res
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int m = r + MC - 1 - s;
-      if (m >= 0 && m < MC) acc[r] = cmac(acc[r], hk[m], z);
+      if (m >= 0 && m < MC) {
+        acc[r].x = fmaf(hk[m].x, z.x, acc[r].x);
+        acc[r].y = fmaf(hk[m].x, z.y, acc[r].y);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = r + MC - 1 - s;
+      if (m >= 0 && m < MC) {
+        acc[r].x = fmaf(-hk[m].y, z.y, acc[r].x);
+        acc[r].y = fmaf(hk[m].y, z.x, acc[r].y);
+      }
     }
   }
 }
@@ -223,6 +236,8 @@ __global__ void __launch_bounds__(256) k_dpd_plan(const DpdArgs* args) {
     a.plan->n = n;
     a.plan->rd_data0 = s_rdd;
     a.plan->wr_out0 = s_wro;
+    a.plan->slot_data0 = s_rdd % a.data.cap;
+    a.plan->slot_out0 = s_wro % a.out.cap;
     a.plan->parity_in = s_par;
     if (n > 0) *a.parity = s_par ^ 1u;
     *rd_ptr(ctr, a.ctrl.id) = s_rdc + n;
@@ -251,58 +266,185 @@ __device__ __forceinline__ float2 hist_sample(const DpdArgs& a, const DpdPlanHdr
   return a.hist[((size_t)pl.parity_in * a.K + k) * H1 + (H1 + pos)];
 }
 
+constexpr int kBranchGroup = 2;           // branch signals staged at once
+
+// u^q from the squares u, u^2, u^4, u^8 (q < 16), else by repeated products.
+__device__ __forceinline__ float pow_sq(float u, float u2, float u4, float u8, int q) {
+  if (q >= 16) {
+    float p = 1.f;
+    for (int i = 0; i < q; ++i) p *= u;
+    return p;
+  }
+  float p = (q & 1) ? u : 1.f;
+  if (q & 2) p *= u2;
+  if (q & 4) p *= u4;
+  if (q & 8) p *= u8;
+  return p;
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__device__ __forceinline__ const uint8_t* slot_at(const ChanDesc& c, uint64_t slot0, uint32_t i) {
+  uint64_t s = slot0 + i;
+  if (s >= c.cap) s -= c.cap;
+  return c.ring + s * c.tok;
+}
+
+struct ItemRef {
+  int g;                    // actor within the group, -1 = none
+  uint32_t i;               // firing
+  uint32_t t0;              // first sample of the tile
+  int len;                  // samples of the tile inside the block
+};
+
+__device__ __forceinline__ ItemRef locate(const DpdArgs* args, const uint64_t* s_off, int G,
+                                          uint64_t item, uint64_t total, uint32_t T) {
+  ItemRef r{-1, 0, 0, 0};
+  if (item >= total) return r;
+  int lo = 0, hi = G;                     // s_off[lo] <= item < s_off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (s_off[mid] <= item) lo = mid; else hi = mid;
+  }
+  const DpdArgs& a = args[lo];
+  const uint64_t local = item - s_off[lo];
+  const uint32_t nt = (a.L + T - 1) / T;
+  r.g = lo;
+  r.i = (uint32_t)(local / nt);
+  r.t0 = (uint32_t)(local % nt) * T;
+  r.len = (int)min(T, a.L - r.t0);
+  return r;
+}
+
+// Copy the x window of `it` (x[t0 - (MT-1) .. t0 + T), zeros outside the block) into xs.
+__device__ __forceinline__ void prefetch_x(const DpdArgs& a, const ItemRef& it, float2* xs, uint32_t T) {
+  const DpdPlanHdr* pl = a.plan;
+  const float2* xb = reinterpret_cast<const float2*>(slot_at(a.data, pl->slot_data0, it.i)) + it.t0;
+  const int MT = a.MT;
+  const int W = (int)T + MT - 1;
+  for (int v = threadIdx.x; v < W; v += blockDim.x) {
+    const int pos = v - (MT - 1);
+    const bool valid = pos < it.len && (int)it.t0 + pos >= 0;
+    cp_async8(xs + v, valid ? (const void*)(xb + pos) : (const void*)xb, valid);
+  }
+}
+
+// u^Q by a fixed multiplication chain (Q known at compile time).
+template <int Q>
+__device__ __forceinline__ float pow_c(float u) {
+  if constexpr (Q == 0) {
+    return 1.f;
+  } else if constexpr (Q == 1) {
+    return u;
+  } else if constexpr (Q % 2 == 0) {
+    const float h = pow_c<Q / 2>(u);
+    return h * h;
+  } else {
+    return pow_c<Q - 1>(u) * u;
+  }
+}
+
+// zg[v + v/R] = |x_v|^(2Q) x_v for the window v < W (padded layout).
+template <int R, int Q>
+__device__ __forceinline__ void zpass(const float2* __restrict__ xs, float2* __restrict__ zg, int W) {
+  const int P = blockDim.x;
+#pragma unroll 4
+  for (int v = threadIdx.x; v < W; v += P) {
+    const float2 x = xs[v];
+    const float pw = pow_c<Q>(fmaf(x.x, x.x, x.y * x.y));
+    zg[v + v / R] = make_float2(pw * x.x, pw * x.y);
+  }
+}
+
+template <int R>
+__device__ void zpass_any(const float2* __restrict__ xs, float2* __restrict__ zg, int W, int q) {
+  for (int v = threadIdx.x; v < W; v += blockDim.x) zg[v + v / R] = psi_q(xs[v], q);
+}
+
+// Shared memory of one body CTA (T = R * blockDim.x samples per tile, W = T + MTmax - 1):
+//   xs[2][W] float2 | zb[kBranchGroup][Wp] float2 (Wp = W + W / R + 2) |
+//   hs[kMaxBranches * MTmax] float2
 template <int R, int MT>
-__device__ void dpd_item(const DpdArgs& a, uint64_t local, float2* xs, float2* zs) {
+__device__ void dpd_compute(const DpdArgs& a, const ItemRef& it, const float2* xs, float2* zb,
+                            int Wp, const float2* hs, int* s_k, int* s_q) {
   const int P = blockDim.x, p = threadIdx.x;
   const uint32_t T = R * P;
-  const DpdPlanHdr pl = *a.plan;
-  const uint64_t nt = (a.L + T - 1) / T;
-  const uint32_t i = (uint32_t)(local / nt);
-  const uint64_t t0 = (local % nt) * T;
-  const int len = (int)min((uint64_t)T, a.L - t0);
-  const uint32_t mask = a.masks[i];
-  float2* yb = reinterpret_cast<float2*>(slot_ptr(a.out, pl.wr_out0 + i)) + t0;
+  const DpdPlanHdr& pl = *a.plan;
+  const uint32_t mask = a.masks[it.i];
+  float2* yb = reinterpret_cast<float2*>(const_cast<uint8_t*>(slot_at(a.out, pl.slot_out0, it.i))) + it.t0;
   if (mask == 0) {
-    for (int o = p; o < len; o += P) yb[o] = make_float2(0.f, 0.f);
+    for (int o = p; o < it.len; o += P) yb[o] = make_float2(0.f, 0.f);
     return;
   }
-  const float2* xb = reinterpret_cast<const float2*>(slot_ptr(a.data, pl.rd_data0 + i));
   const int W = (int)T + MT - 1;
-  for (int v = p; v < W; v += P) {
-    const int64_t pos = (int64_t)t0 - (MT - 1) + v;
-    xs[v] = (pos >= 0 && pos < (int64_t)(t0 + len)) ? xb[pos] : make_float2(0.f, 0.f);
+  int nk = 0;
+  {
+    uint32_t rest = mask;
+    while (rest) {
+      const int k = __ffs(rest) - 1;
+      rest &= rest - 1;
+      if (p == 0) {
+        s_k[nk] = k;
+        s_q[nk] = (a.orders[k] - 1) >> 1;
+      }
+      ++nk;
+    }
   }
   __syncthreads();
   float2 acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = make_float2(0.f, 0.f);
-  for (int k = 0; k < a.K; ++k) {
-    if (!((mask >> k) & 1u)) continue;
-    const int q = (a.orders[k] - 1) >> 1;
-    for (int v = p; v < W; v += P) {
-      const int64_t pos = (int64_t)t0 - (MT - 1) + v;
-      const float2 xv = pos >= 0 ? xs[v] : hist_sample(a, pl, i, k, (int)(MT - 1 + pos));
-      zs[v + v / R] = psi_q(xv, q);
+  for (int g0 = 0; g0 < nk; g0 += kBranchGroup) {
+    const int ng = min(kBranchGroup, nk - g0);
+    // branch signals z = u^q x of this group for the whole window, one tight loop per branch
+    for (int g = 0; g < ng; ++g) {
+      float2* zg = zb + g * Wp;
+      switch (s_q[g0 + g]) {
+#define ZP(Q) case Q: zpass<R, Q>(xs, zg, W); break;
+        ZP(0) ZP(1) ZP(2) ZP(3) ZP(4) ZP(5) ZP(6) ZP(7)
+        ZP(8) ZP(9) ZP(10) ZP(11) ZP(12) ZP(13) ZP(14) ZP(15)
+#undef ZP
+        default: zpass_any<R>(xs, zg, W, s_q[g0 + g]); break;
+      }
+    }
+    if (it.t0 == 0) {
+      // tile 0: the MT-1 samples before the block come from each branch's own history
+      for (int e = p; e < ng * (MT - 1); e += P) {
+        const int g = e / (MT - 1), v = e - g * (MT - 1);
+        zb[g * Wp + v + v / R] = psi_q(hist_sample(a, pl, it.i, s_k[g0 + g], v), s_q[g0 + g]);
+      }
     }
     __syncthreads();
-    fir_branch<R, MT>(acc, zs, p, a.h + (size_t)k * MT, MT);
+#pragma unroll 1
+    for (int g = 0; g < ng; ++g) fir_branch<R, MT>(acc, zb + g * Wp, p, hs + s_k[g0 + g] * MT, MT);
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < R; ++r) zs[p * (R + 1) + r] = acc[r];
+  for (int r = 0; r < R; ++r) zb[p * (R + 1) + r] = acc[r];
   __syncthreads();
-  for (int o = p; o < len; o += P) yb[o] = zs[o + o / R];
-  __syncthreads();
+  for (int o = p; o < it.len; o += P) yb[o] = zb[o + o / R];
 }
 
 constexpr int kMaxGroup = 1024;
 
-template <int R>
+template <int R, int MTMAX>
 __global__ void __launch_bounds__(256) k_dpd_body(const DpdArgs* __restrict__ args, int G) {
   extern __shared__ float4 smem_raw[];
-  __shared__ uint64_t s_off[kMaxGroup + 1];
   __shared__ uint64_t sw[32];
+  __shared__ int s_k[kMaxBranches], s_q[kMaxBranches];
   const uint32_t T = R * blockDim.x;
+  const int Wm = (int)T + MTMAX - 1;
+  const int Wpm = Wm + Wm / R + 2;
+  // work-list offsets of the group's actors live after the tile buffers
+  uint64_t* s_off = reinterpret_cast<uint64_t*>(reinterpret_cast<float2*>(smem_raw) + 2 * Wm +
+                                                kBranchGroup * Wpm + kMaxBranches * MTMAX);
   uint64_t carry = 0;
   for (int base = 0; base < G; base += blockDim.x) {
     const int g = base + threadIdx.x;
@@ -319,30 +461,75 @@ __global__ void __launch_bounds__(256) k_dpd_body(const DpdArgs* __restrict__ ar
   if (threadIdx.x == 0) s_off[G] = carry;
   __syncthreads();
   const uint64_t total = carry;
-  int maxmt = 0;
-  for (int g = 0; g < G; ++g) maxmt = max(maxmt, args[g].MT);
-  float2* xs = reinterpret_cast<float2*>(smem_raw);
-  float2* zs = xs + (T + maxmt);
-  for (uint64_t item = blockIdx.x; item < total; item += gridDim.x) {
-    int lo = 0, hi = G;             // s_off[lo] <= item < s_off[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s_off[mid] <= item) lo = mid; else hi = mid;
+  const int W = (int)T + MTMAX - 1;
+  const int Wp = W + W / R + 2;
+  float2* xsb = reinterpret_cast<float2*>(smem_raw);          // [2][W]
+  float2* zb = xsb + 2 * W;
+  float2* hs = zb + kBranchGroup * Wp;
+  int taps_of = -1;                                            // actor whose taps are in hs
+  uint64_t item = blockIdx.x;
+  ItemRef cur = locate(args, s_off, G, item, total, T);
+  if (cur.g >= 0) prefetch_x(args[cur.g], cur, xsb, T);
+  cp_async_commit();
+  int buf = 0;
+  while (cur.g >= 0) {
+    const uint64_t next_item = item + gridDim.x;
+    const ItemRef nxt = locate(args, s_off, G, next_item, total, T);
+    if (nxt.g >= 0) prefetch_x(args[nxt.g], nxt, xsb + (buf ^ 1) * W, T);
+    cp_async_commit();
+    if (cur.g != taps_of) {
+      const DpdArgs& a = args[cur.g];
+      for (int e = threadIdx.x; e < a.K * a.MT; e += blockDim.x) hs[e] = a.h[e];
+      taps_of = cur.g;
     }
-    const DpdArgs& a = args[lo];
-    const uint64_t local = item - s_off[lo];
+    cp_async_wait1();
+    __syncthreads();
+    const DpdArgs& a = args[cur.g];
     switch (a.MT) {
-#define DPD_CASE(MTV) case MTV: dpd_item<R, MTV>(a, local, xs, zs); break;
+#define DPD_CASE(MTV) \
+      case MTV: if constexpr (MTV <= MTMAX) dpd_compute<R, MTV>(a, cur, xsb + buf * W, zb, Wp, hs, s_k, s_q); break;
       DPD_MT_CASES(DPD_CASE)
 #undef DPD_CASE
       default: break;
     }
+    __syncthreads();
+    cur = nxt;
+    item = next_item;
+    buf ^= 1;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-static size_t body_smem(uint32_t T, int R, int max_mt) {
-  const size_t W = T + max_mt;
-  return (W + (W + W / R + 2)) * sizeof(float2);
+static size_t body_smem(uint32_t T, int R, int mtmax, int G) {
+  const size_t W = T + mtmax - 1;
+  const size_t Wp = W + W / R + 2;
+  return 2 * W * sizeof(float2) + kBranchGroup * Wp * sizeof(float2) +
+         (size_t)kMaxBranches * mtmax * sizeof(float2) + (size_t)(G + 1) * sizeof(uint64_t);
+}
+
+constexpr int kBodySmemMax = 200 * 1024;
+
+template <int R, int MTMAX>
+static cudaError_t body_attr() {
+  return cudaFuncSetAttribute(k_dpd_body<R, MTMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kBodySmemMax);
+}
+
+cudaError_t dpd_prepare() {
+  cudaError_t e;
+  if ((e = body_attr<8, 16>()) != cudaSuccess) return e;
+  if ((e = body_attr<8, 32>()) != cudaSuccess) return e;
+  if ((e = body_attr<16, 16>()) != cudaSuccess) return e;
+  return body_attr<16, 32>();
+}
+
+template <int R, int MTMAX>
+static cudaError_t body_launch(const DpdArgs* args_dev, int n_actors, uint32_t threads, size_t smem,
+                               int n_sm, cudaStream_t s) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dpd_body<R, MTMAX>, threads, smem);
+  k_dpd_body<R, MTMAX><<<n_sm * std::max(per_sm, 1), threads, smem, s>>>(args_dev, n_actors);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile, uint32_t threads,
@@ -350,23 +537,18 @@ cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile
   if (n_actors <= 0) return cudaSuccess;
   if (n_actors > kMaxGroup) return cudaErrorInvalidValue;
   const int R = (int)(tile / threads);
-  const size_t smem = body_smem(tile, R, max_mt);
-  cudaError_t e;
-  int per_sm = 0;
-  if (R == 16) {
-    e = cudaFuncSetAttribute(k_dpd_body<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dpd_body<16>, threads, smem);
-    k_dpd_body<16><<<n_sm * std::max(per_sm, 1), threads, smem, s>>>(args_dev, n_actors);
-  } else if (R == 8) {
-    e = cudaFuncSetAttribute(k_dpd_body<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dpd_body<8>, threads, smem);
-    k_dpd_body<8><<<n_sm * std::max(per_sm, 1), threads, smem, s>>>(args_dev, n_actors);
-  } else {
-    return cudaErrorInvalidValue;
+  const int mtmax = max_mt <= 16 ? 16 : 32;
+  const size_t smem = body_smem(tile, R, mtmax, n_actors);
+  if (smem > (size_t)kBodySmemMax) return cudaErrorInvalidValue;
+  if (R == 8) {
+    return mtmax == 16 ? body_launch<8, 16>(args_dev, n_actors, threads, smem, n_sm, s)
+                       : body_launch<8, 32>(args_dev, n_actors, threads, smem, n_sm, s);
   }
-  return cudaGetLastError();
+  if (R == 16) {
+    return mtmax == 16 ? body_launch<16, 16>(args_dev, n_actors, threads, smem, n_sm, s)
+                       : body_launch<16, 32>(args_dev, n_actors, threads, smem, n_sm, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------- stateless operators ----

@@ -8,17 +8,13 @@
 // Kernels per step:
 //   plan    (1 CTA)   candidate firings n_cand from the frame / count channels
 //                     and the record space; zero the per-frame totals.
-//   main    (1 CTA/SM, persistent)  work = (16-row strip, frame) pairs in
-//                     strip-major order, split evenly over the CTAs.  Each
-//                     strip of the current frame (plus a 2-row halo) is copied
-//                     into shared memory by cp.async.bulk on an mbarrier
-//                     pipeline of 4 stages.  When the previous-frame channel is
-//                     the current-frame channel delayed by one token, the
-//                     previous frame's strip is the stage just consumed, so each
-//                     frame byte is read from HBM once.  Pixels are thresholded
-//                     4 at a time into 32-bit bit planes; erosion and dilation
-//                     are shifts, ANDs and ORs on the bit planes; popcounts give
-//                     the tile counts.
+//   main    (persistent warps)  each warp walks the rows of one 32-row strip
+//                     and 480-pixel column band for a chunk of consecutive
+//                     frames, with the whole per-pixel pipeline in registers
+//                     (see k_md_main).  When the previous-frame channel is the
+//                     current-frame channel delayed by one token, the previous
+//                     frame is read from the current channel's ring, where the
+//                     same warp read it one frame earlier.
 //   finish  (1 CTA)   exclusive scan of the per-frame record totals, the exact
 //                     number of enabled firings, counter commit.
 //   scatter (1 CTA per frame)  raster-order compaction of the tiles with
@@ -28,75 +24,26 @@
 
 namespace dfg {
 
-constexpr int kRH = 16;               // strip rows = one tile row
-constexpr int kBufRows = kRH + 4;     // plus two halo rows above and below
-constexpr int kStages = 4;
-constexpr int kMdThreads = 256;
+constexpr int kMdThreads = 256;     // plan / finish / scatter kernels
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ long long globaltimer_ns() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait: false when `limit_ns` passed without the phase completing.
-__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = globaltimer_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer_ns() - t0 > limit_ns) return false;
-  }
-  return true;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+// Motion bits of 4 pixels: bit i of the result is set iff |c_i - p_i| > thr,
+// with the threshold test done bytewise: for d = |c - p| (per byte), d > thr
+// iff d >= 128 or (d & 0x7f) + (127 - thr) carries into bit 7.  The four byte
+// MSBs (bits 7, 15, 23, 31) are then gathered into bits 28..31 by one multiply.
+__device__ __forceinline__ uint32_t motion_nibble_hi(uint32_t c, uint32_t p, uint32_t add4) {
+  const uint32_t d = __vabsdiffu4(c, p);
+  const uint32_t m = (d | ((d & 0x7f7f7f7fu) + add4)) & 0x80808080u;
+  return m * 0x00204081u;                 // bits 28..31 = pixels 0..3
 }
 
-// 16 pixels of current and previous frame -> 16 motion bits (bit i = pixel i).
-__device__ __forceinline__ uint32_t motion_bits16(uint4 c, uint4 p, uint32_t thr4) {
-  const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
-  const uint32_t pw[4] = {p.x, p.y, p.z, p.w};
-  uint32_t out = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const uint32_t d = __vabsdiffu4(cw[i], pw[i]);
-    const uint32_t m = __vcmpgtu4(d, thr4);           // 0xff in every byte with d > thr
-    // gather the four byte MSBs (bits 7,15,23,31) into bits 28..31
-    const uint32_t nib = ((m & 0x80808080u) * 0x00204081u) >> 28;
-    out |= nib << (4 * i);
-  }
-  return out;
+// 16 pixels (one tile column of a row) -> 16 motion bits, bit i = pixel i.
+__device__ __forceinline__ uint32_t motion_bits16(uint4 c, uint4 p, uint32_t add4) {
+  uint32_t acc = 0;
+  acc = __funnelshift_l(motion_nibble_hi(c.w, p.w, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.z, p.z, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.y, p.y, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.x, p.x, add4), acc, 4);
+  return acc;
 }
 
 __global__ void k_md_plan(MdArgs a) {
@@ -127,182 +74,121 @@ __global__ void k_md_plan(MdArgs a) {
 }
 
 size_t md_smem_bytes(int W) {
-  const size_t words = W / 32;
-  const size_t stage = ((size_t)kBufRows * W + 127) / 128 * 128;
-  return kStages * stage + (2 * kBufRows + kRH) * words * 4 + kStages * 8 + 16;
+  (void)W;
+  return 0;
 }
 
-__global__ void __launch_bounds__(kMdThreads, 1) k_md_main(MdArgs a) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ int s_abort;
+constexpr int kMdRows = 32;               // strip height: two tile rows
+constexpr int kMdWalk = kMdRows + 4;      // rows walked per strip (2-row halo each side)
+constexpr int kMdPre = 4;                 // rows of loads in flight per lane
+constexpr int kMdOwned = 30;              // tile columns owned per warp (lanes 1..30)
+constexpr int kMdWarpsPerCta = 4;
+
+// One warp = one worker.  Work unit = (32-row strip, band of 30 tile columns,
+// chunk of consecutive frames).  Lane l covers tile column 30*band - 1 + l
+// (lanes 0 and 31 are halo lanes that only supply neighbour bits).  For every
+// frame of its chunk the warp walks the strip's rows plus a 2-row halo, each
+// lane loading 16 bytes of the current and of the previous frame per row
+// (coalesced 512-byte rows per warp), and keeps the bit-plane pipeline
+//   b = |cur - prev| > thr  ->  erosion (3 rows)  ->  dilation (3 rows)  ->  popcount
+// in registers; horizontal neighbours come from lane shuffles.  The previous
+// frame of frame j is the current frame of j - 1 that the same warp just read,
+// so it is served by L1/L2 and each frame byte is read from DRAM about once.
+__global__ void __launch_bounds__(kMdWarpsPerCta * 32, 6) k_md_main(MdArgs a) {
   const MdPlanHdr pl = *a.plan;
   const uint64_t n = pl.n_cand;
   if (n == 0) return;
-  const int W = a.W, H = a.H, words = a.words;
-  const size_t stage_bytes = ((size_t)kBufRows * W + 127) / 128 * 128;
-  uint8_t* stages = smem;
-  uint32_t* bw = reinterpret_cast<uint32_t*>(smem + kStages * stage_bytes);
-  uint32_t* ew = bw + kBufRows * words;
-  uint32_t* pc = ew + kBufRows * words;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(pc + kRH * words) + 7) & ~uintptr_t(7));
-
-  const uint64_t total = (uint64_t)a.strips * n;
-  const uint64_t first = total * blockIdx.x / gridDim.x;
-  const uint64_t last = total * (blockIdx.x + 1) / gridDim.x;
-  if (first >= last) return;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
-    mbar_fence_init();
-    s_abort = 0;
-  }
-  __syncthreads();
-
-  const uint32_t thr4 = 0x01010101u * (uint32_t)a.thr;
-  const int chunks_row = W / 16;
-  auto needs_prev_load = [&](uint64_t item) {
-    return !a.dedup || item == first || (item % n) == 0;
-  };
-  // producer state (thread 0)
-  uint64_t p_item = first, p_k = 0;
-  bool p_prev_done = false;
-  auto issue = [&](uint64_t k, uint64_t item, bool is_prev) {
-    const int strip = (int)(item / n);
-    const uint64_t j = item % n;
-    const int y0 = strip * kRH;
-    const int r0 = max(0, y0 - 2), r1 = min(H, y0 + kRH + 2);
-    const uint8_t* tok;
-    if (!is_prev) tok = slot_ptr(a.cur, pl.rd_cur0 + j);
-    else if (a.dedup && j >= 1) tok = slot_ptr(a.cur, pl.rd_cur0 + j - 1);
-    else tok = slot_ptr(a.prev, pl.rd_prev0 + j);
-    uint8_t* dst = stages + (k % kStages) * stage_bytes + (size_t)(r0 - (y0 - 2)) * W;
-    const uint32_t bytes = (uint32_t)(r1 - r0) * W;
-    uint64_t* bar = &bars[k % kStages];
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(dst, tok + (size_t)r0 * W, bytes, bar);
-  };
-
-  uint64_t c_k = 0;     // index of the next load to be consumed
-  for (uint64_t item = first; item < last; ++item) {
-    const int strip = (int)(item / n);
-    const uint64_t j = item % n;
-    const uint64_t k_cur = c_k + (needs_prev_load(item) ? 1 : 0);
-    if (threadIdx.x == 0) {
-      const uint64_t limit = k_cur - 1 + kStages;
-      while (p_k < limit && p_item < last) {
-        if (needs_prev_load(p_item) && !p_prev_done) {
-          issue(p_k, p_item, true);
-          p_prev_done = true;
-        } else {
-          issue(p_k, p_item, false);
-          ++p_item;
-          p_prev_done = false;
-        }
-        ++p_k;
-      }
-      const uint64_t kp = k_cur - 1;
-      const bool ok =
-          mbar_wait_bounded(&bars[kp % kStages], (uint32_t)((kp / kStages) & 1), a.wait_limit_ns) &&
-          mbar_wait_bounded(&bars[k_cur % kStages], (uint32_t)((k_cur / kStages) & 1),
-                            a.wait_limit_ns);
-      if (!ok) {
-        s_abort = 1;
-        set_status(a.eng, DF_ETIMEOUT, kWhereMdPipe);
-      }
-    }
-    __syncthreads();
-    if (s_abort) break;
-    const uint8_t* cb = stages + (k_cur % kStages) * stage_bytes;
-    const uint8_t* pb = stages + ((k_cur - 1) % kStages) * stage_bytes;
-    const int y0 = strip * kRH;
-
-    // 1. motion bits for buffer rows 0..kBufRows-1 (frame rows y0-2 .. y0+kRH+1);
-    //    rows outside the frame read as all ones (erosion border).
-    const int n_chunks = kBufRows * chunks_row;
-    for (int base = 0; base < n_chunks; base += kMdThreads) {
-      const int c = base + threadIdx.x;
-      uint32_t half = 0;
-      int row = 0, ch = 0;
-      if (c < n_chunks) {
-        row = c / chunks_row;
-        ch = c - row * chunks_row;
-        const int y = y0 - 2 + row;
-        if (y < 0 || y >= H) {
-          half = 0xffffu;
-        } else {
-          const size_t off = (size_t)row * W + ch * 16;
-          half = motion_bits16(*reinterpret_cast<const uint4*>(cb + off),
-                               *reinterpret_cast<const uint4*>(pb + off), thr4);
-        }
-      }
-      const uint32_t other = __shfl_xor_sync(0xffffffffu, half, 1);
-      if (c < n_chunks && !(threadIdx.x & 1)) bw[row * words + (ch >> 1)] = half | (other << 16);
-    }
-    __syncthreads();
-
-    // 2. erosion for buffer rows 1..kBufRows-2; rows outside the frame become 0
-    //    (dilation border).
-    for (int e = threadIdx.x; e < (kBufRows - 2) * words; e += kMdThreads) {
-      const int r = 1 + e / words, w = e % words;
-      const int y = y0 - 2 + r;
-      uint32_t v = 0;
-      if (y >= 0 && y < H) {
-        v = 0xffffffffu;
+  const int W = a.W, H = a.H;
+  const int lane = threadIdx.x & 31;
+  const int cols = W / 16;                                    // tile columns
+  const int bands = (cols + kMdOwned - 1) / kMdOwned;
+  const int strips = (H + kMdRows - 1) / kMdRows;
+  const uint32_t pairs = (uint32_t)(strips * bands);
+  const uint32_t G = gridDim.x * kMdWarpsPerCta;              // workers
+  uint32_t chunks = G / pairs;
+  if (chunks < 1) chunks = 1;
+  if (chunks > n) chunks = (uint32_t)n;
+  const uint32_t units = pairs * chunks;
+  const uint32_t add4 = 0x01010101u * (uint32_t)(127 - a.thr);
+  for (uint32_t u = blockIdx.x * kMdWarpsPerCta + (threadIdx.x >> 5); u < units; u += G) {
+    const uint32_t pair = u % pairs, chunk = u / pairs;
+    const int strip = (int)(pair / bands), band = (int)(pair % bands);
+    const uint64_t j0 = n * chunk / chunks, j1 = n * (chunk + 1) / chunks;
+    const int col = band * kMdOwned - 1 + lane;               // this lane's tile column
+    const bool col_in = col >= 0 && col < cols;
+    const bool owned = lane >= 1 && lane <= kMdOwned && col_in;
+    const int y0 = strip * kMdRows;
+    const size_t col_off = (size_t)(col_in ? col : 0) * 16;
+    for (uint64_t j = j0; j < j1; ++j) {
+      const uint8_t* cur = slot_ptr(a.cur, pl.rd_cur0 + j) + col_off;
+      const uint8_t* prv;
+      if (a.dedup && j >= 1) prv = slot_ptr(a.cur, pl.rd_cur0 + j - 1) + col_off;
+      else prv = slot_ptr(a.prev, pl.rd_prev0 + j) + col_off;
+      uint4 cb[kMdPre], pb[kMdPre];
 #pragma unroll
-        for (int dr = -1; dr <= 1; ++dr) {
-          const uint32_t* row = bw + (r + dr) * words;
-          const uint32_t b = row[w];
-          const uint32_t l = w > 0 ? row[w - 1] >> 31 : 1u;
-          const uint32_t rt = w < words - 1 ? row[w + 1] & 1u : 1u;
-          v &= b & ((b << 1) | l) & ((b >> 1) | (rt << 31));
+      for (int r = 0; r < kMdPre; ++r) {
+        const int y = y0 - 2 + r;
+        if (col_in && y >= 0 && y < H) {
+          cb[r] = __ldg(reinterpret_cast<const uint4*>(cur + (size_t)y * W));
+          pb[r] = __ldg(reinterpret_cast<const uint4*>(prv + (size_t)y * W));
         }
       }
-      ew[r * words + w] = v;
-    }
-    __syncthreads();
-
-    // 3. dilation for the kRH strip rows, popcount of each 16-pixel half word.
-    for (int e = threadIdx.x; e < kRH * words; e += kMdThreads) {
-      const int r = 2 + e / words, w = e % words;
-      const int y = y0 - 2 + r;
-      uint32_t packed = 0;
-      if (y < H) {
-        uint32_t o = 0;
+      uint32_t hb1 = 0, hb2 = 0;        // horizontally eroded rows y-2, y-1
+      uint32_t he1 = 0, he2 = 0;        // horizontally dilated erosion rows
+      uint32_t cnt0 = 0, cnt1 = 0;      // tile counts of the two tile rows
+#pragma unroll 1
+      for (int rg = 0; rg < kMdWalk; rg += kMdPre) {
 #pragma unroll
-        for (int dr = -1; dr <= 1; ++dr) {
-          const uint32_t* row = ew + (r + dr) * words;
-          const uint32_t v = row[w];
-          const uint32_t l = w > 0 ? row[w - 1] >> 31 : 0u;
-          const uint32_t rt = w < words - 1 ? row[w + 1] & 1u : 0u;
-          o |= v | ((v << 1) | l) | ((v >> 1) | (rt << 31));
+        for (int q = 0; q < kMdPre; ++q) {
+          const int r = rg + q;
+          const int y = y0 - 2 + r;
+          const bool row_in = y >= 0 && y < H;
+          uint32_t b = 0xffffu;                                  // outside: erosion border
+          if (col_in && row_in) b = motion_bits16(cb[q], pb[q], add4);
+          if (r + kMdPre < kMdWalk) {
+            const int yn = y + kMdPre;
+            if (col_in && yn >= 0 && yn < H) {
+              cb[q] = __ldg(reinterpret_cast<const uint4*>(cur + (size_t)yn * W));
+              pb[q] = __ldg(reinterpret_cast<const uint4*>(prv + (size_t)yn * W));
+            }
+          }
+          // horizontal erosion: x holds pixels -1..16 of this lane in bits 0..17
+          const uint32_t l = __shfl_up_sync(0xffffffffu, b, 1);
+          const uint32_t rr = __shfl_down_sync(0xffffffffu, b, 1);
+          const uint32_t x = ((rr & 1u) << 17) | (b << 1) | ((l >> 15) & 1u);
+          const uint32_t hb = x & (x >> 1) & (x >> 2) & 0xffffu;
+          // erosion of row y-1 (rows y-2, y-1, y); 0 outside the frame (dilation border)
+          const int ye = y - 1;
+          uint32_t e = 0;
+          if (r >= 2 && col_in && ye >= 0 && ye < H) e = hb2 & hb1 & hb;
+          hb2 = hb1;
+          hb1 = hb;
+          const uint32_t le = __shfl_up_sync(0xffffffffu, e, 1);
+          const uint32_t re = __shfl_down_sync(0xffffffffu, e, 1);
+          const uint32_t xe = ((re & 1u) << 17) | (e << 1) | ((le >> 15) & 1u);
+          const uint32_t he = (xe | (xe >> 1) | (xe >> 2)) & 0xffffu;
+          // dilation of row y-2 (erosion rows y-3, y-2, y-1), produced for r = 4 .. 35
+          const int yo = y - 2;
+          if (r >= 4 && yo < H) {
+            const uint32_t pc = __popc(he2 | he1 | he);
+            if (r - 4 < 16) cnt0 += pc;
+            else cnt1 += pc;
+          }
+          he2 = he1;
+          he1 = he;
         }
-        packed = (uint32_t)__popc(o & 0xffffu) | ((uint32_t)__popc(o >> 16) << 16);
       }
-      pc[(r - 2) * words + w] = packed;
-    }
-    __syncthreads();
-
-    // 4. tile counts of this strip (one tile row) and the frame's record total.
-    int nz = 0;
-    for (int base = 0; base < a.tiles_x; base += kMdThreads) {
-      const int t = base + threadIdx.x;
-      uint32_t cnt = 0;
-      if (t < a.tiles_x) {
-        const int w = t >> 1, sh = (t & 1) * 16;
-        for (int r = 0; r < kRH; ++r) cnt += (pc[r * words + w] >> sh) & 0xffffu;
-        a.counts[j * a.n_tiles + (size_t)strip * a.tiles_x + t] = (uint16_t)cnt;
+      // rows y0 .. y0+31 were produced at r = 4 .. 35
+      uint32_t nz = 0;
+      const int ty0 = 2 * strip;
+      if (owned) a.counts[j * a.n_tiles + (size_t)ty0 * a.tiles_x + col] = (uint16_t)cnt0;
+      nz += __popc(__ballot_sync(0xffffffffu, owned && cnt0 > 0));
+      if (ty0 + 1 < a.tiles_y) {
+        if (owned) a.counts[j * a.n_tiles + (size_t)(ty0 + 1) * a.tiles_x + col] = (uint16_t)cnt1;
+        nz += __popc(__ballot_sync(0xffffffffu, owned && cnt1 > 0));
       }
-      nz += __syncthreads_count(cnt > 0);
+      if (lane == 0 && nz) atomicAdd(&a.frame_tot[j], nz);
     }
-    if (threadIdx.x == 0 && nz) atomicAdd(&a.frame_tot[j], (uint32_t)nz);
-    c_k = k_cur + 1;
-    __syncthreads();
-  }
-  if (s_abort && threadIdx.x == 0) {
-    // let copies still in flight land before the CTA's shared memory goes away
-    for (uint64_t k = c_k; k < p_k; ++k)
-      mbar_wait_bounded(&bars[k % kStages], (uint32_t)((k / kStages) & 1), a.wait_limit_ns);
   }
 }
 
@@ -410,13 +296,24 @@ __global__ void __launch_bounds__(kMdThreads) k_md_scatter(MdArgs a) {
     *reinterpret_cast<uint32_t*>(slot_ptr(a.cnt, pl.wr_cnt0 + j)) = a.frame_tot[j];
 }
 
-cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s) {
-  const size_t smem = md_smem_bytes(a.W);
-  cudaError_t e = cudaFuncSetAttribute(k_md_main, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+static int g_md_blocks_per_sm = 0;
+
+cudaError_t md_prepare(int W) {
+  (void)W;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_md_main,
+                                                                kMdWarpsPerCta * 32, 0);
   if (e != cudaSuccess) return e;
+  g_md_blocks_per_sm = per_sm > 0 ? per_sm : 1;
+  return cudaSuccess;
+}
+
+cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0,
+                           cudaEvent_t ev1) {
   k_md_plan<<<1, 256, 0, s>>>(a);
-  k_md_main<<<n_sm, kMdThreads, smem, s>>>(a);
+  if (ev0) cudaEventRecord(ev0, s);
+  k_md_main<<<n_sm * (g_md_blocks_per_sm ? g_md_blocks_per_sm : 8), kMdWarpsPerCta * 32, 0, s>>>(a);
+  if (ev1) cudaEventRecord(ev1, s);
   k_md_finish<<<1, 256, 0, s>>>(a);
   k_md_scatter<<<a.n_max, kMdThreads, 0, s>>>(a);
   return cudaGetLastError();

@@ -10,6 +10,7 @@
 // body launch.  A step never returns to the host: rate decisions, scans,
 // gathers and scatters are all device kernels reading the device counters.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -76,16 +77,28 @@ struct df_net {
   uint64_t* h_pin = nullptr;          // pinned staging (counters, status)
   std::map<std::pair<int64_t, uint32_t>, cudaGraphExec_t> graphs;
   long long wait_limit_ns = 1000000000LL;
+  // kernel timing (df_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double prof_ms[4] = {0, 0, 0, 0};
+  uint64_t prof_n[4] = {0, 0, 0, 0};
 };
 
 namespace {
 
-df_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DF_OK : DF_ECUDA; }
 
-#define DF_CUDA(x)                               \
-  do {                                           \
-    cudaError_t e_ = (x);                        \
-    if (e_ != cudaSuccess) return DF_ECUDA;      \
+thread_local char g_last_error[256] = "";
+
+df_status record_cuda(cudaError_t e, const char* what) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+  return DF_ECUDA;
+}
+
+#define DF_CUDA(x)                                       \
+  do {                                                   \
+    cudaError_t e_ = (x);                                \
+    if (e_ != cudaSuccess) return record_cuda(e_, #x);   \
   } while (0)
 
 struct DeviceGuard {
@@ -209,40 +222,83 @@ df_status ring_copy(df_net* net, const ChanDesc& c, uint64_t t, void* lin, uint6
   return DF_OK;
 }
 
-uint32_t default_tile(const DpdArgs& a) { return a.L >= 2048 ? 2048 : 1024; }
+uint32_t default_tile(const DpdArgs& a) { return a.L >= 1024 ? 1024 : 512; }
 
-df_status enqueue_step(df_net* net, bool no_batch) {
+cudaEvent_t take_event(df_net* net) {
+  if (!net->ev_free.empty()) {
+    cudaEvent_t e = net->ev_free.back();
+    net->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Timing pair for `what` when profiling is on (both null otherwise).
+std::pair<cudaEvent_t, cudaEvent_t> prof_pair(df_net* net, int what, bool capturing) {
+  if (!net->prof || capturing) return {nullptr, nullptr};
+  std::pair<cudaEvent_t, cudaEvent_t> p{take_event(net), take_event(net)};
+  if (!p.first || !p.second) return {nullptr, nullptr};
+  net->ev_pending.push_back({what, p});
+  return p;
+}
+
+df_status prof_collect(df_net* net) {
+  if (net->ev_pending.empty()) return DF_OK;
+  DF_CUDA(cudaStreamSynchronize(net->stream));
+  for (auto& pe : net->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+      net->prof_ms[pe.first] += ms;
+      net->prof_n[pe.first] += 1;
+    }
+    net->ev_free.push_back(pe.second.first);
+    net->ev_free.push_back(pe.second.second);
+  }
+  net->ev_pending.clear();
+  return DF_OK;
+}
+
+df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
   cudaStream_t s = net->stream;
+  const auto step_ev = prof_pair(net, DF_PROF_STEP, capturing);
+  if (step_ev.first) DF_CUDA(cudaEventRecord(step_ev.first, s));
   DF_CUDA(launch_step_begin(net->d_eng, s));
   for (const Op& op : net->program) {
     switch (op.kind) {
-      case kOpCopy:
-        DF_CUDA(launch_copy(op.copy, net->n_sm, s));
+      case kOpCopy: {
+        const auto ev = prof_pair(net, DF_PROF_COPY_BODY, capturing);
+        DF_CUDA(launch_copy(op.copy, net->n_sm, s, ev.first, ev.second));
         break;
-      case kOpMd:
-        DF_CUDA(launch_md_step(op.md, net->n_sm, s));
+      }
+      case kOpMd: {
+        const auto ev = prof_pair(net, DF_PROF_MD_MAIN, capturing);
+        DF_CUDA(launch_md_step(op.md, net->n_sm, s, ev.first, ev.second));
         break;
+      }
       case kOpDpd: {
         const ActorH& A0 = net->actors[op.dpd_first_actor];
         uint32_t tile = A0.tile, threads = A0.threads;
         if (!tile || !threads) {
           const DpdArgs& a = net->dpd_host[net->dpd_index[op.dpd_first_actor]];
           tile = default_tile(a);
-          threads = 128;
+          threads = tile / 8;
         }
-        if (no_batch) {
-          for (int i = 0; i < op.dpd_n; ++i) {
-            DF_CUDA(launch_dpd_plan(op.dpd_dev + i, 1, s));
-            DF_CUDA(launch_dpd_body(op.dpd_dev + i, 1, tile, threads, op.max_mt, net->n_sm, s));
-          }
-        } else {
-          DF_CUDA(launch_dpd_plan(op.dpd_dev, op.dpd_n, s));
-          DF_CUDA(launch_dpd_body(op.dpd_dev, op.dpd_n, tile, threads, op.max_mt, net->n_sm, s));
+        const int n_launch = no_batch ? op.dpd_n : 1;
+        const int per = no_batch ? 1 : op.dpd_n;
+        for (int i = 0; i < n_launch; ++i) {
+          DF_CUDA(launch_dpd_plan(op.dpd_dev + i, per, s));
+          const auto ev = prof_pair(net, DF_PROF_DPD_BODY, capturing);
+          if (ev.first) DF_CUDA(cudaEventRecord(ev.first, s));
+          DF_CUDA(launch_dpd_body(op.dpd_dev + i, per, tile, threads, op.max_mt, net->n_sm, s));
+          if (ev.second) DF_CUDA(cudaEventRecord(ev.second, s));
         }
         break;
       }
     }
   }
+  if (step_ev.second) DF_CUDA(cudaEventRecord(step_ev.second, s));
   return DF_OK;
 }
 
@@ -255,7 +311,13 @@ std::map<int, Scratch> g_scratch;       // per device: backward tap-gradient par
 
 }  // namespace
 
+df_status cuda_status(cudaError_t e) {
+  return e == cudaSuccess ? DF_OK : record_cuda(e, "kernel launch");
+}
+
 extern "C" {
+
+const char* df_last_error(void) { return g_last_error; }
 
 const char* df_status_str(df_status s) {
   switch (s) {
@@ -300,6 +362,11 @@ void df_net_destroy(df_net* net) {
   DeviceGuard g(net->device);
   if (net->stream) cudaStreamSynchronize(net->stream);
   for (auto& kv : net->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& pe : net->ev_pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (cudaEvent_t e : net->ev_free) cudaEventDestroy(e);
   if (net->arena) cudaFree(net->arena);
   if (net->h_pin) cudaFreeHost(net->h_pin);
   if (net->own_stream) cudaStreamDestroy(net->stream);
@@ -599,6 +666,9 @@ df_status df_net_finalize(df_net* net) {
     }
   }
   flush_group();
+  if (!dp.empty()) DF_CUDA(dpd_prepare());
+  for (const Op& op : net->program)
+    if (op.kind == kOpMd) DF_CUDA(md_prepare(op.md.W));
   DF_CUDA(cudaStreamSynchronize(s));
   net->finalized = true;
   return DF_OK;
@@ -666,7 +736,7 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
         cudaGraph_t graph;
         DF_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
         df_status st = DF_OK;
-        for (int64_t i = 0; i < n_steps && st == DF_OK; ++i) st = enqueue_step(net, no_batch);
+        for (int64_t i = 0; i < n_steps && st == DF_OK; ++i) st = enqueue_step(net, no_batch, true);
         const cudaError_t ce = cudaStreamEndCapture(net->stream, &graph);
         if (st != DF_OK) return st;
         DF_CUDA(ce);
@@ -770,6 +840,29 @@ df_status df_dpd_set_tile(df_net* net, int32_t actor, uint32_t tile, uint32_t th
   net->actors[actor].threads = threads;
   for (auto& kv : net->graphs) cudaGraphExecDestroy(kv.second);
   net->graphs.clear();
+  return DF_OK;
+}
+
+df_status df_profile_enable(df_net* net, int32_t on) {
+  if (!net) return DF_EINVAL;
+  DeviceGuard g(net->device);
+  const df_status st = prof_collect(net);
+  if (st != DF_OK) return st;
+  net->prof = on != 0;
+  for (int i = 0; i < 4; ++i) {
+    net->prof_ms[i] = 0;
+    net->prof_n[i] = 0;
+  }
+  return DF_OK;
+}
+
+df_status df_profile_get(df_net* net, int32_t what, double* total_ms, uint64_t* launches) {
+  if (!net || what < 0 || what > 3) return DF_EINVAL;
+  DeviceGuard g(net->device);
+  const df_status st = prof_collect(net);
+  if (st != DF_OK) return st;
+  if (total_ms) *total_ms = net->prof_ms[what];
+  if (launches) *launches = net->prof_n[what];
   return DF_OK;
 }
 

@@ -26,9 +26,15 @@ def _ptr(buf):
 
 
 class Net:
+    """One network.  ``stream`` is a cudaStream_t handle (int) the network runs
+    on; None or 0 lets the network create its own stream (the legacy default
+    stream is never used)."""
+
     def __init__(self, device: int = 0, stream=None):
         h = C.c_void_p()
-        s = C.c_void_p(stream) if stream is not None else None
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        s = C.c_void_p(stream) if stream else None
         L.check(L.lib.df_net_create(C.byref(h), device, s), "df_net_create")
         self.h = h
         self.chan_tok = {}
@@ -151,6 +157,14 @@ class Net:
         L.check(L.lib.df_channel_counters(self.h, ch, C.byref(p), C.byref(c), C.byref(o)),
                 "df_channel_counters")
         return p.value, c.value, o.value
+
+    def profile(self, on=True):
+        L.check(L.lib.df_profile_enable(self.h, 1 if on else 0), "df_profile_enable")
+
+    def profile_get(self, what):
+        ms, n = C.c_double(), C.c_uint64()
+        L.check(L.lib.df_profile_get(self.h, what, C.byref(ms), C.byref(n)), "df_profile_get")
+        return ms.value, n.value
 
     def set_tile(self, actor, tile, threads):
         L.check(L.lib.df_dpd_set_tile(self.h, actor, tile, threads), "df_dpd_set_tile")
