@@ -227,6 +227,24 @@ df_status df_dpd_backward(const void *x, uint64_t n, const void *h, int32_t K, i
                           const int32_t *orders, const void *grad_y, void *grad_x, void *grad_h,
                           void *cuda_stream);
 
+/* Same computation and results as df_dpd_backward, but it allocates nothing.
+ * (The paper has no counterpart; this exists for callers that may not
+ * allocate device memory, e.g. a real-time adaptation loop where cudaMalloc
+ * could synchronise the device and block, or a runtime with a fixed device
+ * memory budget.)  The tap-gradient partial sums live in a fixed array inside
+ * the library image: 131072 complex values (1 MiB) that every GPU loading the
+ * library keeps until the process exits.  A call needs ceil(n/1024) * K * MT
+ * of them (MT = M rounded up to 4, 8, M for 9..16, or 32); larger calls
+ * return DF_ENOTSUP and do nothing.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array, so calls whose kernels overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Each call rewrites
+ * every partial sum it reads, so nothing is carried over between calls. */
+df_status df_dpd_backward_noalloc(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                                  const int32_t *orders, const void *grad_y, void *grad_x,
+                                  void *grad_h, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
