@@ -109,6 +109,7 @@ struct MdArgs {
   int tiles_x, tiles_y, n_tiles;
   int strips;               // ceil(H / 16)
   int dedup;                // prev channel == cur channel delayed by one token
+  int shared_rows;          // dedup and the current ring is under 2 GiB: 8-frame units
   uint32_t n_max;
   MdPlanHdr* plan;
   uint16_t* counts;         // [n_max][n_tiles]

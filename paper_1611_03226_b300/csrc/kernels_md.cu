@@ -9,12 +9,11 @@
 //   plan    (1 CTA)   candidate firings n_cand from the frame / count channels
 //                     and the record space; zero the per-frame totals.
 //   main    (persistent warps)  each warp walks the rows of one 32-row strip
-//                     and 480-pixel column band for a chunk of consecutive
+//                     and 480-pixel column band for a chunk of 8 consecutive
 //                     frames, with the whole per-pixel pipeline in registers
-//                     (see k_md_main).  When the previous-frame channel is the
-//                     current-frame channel delayed by one token, the previous
-//                     frame is read from the current channel's ring, where the
-//                     same warp read it one frame earlier.
+//                     (see md_unit).  When the previous-frame channel is the
+//                     current-frame channel delayed by one token, each frame
+//                     row is loaded once and serves both frames that use it.
 //   finish  (1 CTA)   exclusive scan of the per-frame record totals, the exact
 //                     number of enabled firings, counter commit.
 //   scatter (1 CTA per frame)  raster-order compaction of the tiles with
@@ -34,16 +33,6 @@ __device__ __forceinline__ uint32_t motion_nibble_hi(uint32_t c, uint32_t p, uin
   const uint32_t d = __vabsdiffu4(c, p);
   const uint32_t m = (d | ((d & 0x7f7f7f7fu) + add4)) & 0x80808080u;
   return m * 0x00204081u;                 // bits 28..31 = pixels 0..3
-}
-
-// 16 pixels (one tile column of a row) -> 16 motion bits, bit i = pixel i.
-__device__ __forceinline__ uint32_t motion_bits16(uint4 c, uint4 p, uint32_t add4) {
-  uint32_t acc = 0;
-  acc = __funnelshift_l(motion_nibble_hi(c.w, p.w, add4), acc, 4);
-  acc = __funnelshift_l(motion_nibble_hi(c.z, p.z, add4), acc, 4);
-  acc = __funnelshift_l(motion_nibble_hi(c.y, p.y, add4), acc, 4);
-  acc = __funnelshift_l(motion_nibble_hi(c.x, p.x, add4), acc, 4);
-  return acc;
 }
 
 __global__ void k_md_plan(MdArgs a) {
@@ -80,115 +69,169 @@ size_t md_smem_bytes(int W) {
 
 constexpr int kMdRows = 32;               // strip height: two tile rows
 constexpr int kMdWalk = kMdRows + 4;      // rows walked per strip (2-row halo each side)
-constexpr int kMdPre = 4;                 // rows of loads in flight per lane
 constexpr int kMdOwned = 30;              // tile columns owned per warp (lanes 1..30)
 constexpr int kMdWarpsPerCta = 4;
+constexpr int kMdFrames = 8;              // frames per work unit
+
+// 16 pixels (one tile column of one row) -> 16 motion bits, bit i = pixel i.
+__device__ __forceinline__ uint32_t motion_bits16(uint4 c, uint4 p, uint32_t add4) {
+  uint32_t acc = 0;
+  acc = __funnelshift_l(motion_nibble_hi(c.w, p.w, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.z, p.z, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.y, p.y, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.x, p.x, add4), acc, 4);
+  return acc;
+}
+
+__device__ __forceinline__ const uint8_t* frame_at(const ChanDesc& c, uint64_t slot0, uint64_t j) {
+  uint64_t s = slot0 + j;
+  if (s >= c.cap) s -= c.cap;
+  return c.ring + s * c.tok;
+}
+
+// Two frames' 16-pixel rows packed in one word (frame A in bits 0..15, frame B
+// in bits 16..31).  Horizontal 3-neighbourhoods of both halves at once: pixel i
+// combines pixels i-1, i, i+1, where pixel -1 is bit 15 (31) of the left lane's
+// word and pixel 16 is bit 0 (16) of the right lane's word.
+__device__ __forceinline__ uint32_t left_nb(uint32_t v, uint32_t left) {     // pixel i-1 at bit i
+  return ((v << 1) & 0xfffefffeu) | ((left >> 15) & 0x00010001u);
+}
+__device__ __forceinline__ uint32_t right_nb(uint32_t v, uint32_t right) {   // pixel i+1 at bit i
+  return ((v >> 1) & 0x7fff7fffu) | ((right << 15) & 0x80008000u);
+}
 
 // One warp = one worker.  Work unit = (32-row strip, band of 30 tile columns,
-// chunk of consecutive frames).  Lane l covers tile column 30*band - 1 + l
-// (lanes 0 and 31 are halo lanes that only supply neighbour bits).  For every
-// frame of its chunk the warp walks the strip's rows plus a 2-row halo, each
-// lane loading 16 bytes of the current and of the previous frame per row
-// (coalesced 512-byte rows per warp), and keeps the bit-plane pipeline
+// chunk of up to F consecutive frames, F even).  Lane l covers tile column
+// 30*band - 1 + l; lanes 0 and 31 are halo lanes that only supply neighbour
+// bits.  The warp walks the strip's rows plus a 2-row halo; for every row it
+// reads that row of frames j0-1 .. j0+F-1 once (one 16-byte load per lane and
+// frame, 512 contiguous bytes per warp), and each loaded row serves as the
+// current row of frame j and the previous row of frame j+1.  The pipeline
 //   b = |cur - prev| > thr  ->  erosion (3 rows)  ->  dilation (3 rows)  ->  popcount
-// in registers; horizontal neighbours come from lane shuffles.  The previous
-// frame of frame j is the current frame of j - 1 that the same warp just read,
-// so it is served by L1/L2 and each frame byte is read from DRAM about once.
-__global__ void __launch_bounds__(kMdWarpsPerCta * 32, 6) k_md_main(MdArgs a) {
+// runs in registers on pairs of frames packed into one word; horizontal
+// neighbour bits come from lane shuffles.  With a previous-frame channel that
+// is not the delayed current channel, F = 2 with a separate previous row per
+// frame.
+template <int F>
+__device__ void md_unit(const MdArgs& a, uint64_t slot_cur0, uint64_t slot_prev0, int strip,
+                        int band, uint64_t j0, int nf, uint32_t add4) {
+  static_assert(F % 2 == 0, "frames are processed in pairs");
+  constexpr int NP = F / 2;
+  const int W = a.W, H = a.H;
+  const int lane = threadIdx.x & 31;
+  const int cols = W / 16;
+  const int col = band * kMdOwned - 1 + lane;                // this lane's tile column
+  const bool col_in = col >= 0 && col < cols;
+  const bool owned = lane >= 1 && lane <= kMdOwned && col_in;
+  const int y0 = strip * kMdRows;
+  const size_t col_off = (size_t)(col_in ? col : 0) * 16;
+  // Row sources.  F > 2 (shared previous rows, ring < 2 GiB): frame t of the
+  // unit is at cbase + coff[t]; the previous frame of frame 0 is at p0.  F == 2:
+  // explicit pointers for both frames and both previous frames.
+  const uint8_t* cbase = frame_at(a.cur, slot_cur0, j0);
+  int32_t coff[F];
+#pragma unroll
+  for (int t = 0; t < F; ++t) {
+    const uint8_t* f = frame_at(a.cur, slot_cur0, j0 + (t < nf ? t : 0));
+    coff[t] = (int32_t)(f - cbase);
+  }
+  const uint8_t* p0 = (a.dedup && j0 >= 1) ? frame_at(a.cur, slot_cur0, j0 - 1)
+                                           : frame_at(a.prev, slot_prev0, j0);
+  const uint8_t* p1 = nullptr;               // previous frame of frame 1 when not shared
+  if constexpr (F == 2) {
+    p1 = a.dedup ? frame_at(a.cur, slot_cur0, j0) : frame_at(a.prev, slot_prev0, j0 + (nf > 1 ? 1 : 0));
+  }
+  uint32_t hb1[NP], hb2[NP], he1[NP], he2[NP], cn[F];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) hb1[q] = hb2[q] = he1[q] = he2[q] = 0;
+#pragma unroll
+  for (int t = 0; t < F; ++t) cn[t] = 0;
+#pragma unroll 1
+  for (int r = 0; r < kMdWalk; ++r) {
+    const int y = y0 - 2 + r;
+    const bool ld = col_in && y >= 0 && y < H;
+    const size_t off = (size_t)y * W + col_off;
+    uint4 qc[F], qp0, qp1;
+    qp0 = qp1 = make_uint4(0, 0, 0, 0);
+    const uint8_t* crow = cbase + off;
+#pragma unroll
+    for (int t = 0; t < F; ++t) {
+      qc[t] = make_uint4(0, 0, 0, 0);
+      if (ld && t < nf) qc[t] = __ldg(reinterpret_cast<const uint4*>(crow + coff[t]));
+    }
+    if (ld) qp0 = __ldg(reinterpret_cast<const uint4*>(p0 + off));
+    if constexpr (F == 2) {
+      if (ld && nf > 1) qp1 = __ldg(reinterpret_cast<const uint4*>(p1 + off));
+    }
+    const int ye = y - 1, yo = y - 2;
+    const bool e_in = r >= 2 && col_in && ye >= 0 && ye < H;
+    const bool o_in = r >= 4 && yo < H;
+    const int sh = (r - 4 < 16) ? 0 : 16;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int ta = 2 * q, tb = 2 * q + 1;
+      const uint4 pa = ta == 0 ? qp0 : qc[ta - 1];
+      const uint4 pb = F == 2 ? qp1 : qc[ta];
+      const uint32_t b = ld ? (motion_bits16(qc[ta], pa, add4) | (motion_bits16(qc[tb], pb, add4) << 16))
+                            : 0xffffffffu;
+      const uint32_t bl = __shfl_up_sync(0xffffffffu, b, 1);
+      const uint32_t br = __shfl_down_sync(0xffffffffu, b, 1);
+      const uint32_t hrow = b & left_nb(b, bl) & right_nb(b, br);
+      const uint32_t e = e_in ? (hb2[q] & hb1[q] & hrow) : 0u;
+      hb2[q] = hb1[q];
+      hb1[q] = hrow;
+      const uint32_t el = __shfl_up_sync(0xffffffffu, e, 1);
+      const uint32_t er = __shfl_down_sync(0xffffffffu, e, 1);
+      const uint32_t drow = e | left_nb(e, el) | right_nb(e, er);
+      if (o_in) {
+        const uint32_t o = he2[q] | he1[q] | drow;
+        cn[ta] += (uint32_t)__popc(o & 0xffffu) << sh;
+        cn[tb] += (uint32_t)__popc(o >> 16) << sh;
+      }
+      he2[q] = he1[q];
+      he1[q] = drow;
+    }
+  }
+  // two tile rows per lane and frame
+  const int ty0 = 2 * strip;
+  const bool second = ty0 + 1 < a.tiles_y;
+#pragma unroll
+  for (int t = 0; t < F; ++t) {
+    if (t >= nf) break;
+    const uint64_t j = j0 + t;
+    uint16_t* cnt = a.counts + j * a.n_tiles;
+    const uint32_t lo = cn[t] & 0xffffu, hi = cn[t] >> 16;
+    if (owned) {
+      cnt[(size_t)ty0 * a.tiles_x + col] = (uint16_t)lo;
+      if (second) cnt[(size_t)(ty0 + 1) * a.tiles_x + col] = (uint16_t)hi;
+    }
+    const uint32_t nz = __popc(__ballot_sync(0xffffffffu, owned && lo)) +
+                        __popc(__ballot_sync(0xffffffffu, owned && second && hi));
+    if (lane == 0 && nz) atomicAdd(&a.frame_tot[j], nz);
+  }
+}
+
+template <int F>
+__global__ void __launch_bounds__(kMdWarpsPerCta * 32) k_md_main(MdArgs a) {
   const MdPlanHdr pl = *a.plan;
   const uint64_t n = pl.n_cand;
   if (n == 0) return;
-  const int W = a.W, H = a.H;
-  const int lane = threadIdx.x & 31;
-  const int cols = W / 16;                                    // tile columns
+  const int cols = a.W / 16;
   const int bands = (cols + kMdOwned - 1) / kMdOwned;
-  const int strips = (H + kMdRows - 1) / kMdRows;
+  const int strips = (a.H + kMdRows - 1) / kMdRows;
   const uint32_t pairs = (uint32_t)(strips * bands);
-  const uint32_t G = gridDim.x * kMdWarpsPerCta;              // workers
-  uint32_t chunks = G / pairs;
-  if (chunks < 1) chunks = 1;
-  if (chunks > n) chunks = (uint32_t)n;
-  const uint32_t units = pairs * chunks;
+  const uint64_t chunks = (n + F - 1) / F;
+  const uint64_t units = pairs * chunks;
+  const uint64_t G = (uint64_t)gridDim.x * kMdWarpsPerCta;
   const uint32_t add4 = 0x01010101u * (uint32_t)(127 - a.thr);
-  for (uint32_t u = blockIdx.x * kMdWarpsPerCta + (threadIdx.x >> 5); u < units; u += G) {
-    const uint32_t pair = u % pairs, chunk = u / pairs;
-    const int strip = (int)(pair / bands), band = (int)(pair % bands);
-    const uint64_t j0 = n * chunk / chunks, j1 = n * (chunk + 1) / chunks;
-    const int col = band * kMdOwned - 1 + lane;               // this lane's tile column
-    const bool col_in = col >= 0 && col < cols;
-    const bool owned = lane >= 1 && lane <= kMdOwned && col_in;
-    const int y0 = strip * kMdRows;
-    const size_t col_off = (size_t)(col_in ? col : 0) * 16;
-    for (uint64_t j = j0; j < j1; ++j) {
-      const uint8_t* cur = slot_ptr(a.cur, pl.rd_cur0 + j) + col_off;
-      const uint8_t* prv;
-      if (a.dedup && j >= 1) prv = slot_ptr(a.cur, pl.rd_cur0 + j - 1) + col_off;
-      else prv = slot_ptr(a.prev, pl.rd_prev0 + j) + col_off;
-      uint4 cb[kMdPre], pb[kMdPre];
-#pragma unroll
-      for (int r = 0; r < kMdPre; ++r) {
-        const int y = y0 - 2 + r;
-        if (col_in && y >= 0 && y < H) {
-          cb[r] = __ldg(reinterpret_cast<const uint4*>(cur + (size_t)y * W));
-          pb[r] = __ldg(reinterpret_cast<const uint4*>(prv + (size_t)y * W));
-        }
-      }
-      uint32_t hb1 = 0, hb2 = 0;        // horizontally eroded rows y-2, y-1
-      uint32_t he1 = 0, he2 = 0;        // horizontally dilated erosion rows
-      uint32_t cnt0 = 0, cnt1 = 0;      // tile counts of the two tile rows
-#pragma unroll 1
-      for (int rg = 0; rg < kMdWalk; rg += kMdPre) {
-#pragma unroll
-        for (int q = 0; q < kMdPre; ++q) {
-          const int r = rg + q;
-          const int y = y0 - 2 + r;
-          const bool row_in = y >= 0 && y < H;
-          uint32_t b = 0xffffu;                                  // outside: erosion border
-          if (col_in && row_in) b = motion_bits16(cb[q], pb[q], add4);
-          if (r + kMdPre < kMdWalk) {
-            const int yn = y + kMdPre;
-            if (col_in && yn >= 0 && yn < H) {
-              cb[q] = __ldg(reinterpret_cast<const uint4*>(cur + (size_t)yn * W));
-              pb[q] = __ldg(reinterpret_cast<const uint4*>(prv + (size_t)yn * W));
-            }
-          }
-          // horizontal erosion: x holds pixels -1..16 of this lane in bits 0..17
-          const uint32_t l = __shfl_up_sync(0xffffffffu, b, 1);
-          const uint32_t rr = __shfl_down_sync(0xffffffffu, b, 1);
-          const uint32_t x = ((rr & 1u) << 17) | (b << 1) | ((l >> 15) & 1u);
-          const uint32_t hb = x & (x >> 1) & (x >> 2) & 0xffffu;
-          // erosion of row y-1 (rows y-2, y-1, y); 0 outside the frame (dilation border)
-          const int ye = y - 1;
-          uint32_t e = 0;
-          if (r >= 2 && col_in && ye >= 0 && ye < H) e = hb2 & hb1 & hb;
-          hb2 = hb1;
-          hb1 = hb;
-          const uint32_t le = __shfl_up_sync(0xffffffffu, e, 1);
-          const uint32_t re = __shfl_down_sync(0xffffffffu, e, 1);
-          const uint32_t xe = ((re & 1u) << 17) | (e << 1) | ((le >> 15) & 1u);
-          const uint32_t he = (xe | (xe >> 1) | (xe >> 2)) & 0xffffu;
-          // dilation of row y-2 (erosion rows y-3, y-2, y-1), produced for r = 4 .. 35
-          const int yo = y - 2;
-          if (r >= 4 && yo < H) {
-            const uint32_t pc = __popc(he2 | he1 | he);
-            if (r - 4 < 16) cnt0 += pc;
-            else cnt1 += pc;
-          }
-          he2 = he1;
-          he1 = he;
-        }
-      }
-      // rows y0 .. y0+31 were produced at r = 4 .. 35
-      uint32_t nz = 0;
-      const int ty0 = 2 * strip;
-      if (owned) a.counts[j * a.n_tiles + (size_t)ty0 * a.tiles_x + col] = (uint16_t)cnt0;
-      nz += __popc(__ballot_sync(0xffffffffu, owned && cnt0 > 0));
-      if (ty0 + 1 < a.tiles_y) {
-        if (owned) a.counts[j * a.n_tiles + (size_t)(ty0 + 1) * a.tiles_x + col] = (uint16_t)cnt1;
-        nz += __popc(__ballot_sync(0xffffffffu, owned && cnt1 > 0));
-      }
-      if (lane == 0 && nz) atomicAdd(&a.frame_tot[j], nz);
-    }
+  const uint64_t slot_cur0 = pl.rd_cur0 % a.cur.cap, slot_prev0 = pl.rd_prev0 % a.prev.cap;
+  for (uint64_t u = blockIdx.x * (uint64_t)kMdWarpsPerCta + (threadIdx.x >> 5); u < units; u += G) {
+    const uint32_t pair = (uint32_t)(u % pairs);
+    const uint64_t chunk = u / pairs;
+    const uint64_t j0 = chunk * F;
+    const uint64_t left = n - j0;
+    const int nf = left < (uint64_t)F ? (int)left : F;
+    md_unit<F>(a, slot_cur0, slot_prev0, (int)(pair / bands), (int)(pair % bands), j0, nf, add4);
   }
 }
 
@@ -296,15 +339,18 @@ __global__ void __launch_bounds__(kMdThreads) k_md_scatter(MdArgs a) {
     *reinterpret_cast<uint32_t*>(slot_ptr(a.cnt, pl.wr_cnt0 + j)) = a.frame_tot[j];
 }
 
-static int g_md_blocks_per_sm = 0;
+static int g_md_blocks_per_sm[2] = {0, 0};
 
 cudaError_t md_prepare(int W) {
   (void)W;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_md_main,
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_md_main<kMdFrames>,
                                                                 kMdWarpsPerCta * 32, 0);
   if (e != cudaSuccess) return e;
-  g_md_blocks_per_sm = per_sm > 0 ? per_sm : 1;
+  g_md_blocks_per_sm[0] = per_sm > 0 ? per_sm : 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_md_main<2>, kMdWarpsPerCta * 32, 0);
+  if (e != cudaSuccess) return e;
+  g_md_blocks_per_sm[1] = per_sm > 0 ? per_sm : 1;
   return cudaSuccess;
 }
 
@@ -312,7 +358,10 @@ cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s, cudaEvent_
                            cudaEvent_t ev1) {
   k_md_plan<<<1, 256, 0, s>>>(a);
   if (ev0) cudaEventRecord(ev0, s);
-  k_md_main<<<n_sm * (g_md_blocks_per_sm ? g_md_blocks_per_sm : 8), kMdWarpsPerCta * 32, 0, s>>>(a);
+  if (a.shared_rows)
+    k_md_main<kMdFrames><<<n_sm * std::max(g_md_blocks_per_sm[0], 1), kMdWarpsPerCta * 32, 0, s>>>(a);
+  else
+    k_md_main<2><<<n_sm * std::max(g_md_blocks_per_sm[1], 1), kMdWarpsPerCta * 32, 0, s>>>(a);
   if (ev1) cudaEventRecord(ev1, s);
   k_md_finish<<<1, 256, 0, s>>>(a);
   k_md_scatter<<<a.n_max, kMdThreads, 0, s>>>(a);

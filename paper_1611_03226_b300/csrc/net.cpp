@@ -655,6 +655,7 @@ df_status df_net_finalize(df_net* net) {
       // current channel has no initial token and the previous channel one.
       m.dedup = (cur.src == prev.src && net->actors[cur.src].kind == DF_SOURCE &&
                  cur.init == 0 && prev.init == 1) ? 1 : 0;
+      m.shared_rows = (m.dedup && (uint64_t)cur.cap * cur.tok < (1ull << 31)) ? 1 : 0;
       m.n_max = std::min({cur.cap, prev.cap, net->chans[A.out[1]].cap});
       m.plan = reinterpret_cast<MdPlanHdr*>(base + q.plan.off);
       m.counts = reinterpret_cast<uint16_t*>(base + q.counts.off);
