@@ -76,7 +76,7 @@ struct DpdPlanHdr {
 };
 
 struct DpdArgs {            // one per predistorter actor, stored in device memory
-  ChanDesc ctrl, data, out;
+  ChanDesc ctrl, data, out;  // ctrl.ring == nullptr: static actor, every firing has mask 1
   uint64_t* ctr;
   EngineDev* eng;
   int K, M, MT;             // MT = padded tap count of the kernel instantiation
@@ -91,6 +91,36 @@ struct DpdArgs {            // one per predistorter actor, stored in device memo
   uint32_t* cnt;            // [K]: active firings of k this step
   float2* hist;             // [2][K][MT-1]: raw input samples preceding the batch
   uint32_t* parity;         // which half of hist is current
+};
+
+// --------------------------------------- bitmask-controlled dynamic actors ----
+// Poly (in 0 control, in 1 data -> out k = branch k) and Adder (in 0 control,
+// in k+1 = branch k -> out 0) of the expanded predistorter network.  Regular
+// port p is active in a firing iff bit[p] of its control token is set (bit -1:
+// always); an active port moves `rate` tokens.
+constexpr int kDynPorts = kMaxBranches + 1;
+
+struct DynPlanHdr {
+  uint64_t n;                     // firings this step
+  uint64_t base[kDynPorts];       // rd (inputs) / wr (outputs) of each port before the step
+};
+
+struct DynArgs {
+  ChanDesc ctrl;
+  ChanDesc port[kDynPorts];
+  int is_out[kDynPorts];
+  int bit[kDynPorts];
+  int np;                         // regular ports
+  int kind;                       // DF_DPD_POLY or DF_DPD_ADD
+  int K;
+  int orders[kMaxBranches];
+  uint32_t L;                     // samples per token
+  uint32_t n_max;
+  uint64_t* ctr;
+  EngineDev* eng;
+  DynPlanHdr* plan;
+  uint32_t* masks;                // [n_max]
+  uint32_t* rank;                 // [np][n_max] active firings of port p before firing i
 };
 
 // ----------------------------------------------------- motion detector ----
@@ -131,6 +161,8 @@ cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile
 int dpd_supported_mt(int M);   // padded tap count used for M (0 = unsupported)
 cudaError_t dpd_prepare();     // one-time kernel attributes (outside graph capture)
 
+cudaError_t launch_dyn(const DynArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                       cudaEvent_t ev1 = nullptr);
 cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                            cudaEvent_t ev1 = nullptr);
 cudaError_t md_prepare(int W);     // one-time kernel attributes (outside graph capture)

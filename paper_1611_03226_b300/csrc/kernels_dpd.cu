@@ -183,8 +183,10 @@ __global__ void __launch_bounds__(256) k_dpd_plan(const DpdArgs* args) {
   __shared__ uint32_t s_par;
   __shared__ uint64_t sw[32];
   uint64_t* ctr = a.ctr;
+  const bool has_ctrl = a.ctrl.ring != nullptr;
   if (threadIdx.x == 0) {
-    const uint64_t rdc = *rd_ptr(ctr, a.ctrl.id), wrc = *wr_ptr(ctr, a.ctrl.id);
+    const uint64_t rdc = has_ctrl ? *rd_ptr(ctr, a.ctrl.id) : 0;
+    const uint64_t wrc = has_ctrl ? *wr_ptr(ctr, a.ctrl.id) : ~0ull;
     const uint64_t rdd = *rd_ptr(ctr, a.data.id), wrd = *wr_ptr(ctr, a.data.id);
     const uint64_t wro = *wr_ptr(ctr, a.out.id), rdo = *rd_ptr(ctr, a.out.id);
     uint64_t n = wrc - rdc;
@@ -197,7 +199,8 @@ __global__ void __launch_bounds__(256) k_dpd_plan(const DpdArgs* args) {
   const uint32_t n = (uint32_t)s_n;
   const uint32_t kmask = a.K >= 32 ? 0xffffffffu : ((1u << a.K) - 1u);
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-    a.masks[i] = *reinterpret_cast<const uint32_t*>(slot_ptr(a.ctrl, s_rdc + i)) & kmask;
+    a.masks[i] = has_ctrl ? *reinterpret_cast<const uint32_t*>(slot_ptr(a.ctrl, s_rdc + i)) & kmask
+                          : kmask;
   __syncthreads();
   for (int k = 0; k < a.K; ++k) {
     uint64_t carry = 0;
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(256) k_dpd_plan(const DpdArgs* args) {
     a.plan->slot_out0 = s_wro % a.out.cap;
     a.plan->parity_in = s_par;
     if (n > 0) *a.parity = s_par ^ 1u;
-    *rd_ptr(ctr, a.ctrl.id) = s_rdc + n;
+    if (has_ctrl) *rd_ptr(ctr, a.ctrl.id) = s_rdc + n;
     *rd_ptr(ctr, a.data.id) = s_rdd + n;
     *wr_ptr(ctr, a.out.id) = s_wro + n;
     atomicAdd(&a.eng->fired_step, (unsigned long long)n);

@@ -40,12 +40,13 @@ struct ChanH {
   ChanDesc desc{};
 };
 
-enum OpKind { kOpCopy = 1, kOpDpd = 2, kOpMd = 3 };
+enum OpKind { kOpCopy = 1, kOpDpd = 2, kOpMd = 3, kOpDyn = 4 };
 
 struct Op {
   OpKind kind;
   CopyArgs copy{};
   MdArgs md{};
+  DynArgs dyn{};
   DpdArgs* dpd_dev = nullptr;        // group args (device)
   int dpd_n = 0;                      // actors in the group
   int dpd_first_actor = -1;           // actor id of the first member
@@ -171,10 +172,35 @@ df_status validate_actor(const df_net* net, int a) {
       if (n.tok != 4 || n.rate != 1) return DF_EINVAL;
       return DF_OK;
     }
-    case DF_DPD_POLY:
-    case DF_DPD_FIR:
-    case DF_DPD_ADD:
-      return DF_ENOTSUP;
+    case DF_DPD_POLY: {
+      const df_dpd_params& p = A.dpd;
+      const uint64_t blk = (uint64_t)p.block_len * 8;
+      if (A.in.size() != 2 || (int)A.out.size() != p.K) return DF_EINVAL;
+      if (ch(A.in[0]).tok != 4 || ch(A.in[0]).rate != 1) return DF_EINVAL;
+      if (ch(A.in[1]).tok != blk || ch(A.in[1]).rate != 1) return DF_EINVAL;
+      for (int32_t o : A.out)
+        if (ch(o).tok != blk || ch(o).rate != 1) return DF_EINVAL;
+      return DF_OK;
+    }
+    case DF_DPD_ADD: {
+      const df_dpd_params& p = A.dpd;
+      const uint64_t blk = (uint64_t)p.block_len * 8;
+      if ((int)A.in.size() != p.K + 1 || A.out.size() != 1) return DF_EINVAL;
+      if (ch(A.in[0]).tok != 4 || ch(A.in[0]).rate != 1) return DF_EINVAL;
+      for (size_t i = 1; i < A.in.size(); ++i)
+        if (ch(A.in[i]).tok != blk || ch(A.in[i]).rate != 1) return DF_EINVAL;
+      if (ch(A.out[0]).tok != blk || ch(A.out[0]).rate != 1) return DF_EINVAL;
+      return DF_OK;
+    }
+    case DF_DPD_FIR: {
+      const df_dpd_params& p = A.dpd;
+      const uint64_t blk = (uint64_t)p.block_len * 8;
+      if (A.in.size() != 1 || A.out.size() != 1) return DF_EINVAL;
+      if (p.branch < 0 || p.branch >= p.K) return DF_EINVAL;
+      if (ch(A.in[0]).tok != blk || ch(A.in[0]).rate != 1) return DF_EINVAL;
+      if (ch(A.out[0]).tok != blk || ch(A.out[0]).rate != 1) return DF_EINVAL;
+      return DF_OK;
+    }
     default:
       return DF_EINVAL;
   }
@@ -277,6 +303,9 @@ df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
         DF_CUDA(launch_md_step(op.md, net->n_sm, s, ev.first, ev.second));
         break;
       }
+      case kOpDyn:
+        DF_CUDA(launch_dyn(op.dyn, net->n_sm, s));
+        break;
       case kOpDpd: {
         const ActorH& A0 = net->actors[op.dpd_first_actor];
         uint32_t tile = A0.tile, threads = A0.threads;
@@ -481,21 +510,38 @@ df_status df_net_finalize(df_net* net) {
   std::vector<Piece> cp;
   net->dpd_index.assign(net->actors.size(), -1);
   std::vector<int> md_index(net->actors.size(), -1), copy_index(net->actors.size(), -1);
+  struct DynPieces { Piece plan, masks, rank; };
+  std::vector<DynPieces> yp;
+  std::vector<int> dyn_index(net->actors.size(), -1);
+  auto is_dpd_like = [](int kind) { return kind == DF_DPD || kind == DF_DPD_FIR; };
+  auto dpd_nmax = [&](const ActorH& A) {
+    if (A.kind == DF_DPD_FIR) return std::min(net->chans[A.in[0]].cap, net->chans[A.out[0]].cap);
+    return std::min({net->chans[A.in[0]].cap, net->chans[A.in[1]].cap, net->chans[A.out[0]].cap});
+  };
   for (int a = 0; a < (int)net->actors.size(); ++a) {
     const ActorH& A = net->actors[a];
-    if (A.kind == DF_DPD) {
+    if (A.kind == DF_DPD_POLY || A.kind == DF_DPD_ADD) {
+      const uint32_t nmax = net->chans[A.in[0]].cap;
+      DynPieces q;
+      q.plan = take(sizeof(DynPlanHdr));
+      q.masks = take(4ull * nmax);
+      q.rank = take(4ull * nmax * (A.dpd.K + 1));
+      dyn_index[a] = (int)yp.size();
+      yp.push_back(q);
+    }
+    if (is_dpd_like(A.kind)) {
+      const int K = A.kind == DF_DPD_FIR ? 1 : A.dpd.K;
       const int MT = dpd_supported_mt(A.dpd.M);
-      const uint32_t nmax = std::min({net->chans[A.in[0]].cap, net->chans[A.in[1]].cap,
-                                      net->chans[A.out[0]].cap});
+      const uint32_t nmax = dpd_nmax(A);
       DpdPieces q;
       q.plan = take(sizeof(DpdPlanHdr));
       q.masks = take(4ull * nmax);
-      q.rank = take(4ull * nmax * A.dpd.K);
-      q.act = take(4ull * nmax * A.dpd.K);
-      q.cnt = take(4ull * A.dpd.K);
-      q.hist = take(8ull * 2 * A.dpd.K * std::max(1, MT - 1));
+      q.rank = take(4ull * nmax * K);
+      q.act = take(4ull * nmax * K);
+      q.cnt = take(4ull * K);
+      q.hist = take(8ull * 2 * K * std::max(1, MT - 1));
       q.parity = take(4);
-      q.h = take(8ull * A.dpd.K * MT);
+      q.h = take(8ull * K * MT);
       net->dpd_index[a] = (int)dp.size();
       dp.push_back(q);
     } else if (A.kind == DF_MD) {
@@ -547,22 +593,29 @@ df_status df_net_finalize(df_net* net) {
   net->d_dpd = reinterpret_cast<DpdArgs*>(base + p_dpd_args.off);
   for (int a = 0; a < (int)net->actors.size(); ++a) {
     const ActorH& A = net->actors[a];
-    if (A.kind == DF_DPD) {
+    if (is_dpd_like(A.kind)) {
+      const bool fir = A.kind == DF_DPD_FIR;
       const int i = net->dpd_index[a];
       const DpdPieces& q = dp[i];
       DpdArgs& d = net->dpd_host[i];
-      d.ctrl = net->chans[A.in[0]].desc;
-      d.data = net->chans[A.in[1]].desc;
+      if (fir) {
+        d.ctrl = ChanDesc{};                 // static: every firing has mask 1
+        d.data = net->chans[A.in[0]].desc;
+      } else {
+        d.ctrl = net->chans[A.in[0]].desc;
+        d.data = net->chans[A.in[1]].desc;
+      }
       d.out = net->chans[A.out[0]].desc;
       d.ctr = net->d_ctr;
       d.eng = net->d_eng;
-      d.K = A.dpd.K;
+      d.K = fir ? 1 : A.dpd.K;
       d.M = A.dpd.M;
       d.MT = dpd_supported_mt(A.dpd.M);
       d.L = A.dpd.block_len;
-      d.n_max = std::min({net->chans[A.in[0]].cap, net->chans[A.in[1]].cap,
-                          net->chans[A.out[0]].cap});
-      for (int k = 0; k < A.dpd.K; ++k) d.orders[k] = A.dpd.orders[k];
+      d.n_max = dpd_nmax(A);
+      if (fir) d.orders[0] = 1;              // the branch signal arrives already formed
+      else
+        for (int k = 0; k < A.dpd.K; ++k) d.orders[k] = A.dpd.orders[k];
       d.plan = reinterpret_cast<DpdPlanHdr*>(base + q.plan.off);
       d.masks = reinterpret_cast<uint32_t*>(base + q.masks.off);
       d.rank = reinterpret_cast<uint32_t*>(base + q.rank.off);
@@ -573,10 +626,12 @@ df_status df_net_finalize(df_net* net) {
       float2* hd = reinterpret_cast<float2*>(base + q.h.off);
       d.h = hd;
       hpad[i].assign((size_t)d.K * d.MT, make_float2(0.f, 0.f));
-      for (int k = 0; k < d.K; ++k)
+      for (int k = 0; k < d.K; ++k) {
+        const size_t row = fir ? (size_t)A.dpd.branch : (size_t)k;
         for (int m = 0; m < d.M; ++m)
           hpad[i][(size_t)k * d.MT + m] =
-              make_float2(A.h[2 * ((size_t)k * d.M + m)], A.h[2 * ((size_t)k * d.M + m) + 1]);
+              make_float2(A.h[2 * (row * d.M + m)], A.h[2 * (row * d.M + m) + 1]);
+      }
       DF_CUDA(cudaMemcpyAsync(hd, hpad[i].data(), hpad[i].size() * sizeof(float2),
                               cudaMemcpyHostToDevice, s));
     }
@@ -604,8 +659,34 @@ df_status df_net_finalize(df_net* net) {
   };
   for (int a = 0; a < (int)net->actors.size(); ++a) {
     const ActorH& A = net->actors[a];
-    if (A.kind != DF_DPD) flush_group();
-    if (A.kind == DF_DPD) {
+    if (!is_dpd_like(A.kind)) flush_group();
+    if (A.kind == DF_DPD_POLY || A.kind == DF_DPD_ADD) {
+      Op op{};
+      op.kind = kOpDyn;
+      DynArgs& y = op.dyn;
+      const DynPieces& q = yp[dyn_index[a]];
+      const bool poly = A.kind == DF_DPD_POLY;
+      y.kind = A.kind;
+      y.K = A.dpd.K;
+      for (int k = 0; k < A.dpd.K; ++k) y.orders[k] = A.dpd.orders[k];
+      y.L = A.dpd.block_len;
+      y.ctrl = net->chans[A.in[0]].desc;
+      y.np = A.dpd.K + 1;
+      for (int p = 0; p < y.np; ++p) {
+        const bool always = poly ? p == 0 : p == A.dpd.K;
+        y.bit[p] = always ? -1 : (poly ? p - 1 : p);
+        y.is_out[p] = poly ? (p > 0) : (p == A.dpd.K);
+        const int32_t c = poly ? (p == 0 ? A.in[1] : A.out[p - 1]) : (p < A.dpd.K ? A.in[p + 1] : A.out[0]);
+        y.port[p] = net->chans[c].desc;
+      }
+      y.n_max = net->chans[A.in[0]].cap;
+      y.ctr = net->d_ctr;
+      y.eng = net->d_eng;
+      y.plan = reinterpret_cast<DynPlanHdr*>(base + q.plan.off);
+      y.masks = reinterpret_cast<uint32_t*>(base + q.masks.off);
+      y.rank = reinterpret_cast<uint32_t*>(base + q.rank.off);
+      net->program.push_back(op);
+    } else if (is_dpd_like(A.kind)) {
       bool ok = (int)group.size() < 1024;
       for (int b : group) ok = ok && !linked(a, b);
       if (!ok) flush_group();
@@ -667,7 +748,7 @@ df_status df_net_finalize(df_net* net) {
     }
   }
   flush_group();
-  if (!dp.empty()) DF_CUDA(dpd_prepare());
+  if (!dp.empty()) DF_CUDA(dpd_prepare());  // also covers branch FIR actors
   for (const Op& op : net->program)
     if (op.kind == kOpMd) DF_CUDA(md_prepare(op.md.W));
   DF_CUDA(cudaStreamSynchronize(s));
@@ -831,7 +912,7 @@ df_status df_channel_counters(df_net* net, int32_t ch, uint64_t* produced, uint6
 
 df_status df_dpd_set_tile(df_net* net, int32_t actor, uint32_t tile, uint32_t threads) {
   if (!net || actor < 0 || actor >= (int)net->actors.size()) return DF_EINVAL;
-  if (net->actors[actor].kind != DF_DPD) return DF_EINVAL;
+  if (net->actors[actor].kind != DF_DPD && net->actors[actor].kind != DF_DPD_FIR) return DF_EINVAL;
   if (tile || threads) {
     if (threads != 64 && threads != 128 && threads != 256) return DF_EINVAL;
     const uint32_t R = tile / threads;

@@ -44,3 +44,29 @@ def motion_fused(Net, height, width, capacity, rec_capacity=None, t=25, prev_ini
     ids["ch_cnt"] = net.connect(ids["md"], 1, ids["cnt"], 0, 4, 1, capacity)
     net.finalize()
     return net, ids
+
+
+def dpd_expanded(Net, h, orders, block_len, delay, capacity, branch_capacity=None):
+    """The Sec. 4.2 network on the engine: control source feeds Poly and Adder;
+    Poly -> FIR_k -> Adder; same actor and channel order as the oracle's builder."""
+    from paper_1611_03226_b300 import _lib as L
+    K = len(orders)
+    bc = capacity if branch_capacity is None else branch_capacity
+    blk = block_len * CPLX
+    net = Net()
+    ids = {}
+    ids["ctrl"] = net.add_source()
+    ids["data"] = net.add_source()
+    ids["poly"] = net.add_dpd(h, orders, block_len, kind=L.DF_DPD_POLY)
+    ids["fir"] = [net.add_dpd(h, orders, block_len, kind=L.DF_DPD_FIR, branch=k) for k in range(K)]
+    ids["add"] = net.add_dpd(h, orders, block_len, kind=L.DF_DPD_ADD)
+    ids["sink"] = net.add_sink()
+    net.connect(ids["ctrl"], 0, ids["poly"], 0, 4, 1, capacity)
+    net.connect(ids["ctrl"], 1, ids["add"], 0, 4, 1, capacity)
+    ids["ch_data"] = net.connect(ids["data"], 0, ids["poly"], 1, blk, 1, capacity, delay)
+    for k in range(K):
+        net.connect(ids["poly"], k, ids["fir"][k], 0, blk, 1, bc)
+        net.connect(ids["fir"][k], 0, ids["add"], k + 1, blk, 1, bc)
+    ids["ch_out"] = net.connect(ids["add"], 0, ids["sink"], 0, blk, 1, capacity)
+    net.finalize()
+    return net, ids

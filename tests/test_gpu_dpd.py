@@ -182,3 +182,43 @@ def test_stateless_forward_backward(Net):
         assert D.rel_l2(gh.cpu().numpy(), rh) <= 1e-3
         gx2, gh2 = G.dpd_backward(xt, ht, orders, gt)       # deterministic reduction
         assert torch.equal(gh, gh2) and torch.equal(gx, gx2)
+
+
+@pytest.mark.parametrize("L,M,K,d,bc", [(512, 10, 4, 1, 2), (3, 6, 3, 2, 1), (2000, 16, 8, 1, 3)])
+def test_expanded_network_step_by_step(Net, L, M, K, d, bc):
+    """The paper's Poly -> FIR_k -> Adder network with dynamic per-firing branch
+    rates: every channel's counters equal the oracle's after every step, and
+    the output stream matches within 1e-5 per block."""
+    rng = np.random.default_rng(L + K)
+    n = 10
+    orders = tuple(range(1, 2 * K, 2))
+    x = (rng.normal(0, .3, (n, L)) + 1j * rng.normal(0, .3, (n, L))).astype(np.complex64)
+    h = (rng.normal(0, .1, (K, M)) + 1j * rng.normal(0, .1, (K, M))).astype(np.complex64)
+    masks = rng.integers(0, 1 << K, n).astype(np.uint32)
+    cap = 4
+    onet, oi = ON.dpd_expanded(h, orders, L, d, cap, branch_capacity=bc)
+    enet, ei = EN.dpd_expanded(Net, h, orders, L, d, cap, branch_capacity=bc)
+    i = 0
+    yo, ye = [], []
+    for step in range(200):
+        free = min(onet.channels[0].free, onet.channels[1].free, onet.channels[oi["ch_data"]].free)
+        k = min(2, n - i, free)
+        if k > 0:
+            onet.push(oi["ctrl"], ON.as_tokens_ctrl(masks[i:i + k]))
+            onet.push(oi["data"], ON.as_tokens_blocks(x[i:i + k]))
+            enet.push(ei["ctrl"], np.ascontiguousarray(masks[i:i + k]))
+            enet.push(ei["data"], np.ascontiguousarray(x[i:i + k]))
+            i += k
+        fo, fe = onet.run(1), enet.run(1)
+        assert fo == fe, step
+        for c in range(len(onet.channels)):
+            assert onet.counters(c) == enet.counters(c), (step, c)
+        yo += onet.pop(oi["sink"])
+        ye.append(enet.pop(ei["sink"], dtype=np.complex64))
+        if i >= n and fo == 0:
+            break
+    enet.close()
+    yo = np.array(yo).reshape(-1, L)
+    ye = np.concatenate(ye).reshape(-1, L)
+    assert len(ye) == n
+    check_blocks(yo, ye)
