@@ -404,6 +404,197 @@ def bench_dpd_tiny(args, P, torch, pk):
             "note": "device time of the 10 engine steps that stream 64 blocks through capacity-8 FIFOs"}
 
 
+def bench_dpd_batch(args, P, torch, pk):
+    """256 independent channels (uneven lengths, taps and branch sets) with 16
+    resident blocks each; one engine step fires all of them."""
+    from paper_1611_03226_b300 import _lib as L
+    w = synth.dpd_batch()
+    C, nb = w.n_channels, w.blocks_per_channel
+    pairs = [(c, b) for c in range(C) for b in range(nb)]
+    blocks = gen_parallel(lambda i: w.block(*pairs[i]), len(pairs))
+    dev = [torch.from_numpy(np.stack(blocks[c * nb:(c + 1) * nb])).to("cuda") for c in range(C)]
+    del blocks
+    masks = [torch.full((nb,), int(w.masks[c]), dtype=torch.int32, device="cuda") for c in range(C)]
+    outs = [torch.empty_like(d) for d in dev]
+    net = P.Net(stream=torch.cuda.current_stream().cuda_stream)
+    ids = []
+    for c in range(C):
+        Lc = int(w.lengths[c])
+        d = {"ctrl": net.add_source(), "data": net.add_source(),
+             "dpd": net.add_dpd(w.h[c], w.orders, Lc), "sink": net.add_sink()}
+        net.connect(d["ctrl"], 0, d["dpd"], 0, 4, 1, nb)
+        net.connect(d["data"], 0, d["dpd"], 1, Lc * 8, 1, nb)
+        net.connect(d["dpd"], 0, d["sink"], 0, Lc * 8, 1, nb)
+        ids.append(d)
+    net.finalize()
+    stream = torch.cuda.current_stream()
+
+    def push_all():
+        for c in range(C):
+            net.push(ids[c]["ctrl"], masks[c])
+            net.push(ids[c]["data"], dev[c])
+
+    def pop_all():
+        for c in range(C):
+            net.pop(ids[c]["sink"], out=outs[c])
+
+    push_all()
+    assert net.autotune() == C * nb
+    pop_all()
+    tuned = net.get_tile(ids[0]["dpd"])
+
+    def timed(flags, steps):
+        ms = []
+        for i in range(args.warmup + steps):
+            push_all()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            net.run_async(1, flags)
+            e1.record(stream)
+            assert net.sync() >= 0
+            pop_all()
+            if i >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms)
+
+    steps = max(3, args.steps // 4)
+    t_graph = timed(L.DF_RUN_GRAPH, steps)
+    t_eager = timed(0, steps)
+    t_per = timed(L.DF_RUN_NO_BATCH, steps)
+    t_per_graph = timed(L.DF_RUN_NO_BATCH | L.DF_RUN_GRAPH, steps)
+    # kernel time of the batched body
+    push_all()
+    net.profile(True)
+    net.run(1)
+    body_ms, _ = net.profile_get(L.DF_PROF_DPD_BODY)
+    net.profile(False)
+    pop_all()
+    net.close()
+    samples = int(w.lengths.sum()) * nb
+    flops = float(sum(8 * int(w.taps[c]) * int(w.lengths[c]) * nb * bin(int(w.masks[c])).count("1")
+                      for c in range(C)))
+    peak_tf = 148 * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    ach = flops / (body_ms / 1e3) / 1e12
+    # oracle on the first four channels
+    from oracle import nets as ON
+    t0 = time.perf_counter()
+    n_cpu = 0
+    for c in range(4):
+        onet, oi = ON.dpd_fused(w.h[c], w.orders, int(w.lengths[c]), 0, nb)
+        onet.push(oi["ctrl"], ON.as_tokens_ctrl([int(w.masks[c])] * nb))
+        onet.push(oi["data"], ON.as_tokens_blocks([w.block(c, b) for b in range(nb)]))
+        onet.run(-1)
+        n_cpu += int(w.lengths[c]) * nb
+    cpu_s = time.perf_counter() - t0
+    return {
+        "workload": f"dpd_batch_{C}ch_x{nb}blocks", "value": samples / (t_graph / 1e3) / 1e6,
+        "unit": "Msamples/s", "ms_per_step": t_graph, "dtype": "f32", "samples_per_step": samples,
+        "launch_modes_ms": {"batched_graph": t_graph, "batched_eager": t_eager,
+                            "per_channel_eager": t_per, "per_channel_graph": t_per_graph},
+        "batched_vs_per_channel": t_per / t_graph,
+        "autotuned_tile": {"samples": tuned[0], "threads": tuned[1]},
+        "gpu_launches_per_step": {"batched": 3, "per_channel": 1 + 2 * C},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": ach / peak_tf, "traffic": None, "kernel": "k_dpd_body",
+                     "algorithmic_flops_per_launch": flops},
+        "cpu_baseline": {"value": n_cpu / cpu_s / 1e6, "unit": "Msamples/s", "cores": 1,
+                         "kind": "oracle", "sample": "channels 0-3, 16 blocks each"},
+    }
+
+
+def bench_dpd_fit(args, P, torch, pk):
+    """Indirect-learning fit: 2^18 samples, 4 branches x 10 taps, 200 Adam steps."""
+    from paper_1611_03226_b300 import dpd as G
+    from paper_1611_03226_b300 import fit as F
+    w = synth.dpd_fit()
+    x = torch.from_numpy(w.x).to("cuda")
+    n = x.numel()
+    stream = torch.cuda.current_stream()
+    F.ila_fit(x, steps=3)                                   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h, losses = F.ila_fit(x, steps=w.steps, lr=w.lr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fit = e0.elapsed_time(e1)
+    gain = F.small_signal_gain()
+    nmse_off = F.nmse_db(F.saleh_pa(x) / gain, x)
+    nmse_on = F.nmse_db(F.saleh_pa(G.dpd_forward(x, h, w.orders)) / gain, x)
+    # forward and adjoint kernels alone
+    u = (F.saleh_pa(x) / gain).to(torch.complex64).contiguous()
+    gy = torch.randn_like(u)
+
+    def avg(fn, reps=20):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    fwd_ms = avg(lambda: G.dpd_forward(u, h, w.orders))
+    bwd_ms = avg(lambda: G.dpd_backward(u, h, w.orders, gy))
+    # the same forward through a one-block engine network (all branches active)
+    net = P.Net(stream=stream.cuda_stream)
+    c, d = net.add_source(), net.add_source()
+    a = net.add_dpd(h.cpu().numpy(), w.orders, n)
+    s = net.add_sink()
+    net.connect(c, 0, a, 0, 4, 1, 1)
+    net.connect(d, 0, a, 1, n * 8, 1, 1)
+    net.connect(a, 0, s, 0, n * 8, 1, 1)
+    net.finalize()
+    mask = torch.full((1,), 15, dtype=torch.int32, device="cuda")
+    out = torch.empty_like(u)
+
+    def engine_fwd():
+        net.push(c, mask)
+        net.push(d, u)
+        net.run_async(1)
+        net.sync()
+        net.pop(s, out=out)
+
+    eng_ms = []
+    for i in range(6):
+        net.push(c, mask)
+        net.push(d, u)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        net.run_async(1)
+        a1.record(stream)
+        net.sync()
+        net.pop(s, out=out)
+        if i >= 2:
+            eng_ms.append(a0.elapsed_time(a1))
+    engine_ms = statistics.mean(eng_ms)
+    # the network continues each branch's FIR history across blocks; the
+    # stateless operator starts from zeros, so compare past the first M-1 samples
+    ref = G.dpd_forward(u, h, w.orders)
+    m0 = w.n_taps - 1
+    err = float((out[m0:] - ref[m0:]).abs().norm() / ref[m0:].abs().norm())
+    net.close()
+    # oracle: 10 float64 steps on the same signal
+    from oracle import fit as OF
+    t0 = time.perf_counter()
+    OF.ila_fit(w.x, steps=10, lr=w.lr)
+    cpu_ms = (time.perf_counter() - t0) / 10 * 1e3
+    return {
+        "workload": f"dpd_fit_{n}_K4_M10_{w.steps}steps", "value": ms_fit / w.steps,
+        "unit": "ms/Adam step", "higher_is_better": False, "dtype": "f32",
+        "fwd_bwd_msamples_s": n / ((fwd_ms + bwd_ms) / 1e3) / 1e6,
+        "kernel_ms": {"forward": fwd_ms, "backward": bwd_ms},
+        "loss_first_last": [float(losses[0]), float(losses[-1])],
+        "nmse_db": {"without_dpd": nmse_off, "with_dpd": nmse_on},
+        "engine_network_forward_ms": engine_ms, "engine_vs_stateless_rel_l2": err,
+        "cpu_baseline": {"value": cpu_ms, "unit": "ms/Adam step", "cores": 1, "kind": "oracle",
+                         "sample": "10 float64 steps of the 2^18-sample fit"},
+    }
+
+
 # --------------------------------------------------------------- arms ----
 def gpu_arm(args):
     import torch
@@ -430,6 +621,9 @@ def gpu_arm(args):
             extra["dpd_large"] = dl
             if ws == 1:
                 extra["dpd_tiny"] = bench_dpd_tiny(args, P, torch, pk)
+                if not args.quick:
+                    extra["dpd_batch"] = bench_dpd_batch(args, P, torch, pk)
+                extra["dpd_fit"] = bench_dpd_fit(args, P, torch, pk)
     clocks = sampler.stop() if rank == 0 else None
     if rank != 0:
         return

@@ -185,6 +185,10 @@ df_status df_dpd_set_tile(df_net *net, int32_t actor, uint32_t tile, uint32_t th
  * for every DF_DPD actor / group.  Runs one step; returns its firings. */
 df_status df_autotune(df_net *net, uint64_t *n_firings);
 
+/* The tile configuration an actor (the first actor of a batched group) uses;
+ * 0/0 = the default. */
+df_status df_dpd_get_tile(df_net *net, int32_t actor, uint32_t *tile, uint32_t *threads);
+
 /* Kernel timing.  While enabled, every non-graph step records CUDA events on
  * the network's stream around the kernels named below; df_profile_get waits
  * for the stream and returns their summed device time (ms) and launch count

@@ -1,0 +1,44 @@
+"""Indirect-learning fit in float64 (oracle; test infrastructure).
+
+Same procedure as the engine's fit: postdistorter P trained so that
+P(y/G) ~ x (y = PA(x), G = small-signal gain), loss mean |P(y/G) - x|^2,
+Adam from the identity.  Gradients come from the float64 adjoint
+(dpd.dpd_stream_backward); Adam acts on the real and imaginary parts as
+separate real parameters (bias-corrected first and second moments).
+Parity unpinned: there is no paper value for the fit outcome; the tests
+compare the engine's loss curve with this one.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import dpd as D
+from . import pa as PA
+
+
+def ila_fit(x, orders=(1, 3, 5, 7), M=10, steps=200, lr=1e-3, betas=(0.9, 0.999), eps=1e-8,
+            saleh=(2.1587, 1.1517, 4.0033, 9.1040), memory=(1.0, 0.1, -0.05)):
+    x = np.asarray(x, np.complex128)
+    K = len(orders)
+    G = PA.small_signal_gain(saleh, memory)
+    u = PA.pa(x, saleh, memory) / G
+    h = np.zeros((K, M), np.complex128)
+    h[0, 0] = 1
+    m = np.zeros((K, M, 2))
+    v = np.zeros((K, M, 2))
+    losses = []
+    N = len(x)
+    for t in range(1, steps + 1):
+        out = D.dpd_stream(u, h, orders)
+        r = out - x
+        losses.append(float(np.mean(r.real ** 2 + r.imag ** 2)))
+        g = 2.0 * r / N                          # dL/dRe(out) + i dL/dIm(out)
+        _, gh = D.dpd_stream_backward(u, h, orders, g)
+        gr = np.stack([gh.real, gh.imag], axis=-1)
+        m = betas[0] * m + (1 - betas[0]) * gr
+        v = betas[1] * v + (1 - betas[1]) * gr * gr
+        mh = m / (1 - betas[0] ** t)
+        vh = v / (1 - betas[1] ** t)
+        step = lr * mh / (np.sqrt(vh) + eps)
+        h = h - (step[..., 0] + 1j * step[..., 1])
+    return h, np.array(losses)

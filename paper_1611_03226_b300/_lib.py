@@ -54,6 +54,7 @@ _PROTOS = {
                                         C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "df_dpd_set_tile": (C.c_int32, [_P, C.c_int32, C.c_uint32, C.c_uint32]),
     "df_autotune": (C.c_int32, [_P, C.POINTER(C.c_uint64)]),
+    "df_dpd_get_tile": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "df_status_str": (C.c_char_p, [C.c_int32]),
     "df_last_error": (C.c_char_p, []),
     "df_profile_enable": (C.c_int32, [_P, C.c_int32]),

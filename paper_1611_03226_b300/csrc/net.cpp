@@ -659,6 +659,8 @@ df_status df_net_finalize(df_net* net) {
   };
   for (int a = 0; a < (int)net->actors.size(); ++a) {
     const ActorH& A = net->actors[a];
+    // host endpoints never fire inside a step, so they do not split a group
+    if (A.kind == DF_SOURCE || A.kind == DF_SINK) continue;
     if (!is_dpd_like(A.kind)) flush_group();
     if (A.kind == DF_DPD_POLY || A.kind == DF_DPD_ADD) {
       Op op{};
@@ -949,9 +951,81 @@ df_status df_profile_get(df_net* net, int32_t what, double* total_ms, uint64_t* 
 }
 
 df_status df_autotune(df_net* net, uint64_t* n_firings) {
-  (void)net;
-  (void)n_firings;
-  return DF_ENOTSUP;
+  if (!net) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  DeviceGuard g(net->device);
+  cudaStream_t s = net->stream;
+  static const uint32_t kCand[][2] = {{512, 64},   {1024, 128}, {2048, 256}, {1024, 64},
+                                      {2048, 128}, {4096, 256}};
+  uint64_t before = 0;
+  DF_CUDA(cudaStreamSynchronize(s));
+  DF_CUDA(cudaMemcpy(&before, &net->d_eng->fired_total, 8, cudaMemcpyDeviceToHost));
+  cudaEvent_t e0, e1;
+  DF_CUDA(cudaEventCreate(&e0));
+  DF_CUDA(cudaEventCreate(&e1));
+  df_status st = DF_OK;
+  DF_CUDA(launch_step_begin(net->d_eng, s));
+  for (const Op& op : net->program) {
+    if (op.kind == kOpCopy) {
+      DF_CUDA(launch_copy(op.copy, net->n_sm, s));
+    } else if (op.kind == kOpMd) {
+      DF_CUDA(launch_md_step(op.md, net->n_sm, s));
+    } else if (op.kind == kOpDyn) {
+      DF_CUDA(launch_dyn(op.dyn, net->n_sm, s));
+    } else {
+      // one plan, then the (idempotent) body once per candidate; keep the fastest
+      DF_CUDA(launch_dpd_plan(op.dpd_dev, op.dpd_n, s));
+      float best = 1e30f;
+      uint32_t bt = 0, bth = 0;
+      for (const auto& c : kCand) {
+        for (int rep = 0; rep < 2; ++rep) {
+          DF_CUDA(cudaEventRecord(e0, s));
+          const cudaError_t le =
+              launch_dpd_body(op.dpd_dev, op.dpd_n, c[0], c[1], op.max_mt, net->n_sm, s);
+          if (le != cudaSuccess) {
+            cudaGetLastError();            // configuration does not fit: skip it
+            break;
+          }
+          DF_CUDA(cudaEventRecord(e1, s));
+          DF_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          DF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep == 1 && ms < best) {     // second run: warm caches and clocks
+            best = ms;
+            bt = c[0];
+            bth = c[1];
+          }
+        }
+      }
+      if (bt) {
+        DF_CUDA(launch_dpd_body(op.dpd_dev, op.dpd_n, bt, bth, op.max_mt, net->n_sm, s));
+        net->actors[op.dpd_first_actor].tile = bt;
+        net->actors[op.dpd_first_actor].threads = bth;
+      } else {
+        st = DF_ENOTSUP;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (auto& kv : net->graphs) cudaGraphExecDestroy(kv.second);
+  net->graphs.clear();
+  if (st != DF_OK) return st;
+  st = fail_if_device_error(net);
+  if (st != DF_OK) return st;
+  if (n_firings) {
+    uint64_t after = 0;
+    DF_CUDA(cudaMemcpy(&after, &net->d_eng->fired_total, 8, cudaMemcpyDeviceToHost));
+    *n_firings = after - before;
+  }
+  return DF_OK;
+}
+
+df_status df_dpd_get_tile(df_net* net, int32_t actor, uint32_t* tile, uint32_t* threads) {
+  if (!net || actor < 0 || actor >= (int)net->actors.size()) return DF_EINVAL;
+  if (tile) *tile = net->actors[actor].tile;
+  if (threads) *threads = net->actors[actor].threads;
+  return DF_OK;
 }
 
 df_status df_dpd_forward(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,

@@ -1,0 +1,64 @@
+"""Indirect-learning fit of a predistorter to a power amplifier (torch plumbing
+around the CUDA predistorter and its adjoint).
+
+The amplifier is a Saleh model (AM/AM alpha_a r / (1 + beta_a r^2), AM/PM
+alpha_p r^2 / (1 + beta_p r^2)) followed by a 3-tap memory FIR.  Indirect
+learning: the postdistorter P is trained so that P(y / G) ~ x, where y is the
+amplifier output for input x and G = alpha_a * sum(memory taps) its
+small-signal gain; the trained P is then used as the predistorter.  The loss
+is mean |P(y/G) - x|^2 over the whole signal, minimised with Adam starting
+from the identity (h[0,0] = 1).  P's forward and gradient run in the
+engine's kernels (DPDFunction); everything else is plain torch.
+"""
+from __future__ import annotations
+
+import torch
+
+from .dpd import dpd
+
+
+def saleh_pa(x: torch.Tensor, saleh=(2.1587, 1.1517, 4.0033, 9.1040),
+             memory=(1.0, 0.1, -0.05)) -> torch.Tensor:
+    aa, ba, ap, bp = saleh
+    r = x.abs()
+    r2 = r * r
+    amp = aa * r / (1 + ba * r2)
+    phase = torch.angle(x) + ap * r2 / (1 + bp * r2)
+    v = torch.polar(amp, phase)
+    y = torch.zeros_like(v)
+    for i, c in enumerate(memory):
+        if i == 0:
+            y += c * v
+        else:
+            y[i:] += c * v[:-i]
+    return y
+
+
+def small_signal_gain(saleh=(2.1587, 1.1517, 4.0033, 9.1040), memory=(1.0, 0.1, -0.05)) -> float:
+    return saleh[0] * float(sum(memory))
+
+
+def nmse_db(a: torch.Tensor, ref: torch.Tensor) -> float:
+    num = (a - ref).abs().pow(2).sum()
+    den = ref.abs().pow(2).sum()
+    return float(10 * torch.log10(num / den))
+
+
+def ila_fit(x: torch.Tensor, K=4, M=10, orders=(1, 3, 5, 7), steps=200, lr=1e-3,
+            saleh=(2.1587, 1.1517, 4.0033, 9.1040), memory=(1.0, 0.1, -0.05)):
+    """Returns (h, losses) for complex64 CUDA input x."""
+    G = small_signal_gain(saleh, memory)
+    u = (saleh_pa(x, saleh, memory) / G).to(torch.complex64).contiguous()
+    h = torch.zeros((K, M), dtype=torch.complex64, device=x.device)
+    h[0, 0] = 1
+    h.requires_grad_(True)
+    opt = torch.optim.Adam([h], lr=lr)
+    losses = []
+    for _ in range(steps):
+        opt.zero_grad(set_to_none=True)
+        out = dpd(u, h, orders)
+        loss = (out - x).abs().pow(2).mean()
+        loss.backward()
+        opt.step()
+        losses.append(loss.detach())
+    return h.detach(), torch.stack(losses).cpu().numpy()

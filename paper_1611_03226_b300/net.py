@@ -166,5 +166,15 @@ class Net:
         L.check(L.lib.df_profile_get(self.h, what, C.byref(ms), C.byref(n)), "df_profile_get")
         return ms.value, n.value
 
+    def autotune(self):
+        n = C.c_uint64()
+        L.check(L.lib.df_autotune(self.h, C.byref(n)), "df_autotune")
+        return n.value
+
+    def get_tile(self, actor):
+        t, th = C.c_uint32(), C.c_uint32()
+        L.check(L.lib.df_dpd_get_tile(self.h, actor, C.byref(t), C.byref(th)), "df_dpd_get_tile")
+        return t.value, th.value
+
     def set_tile(self, actor, tile, threads):
         L.check(L.lib.df_dpd_set_tile(self.h, actor, tile, threads), "df_dpd_set_tile")

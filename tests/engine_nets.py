@@ -70,3 +70,23 @@ def dpd_expanded(Net, h, orders, block_len, delay, capacity, branch_capacity=Non
     ids["ch_out"] = net.connect(ids["add"], 0, ids["sink"], 0, blk, 1, capacity)
     net.finalize()
     return net, ids
+
+
+def dpd_batch(Net, chans, capacity, stream=None):
+    """Independent predistorter channels in one network.  chans: list of
+    (h, orders, block_len).  Returns (net, per-channel dict of ids)."""
+    net = Net(stream=stream)
+    ids = []
+    for (h, orders, L) in chans:
+        d = {}
+        d["ctrl"] = net.add_source()
+        d["data"] = net.add_source()
+        d["dpd"] = net.add_dpd(h, orders, L)
+        d["sink"] = net.add_sink()
+        blk = L * CPLX
+        net.connect(d["ctrl"], 0, d["dpd"], 0, 4, 1, capacity)
+        net.connect(d["data"], 0, d["dpd"], 1, blk, 1, capacity)
+        net.connect(d["dpd"], 0, d["sink"], 0, blk, 1, capacity)
+        ids.append(d)
+    net.finalize()
+    return net, ids

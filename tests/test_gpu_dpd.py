@@ -222,3 +222,52 @@ def test_expanded_network_step_by_step(Net, L, M, K, d, bc):
     ye = np.concatenate(ye).reshape(-1, L)
     assert len(ye) == n
     check_blocks(yo, ye)
+
+
+def test_batched_channels_match_oracle_and_per_channel_launches(Net):
+    """Uneven channels in one network: the batched launch, one launch per
+    channel, a CUDA-graph replay and the autotuned configuration all give each
+    channel's oracle output."""
+    from paper_1611_03226_b300 import _lib as L
+    rng = np.random.default_rng(77)
+    C, nb = 12, 3
+    orders = tuple(range(1, 16, 2))
+    chans, data, masks = [], [], []
+    for c in range(C):
+        Lc = int(rng.integers(700, 5000))
+        M = int(rng.integers(8, 17))
+        h = (rng.normal(0, .1, (8, M)) + 1j * rng.normal(0, .1, (8, M))).astype(np.complex64)
+        chans.append((h, orders, Lc))
+        data.append((rng.normal(0, .3, (nb, Lc)) + 1j * rng.normal(0, .3, (nb, Lc))).astype(np.complex64))
+        masks.append(np.full(nb, int(rng.integers(1, 256)), np.uint32))
+    want = []
+    for c in range(C):
+        onet, oi = ON.dpd_fused(chans[c][0], orders, chans[c][2], 0, nb)
+        onet.push(oi["ctrl"], ON.as_tokens_ctrl(masks[c]))
+        onet.push(oi["data"], ON.as_tokens_blocks(data[c]))
+        onet.run(-1)
+        want.append(np.array(onet.pop(oi["sink"])))
+
+    def run_once(flags, tune=False):
+        net, ids = EN.dpd_batch(Net, chans, nb)
+        for c in range(C):
+            net.push(ids[c]["ctrl"], masks[c])
+            net.push(ids[c]["data"], data[c])
+        if tune:
+            assert net.autotune() == C * nb
+            t = net.get_tile(ids[0]["dpd"])
+            assert t[0] > 0 and t[1] > 0
+        else:
+            assert net.run(1, flags) == C * nb
+        outs = [net.pop(ids[c]["sink"], dtype=np.complex64).reshape(nb, -1) for c in range(C)]
+        net.close()
+        return outs
+
+    variants = {"batched": run_once(0), "per_channel": run_once(L.DF_RUN_NO_BATCH),
+                "graph": run_once(L.DF_RUN_GRAPH), "autotuned": run_once(0, tune=True)}
+    for name, outs in variants.items():
+        for c in range(C):
+            check_blocks(want[c], outs[c])
+    for c in range(C):
+        np.testing.assert_array_equal(variants["batched"][c], variants["per_channel"][c])
+        np.testing.assert_array_equal(variants["batched"][c], variants["graph"][c])

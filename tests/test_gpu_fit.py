@@ -1,0 +1,48 @@
+"""The differentiable predistorter: torch.autograd.gradcheck of DPDFunction and
+the indirect-learning fit against the float64 oracle fit."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fit as OF
+from oracle import pa as OPA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.filterwarnings("ignore:Input #")
+def test_gradcheck_small():
+    """The kernels are float32, so finite differences use a large step and loose tolerances."""
+    import torch
+    from paper_1611_03226_b300.dpd import dpd
+    rng = np.random.default_rng(3)
+    n, K, M = 64, 3, 5
+    x = torch.tensor((rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n)).astype(np.complex64),
+                     device="cuda", requires_grad=True)
+    h = torch.tensor((rng.normal(0, .2, (K, M)) + 1j * rng.normal(0, .2, (K, M))).astype(np.complex64),
+                     device="cuda", requires_grad=True)
+    f = lambda a, b: dpd(a, b, (1, 3, 5))
+    assert torch.autograd.gradcheck(f, (x, h), eps=2e-3, atol=2e-2, rtol=2e-2, nondet_tol=0.0)
+
+
+def test_pa_model_matches_oracle():
+    import torch
+    from paper_1611_03226_b300 import fit as F
+    w = synth.dpd_fit(n=4096)
+    y = F.saleh_pa(torch.from_numpy(w.x).cuda()).cpu().numpy()
+    ref = OPA.pa(w.x)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_ila_fit_tracks_float64_oracle():
+    """40 Adam steps on 2^14 samples: the engine's loss curve follows the
+    float64 oracle's within 1e-3 relative, and the fit improves the PA."""
+    import torch
+    from paper_1611_03226_b300 import fit as F
+    w = synth.dpd_fit(n=1 << 14)
+    steps = 40
+    h, losses = F.ila_fit(torch.from_numpy(w.x).cuda(), steps=steps, lr=1e-3)
+    h64, losses64 = OF.ila_fit(w.x, steps=steps, lr=1e-3)
+    assert np.max(np.abs(losses - losses64) / losses64) < 1e-3
+    assert losses[-1] < 0.9 * losses[0]
+    assert np.linalg.norm(h.cpu().numpy() - h64) / np.linalg.norm(h64) < 1e-3
