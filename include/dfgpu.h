@@ -157,7 +157,9 @@ df_status df_run(df_net *net, int64_t n_steps, uint64_t *n_firings);
 enum {
     DF_RUN_ASYNC = 1,        /* enqueue only (n_steps >= 0); no host sync, no firing count */
     DF_RUN_GRAPH = 2,        /* replay a CUDA graph of n_steps steps (captured once per n) */
-    DF_RUN_PERSISTENT = 4,   /* one persistent cooperative kernel runs all steps */
+    DF_RUN_PERSISTENT = 4,   /* one cooperative persistent kernel runs all steps (for n_steps < 0
+                                also the quiescence check); phases are separated by a grid
+                                barrier bounded by the wait limit (df_set_wait_limit) */
     DF_RUN_NO_BATCH = 8      /* one launch per predistorter actor instead of one per group */
 };
 df_status df_run_ex(df_net *net, int64_t n_steps, uint32_t flags, uint64_t *n_firings);
@@ -201,6 +203,17 @@ enum {
 };
 df_status df_profile_enable(df_net *net, int32_t on);
 df_status df_profile_get(df_net *net, int32_t what, double *total_ms, uint64_t *launches);
+
+/* Upper bound, in nanoseconds, of every device-side wait of the network (the
+ * persistent kernel's grid barrier); default one second.  A wait that runs out
+ * records DF_ETIMEOUT in the status word and the kernel returns. */
+df_status df_set_wait_limit(df_net *net, int64_t limit_ns);
+
+/* Self-test of the bounded waits: runs a grid barrier that waits for one more
+ * CTA than it has, so it can only end by its limit.  Returns the status word
+ * that run left (DF_ETIMEOUT when the bound works), then clears it so the
+ * network stays usable. */
+df_status df_selftest_wait_timeout(df_net *net, int64_t limit_ns);
 
 /* Text for a status code (static storage). */
 const char *df_status_str(df_status s);

@@ -56,6 +56,8 @@ _PROTOS = {
     "df_autotune": (C.c_int32, [_P, C.POINTER(C.c_uint64)]),
     "df_dpd_get_tile": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "df_status_str": (C.c_char_p, [C.c_int32]),
+    "df_set_wait_limit": (C.c_int32, [_P, C.c_int64]),
+    "df_selftest_wait_timeout": (C.c_int32, [_P, C.c_int64]),
     "df_last_error": (C.c_char_p, []),
     "df_profile_enable": (C.c_int32, [_P, C.c_int32]),
     "df_profile_get": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),

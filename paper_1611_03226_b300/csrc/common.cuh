@@ -35,6 +35,12 @@ struct EngineDev {          // device-resident engine state
 // where-codes for EngineDev::status_where
 enum : int32_t { kWhereMdPipe = 1, kWhereGridBarrier = 2, kWhereDpd = 3 };
 
+// Virtual grid: block index and block count of a phase (the launch's own grid
+// for the per-phase kernels, the persistent kernel's grid otherwise).
+struct Grid {
+  uint32_t b, n;
+};
+
 __host__ __device__ inline uint64_t* wr_ptr(uint64_t* ctr, uint32_t ch) { return ctr + 2 * ch; }
 __host__ __device__ inline uint64_t* rd_ptr(uint64_t* ctr, uint32_t ch) { return ctr + 2 * ch + 1; }
 
@@ -148,6 +154,16 @@ struct MdArgs {
   long long wait_limit_ns;  // bound of every device-side wait
 };
 
+// ------------------------------------------------ persistent step kernel ----
+constexpr int kPersistThreads = 256;
+enum : int { kPersistCopy = 1, kPersistDpd = 2, kPersistDyn = 3, kPersistMd = 4 };
+
+struct PersistOp {            // one entry of the device-side step program
+  int kind;
+  int n;                      // predistorter group size
+  const void* args;           // CopyArgs / DpdArgs[n] / DynArgs / MdArgs in device memory
+};
+
 // ----------------------------------------------------------- launchers ----
 cudaError_t launch_set_u64(uint64_t* p, uint64_t v, cudaStream_t s);
 cudaError_t launch_add_u64(uint64_t* p, uint64_t v, cudaStream_t s);
@@ -167,6 +183,12 @@ cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s, cudaEvent_
                            cudaEvent_t ev1 = nullptr);
 cudaError_t md_prepare(int W);     // one-time kernel attributes (outside graph capture)
 size_t md_smem_bytes(int W);
+
+cudaError_t persistent_prepare(size_t smem);
+size_t persistent_smem(int mtmax, int max_group);
+cudaError_t launch_persistent(const PersistOp* ops, int n_ops, EngineDev* eng, int64_t n_steps,
+                              long long limit_ns, int mtmax, size_t smem, int n_sm, cudaStream_t s);
+cudaError_t launch_barrier_selftest(EngineDev* eng, long long limit_ns, cudaStream_t s);
 
 cudaError_t dpd_forward_stateless(const float2* x, uint64_t n, const float2* h, int K, int M,
                                   const int* orders, float2* y, cudaStream_t s);

@@ -1,12 +1,5 @@
-// Counter maintenance and the static copy actor.
-//
-// Copy actor (a static actor in the sense of Sec. 2.2): each firing consumes
-// r_in tokens from its input and writes the same bytes, re-cut into r_out
-// tokens, to every output.  Its plan is one thread: the number of firings is
-// the largest n with n*r_in tokens present and n*r_out free slots on every
-// output.  The plan commits the counters immediately; the body then moves the
-// bytes of the n firings, wrapping around both rings.
-#include "common.cuh"
+// Counter maintenance and the launchers of the copy actor.
+#include "core_dev.cuh"
 
 namespace dfg {
 
@@ -27,58 +20,8 @@ cudaError_t launch_step_begin(EngineDev* e, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-__global__ void k_copy_plan(CopyArgs a) {
-  uint64_t* ctr = a.ctr;
-  uint64_t rd = *rd_ptr(ctr, a.in.id), wr_in = *wr_ptr(ctr, a.in.id);
-  uint64_t n = (wr_in - rd) / a.in.rate;
-  for (int p = 0; p < a.n_out; ++p) {
-    const ChanDesc& o = a.out[p];
-    uint64_t occ = *wr_ptr(ctr, o.id) - *rd_ptr(ctr, o.id);
-    uint64_t f = (o.cap - occ) / o.rate;
-    n = f < n ? f : n;
-  }
-  a.plan->n = n;
-  a.plan->rd0 = rd;
-  *rd_ptr(ctr, a.in.id) = rd + n * a.in.rate;
-  for (int p = 0; p < a.n_out; ++p) {
-    uint64_t w = *wr_ptr(ctr, a.out[p].id);
-    a.plan->wr0[p] = w;
-    *wr_ptr(ctr, a.out[p].id) = w + n * a.out[p].rate;
-  }
-  atomicAdd(&a.eng->fired_step, (unsigned long long)n);
-  atomicAdd(&a.eng->fired_total, (unsigned long long)n);
-}
-
-template <typename U>
-__device__ void copy_units(const CopyArgs& a, const CopyPlan& pl) {
-  const uint64_t unit = sizeof(U);
-  const uint64_t bytes = pl.n * a.in.rate * a.in.tok;
-  const uint64_t n_units = bytes / unit;
-  const uint64_t in_ring = a.in.cap * a.in.tok;
-  const uint64_t in_off = (pl.rd0 % a.in.cap) * a.in.tok;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (int p = 0; p < a.n_out; ++p) {
-    const ChanDesc& o = a.out[p];
-    const uint64_t out_ring = o.cap * o.tok;
-    const uint64_t out_off = (pl.wr0[p] % o.cap) * o.tok;
-    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n_units; u += stride) {
-      uint64_t b = u * unit;
-      uint64_t si = in_off + b;
-      if (si >= in_ring) si -= in_ring;
-      uint64_t di = out_off + b;
-      if (di >= out_ring) di -= out_ring;
-      *reinterpret_cast<U*>(o.ring + di) = *reinterpret_cast<const U*>(a.in.ring + si);
-    }
-  }
-}
-
-__global__ void k_copy_body(CopyArgs a) {
-  const CopyPlan pl = *a.plan;
-  if (pl.n == 0) return;
-  if (a.unit == 16) copy_units<uint4>(a, pl);
-  else if (a.unit == 4) copy_units<uint32_t>(a, pl);
-  else copy_units<uint8_t>(a, pl);
-}
+__global__ void k_copy_plan(CopyArgs a) { copy_plan_dev(a); }
+__global__ void k_copy_body(CopyArgs a) { copy_body_dev(a, Grid{blockIdx.x, gridDim.x}); }
 
 cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0,
                         cudaEvent_t ev1) {

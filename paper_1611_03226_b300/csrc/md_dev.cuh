@@ -1,0 +1,356 @@
+// Device-side phases of the fused motion-detection actor: frame difference against the previous frame
+// (delivered by a channel with one initial token, Sec. 4.1), threshold, 3x3
+// erosion then dilation, and emission of one record per 16x16 tile with
+// motion.  The record port has a variable rate (0..r_max records per firing,
+// r_max = tiles per frame); a firing is enabled only while r_max record slots
+// are free, so the number of firings is known only after the counts are.
+//
+// Kernels per step:
+//   plan    (1 CTA)   candidate firings n_cand from the frame / count channels
+//                     and the record space; zero the per-frame totals.
+//   main    (persistent warps)  each warp walks the rows of one 32-row strip
+//                     and 480-pixel column band for a chunk of 8 consecutive
+//                     frames, with the whole per-pixel pipeline in registers
+//                     (see md_unit).  When the previous-frame channel is the
+//                     current-frame channel delayed by one token, each frame
+//                     row is loaded once and serves both frames that use it.
+//   finish  (1 CTA)   exclusive scan of the per-frame record totals, the exact
+//                     number of enabled firings, counter commit.
+//   scatter (1 CTA per frame)  raster-order compaction of the tiles with
+//                     count > 0 into the record ring, and the count token.
+#pragma once
+#include <algorithm>
+#include "common.cuh"
+
+namespace dfg {
+
+
+constexpr int kMdThreads = 256;     // plan / finish / scatter kernels
+
+// Motion bits of 4 pixels: bit i of the result is set iff |c_i - p_i| > thr,
+// with the threshold test done bytewise: for d = |c - p| (per byte), d > thr
+// iff d >= 128 or (d & 0x7f) + (127 - thr) carries into bit 7.  The four byte
+// MSBs (bits 7, 15, 23, 31) are then gathered into bits 28..31 by one multiply.
+__device__ __forceinline__ uint32_t motion_nibble_hi(uint32_t c, uint32_t p, uint32_t add4) {
+  const uint32_t d = __vabsdiffu4(c, p);
+  const uint32_t m = (d | ((d & 0x7f7f7f7fu) + add4)) & 0x80808080u;
+  return m * 0x00204081u;                 // bits 28..31 = pixels 0..3
+}
+
+__device__ inline void md_plan_dev(const MdArgs& a) {
+  __shared__ uint64_t s_n;
+  if (threadIdx.x == 0) {
+    uint64_t* ctr = a.ctr;
+    const uint64_t rdc = *rd_ptr(ctr, a.cur.id), wrc = *wr_ptr(ctr, a.cur.id);
+    const uint64_t rdp = *rd_ptr(ctr, a.prev.id), wrp = *wr_ptr(ctr, a.prev.id);
+    const uint64_t wrr = *wr_ptr(ctr, a.rec.id), rdr = *rd_ptr(ctr, a.rec.id);
+    const uint64_t wrn = *wr_ptr(ctr, a.cnt.id), rdn = *rd_ptr(ctr, a.cnt.id);
+    uint64_t n = wrc - rdc;
+    n = min(n, wrp - rdp);
+    n = min(n, a.cnt.cap - (wrn - rdn));
+    n = min(n, (uint64_t)a.n_max);
+    const uint64_t free_rec = a.rec.cap - (wrr - rdr);
+    if (free_rec < (uint64_t)a.n_tiles) n = 0;
+    MdPlanHdr* pl = a.plan;
+    pl->n_cand = n;
+    pl->rd_cur0 = rdc;
+    pl->rd_prev0 = rdp;
+    pl->wr_rec0 = wrr;
+    pl->wr_cnt0 = wrn;
+    pl->free_rec = free_rec;
+    s_n = n;
+  }
+  __syncthreads();
+  for (uint64_t j = threadIdx.x; j < s_n; j += blockDim.x) a.frame_tot[j] = 0;
+}
+
+
+constexpr int kMdRows = 32;               // strip height: two tile rows
+constexpr int kMdWalk = kMdRows + 4;      // rows walked per strip (2-row halo each side)
+constexpr int kMdOwned = 30;              // tile columns owned per warp (lanes 1..30)
+constexpr int kMdWarpsPerCta = 4;
+constexpr int kMdFrames = 8;              // frames per work unit
+
+// 16 pixels (one tile column of one row) -> 16 motion bits, bit i = pixel i.
+__device__ __forceinline__ uint32_t motion_bits16(uint4 c, uint4 p, uint32_t add4) {
+  uint32_t acc = 0;
+  acc = __funnelshift_l(motion_nibble_hi(c.w, p.w, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.z, p.z, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.y, p.y, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.x, p.x, add4), acc, 4);
+  return acc;
+}
+
+// 16-byte row load; NC selects the read-only (non-coherent) path, valid only
+// when no CTA of the same launch writes the ring.
+template <bool NC>
+__device__ __forceinline__ uint4 ld16(const uint8_t* p) {
+  if constexpr (NC) return __ldg(reinterpret_cast<const uint4*>(p));
+  else return *reinterpret_cast<const uint4*>(p);
+}
+
+__device__ __forceinline__ const uint8_t* frame_at(const ChanDesc& c, uint64_t slot0, uint64_t j) {
+  uint64_t s = slot0 + j;
+  if (s >= c.cap) s -= c.cap;
+  return c.ring + s * c.tok;
+}
+
+// Two frames' 16-pixel rows packed in one word (frame A in bits 0..15, frame B
+// in bits 16..31).  Horizontal 3-neighbourhoods of both halves at once: pixel i
+// combines pixels i-1, i, i+1, where pixel -1 is bit 15 (31) of the left lane's
+// word and pixel 16 is bit 0 (16) of the right lane's word.
+__device__ __forceinline__ uint32_t left_nb(uint32_t v, uint32_t left) {     // pixel i-1 at bit i
+  return ((v << 1) & 0xfffefffeu) | ((left >> 15) & 0x00010001u);
+}
+__device__ __forceinline__ uint32_t right_nb(uint32_t v, uint32_t right) {   // pixel i+1 at bit i
+  return ((v >> 1) & 0x7fff7fffu) | ((right << 15) & 0x80008000u);
+}
+
+// One warp = one worker.  Work unit = (32-row strip, band of 30 tile columns,
+// chunk of up to F consecutive frames, F even).  Lane l covers tile column
+// 30*band - 1 + l; lanes 0 and 31 are halo lanes that only supply neighbour
+// bits.  The warp walks the strip's rows plus a 2-row halo; for every row it
+// reads that row of frames j0-1 .. j0+F-1 once (one 16-byte load per lane and
+// frame, 512 contiguous bytes per warp), and each loaded row serves as the
+// current row of frame j and the previous row of frame j+1.  The pipeline
+//   b = |cur - prev| > thr  ->  erosion (3 rows)  ->  dilation (3 rows)  ->  popcount
+// runs in registers on pairs of frames packed into one word; horizontal
+// neighbour bits come from lane shuffles.  With a previous-frame channel that
+// is not the delayed current channel, F = 2 with a separate previous row per
+// frame.
+template <int F, bool NC>
+__device__ inline void md_unit(const MdArgs& a, uint64_t slot_cur0, uint64_t slot_prev0, int strip,
+                        int band, uint64_t j0, int nf, uint32_t add4) {
+  static_assert(F % 2 == 0, "frames are processed in pairs");
+  constexpr int NP = F / 2;
+  const int W = a.W, H = a.H;
+  const int lane = threadIdx.x & 31;
+  const int cols = W / 16;
+  const int col = band * kMdOwned - 1 + lane;                // this lane's tile column
+  const bool col_in = col >= 0 && col < cols;
+  const bool owned = lane >= 1 && lane <= kMdOwned && col_in;
+  const int y0 = strip * kMdRows;
+  const size_t col_off = (size_t)(col_in ? col : 0) * 16;
+  // Row sources.  F > 2 (shared previous rows, ring < 2 GiB): frame t of the
+  // unit is at cbase + coff[t]; the previous frame of frame 0 is at p0.  F == 2:
+  // explicit pointers for both frames and both previous frames.
+  const uint8_t* cbase = frame_at(a.cur, slot_cur0, j0);
+  int32_t coff[F];
+#pragma unroll
+  for (int t = 0; t < F; ++t) {
+    const uint8_t* f = frame_at(a.cur, slot_cur0, j0 + (t < nf ? t : 0));
+    coff[t] = (int32_t)(f - cbase);
+  }
+  const uint8_t* p0 = (a.dedup && j0 >= 1) ? frame_at(a.cur, slot_cur0, j0 - 1)
+                                           : frame_at(a.prev, slot_prev0, j0);
+  const uint8_t* p1 = nullptr;               // previous frame of frame 1 when not shared
+  if constexpr (F == 2) {
+    p1 = a.dedup ? frame_at(a.cur, slot_cur0, j0) : frame_at(a.prev, slot_prev0, j0 + (nf > 1 ? 1 : 0));
+  }
+  uint32_t hb1[NP], hb2[NP], he1[NP], he2[NP], cn[F];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) hb1[q] = hb2[q] = he1[q] = he2[q] = 0;
+#pragma unroll
+  for (int t = 0; t < F; ++t) cn[t] = 0;
+#pragma unroll 1
+  for (int r = 0; r < kMdWalk; ++r) {
+    const int y = y0 - 2 + r;
+    const bool ld = col_in && y >= 0 && y < H;
+    const size_t off = (size_t)y * W + col_off;
+    uint4 qc[F], qp0, qp1;
+    qp0 = qp1 = make_uint4(0, 0, 0, 0);
+    const uint8_t* crow = cbase + off;
+#pragma unroll
+    for (int t = 0; t < F; ++t) {
+      qc[t] = make_uint4(0, 0, 0, 0);
+      if (ld && t < nf) qc[t] = ld16<NC>(crow + coff[t]);
+    }
+    if (ld) qp0 = ld16<NC>(p0 + off);
+    if constexpr (F == 2) {
+      if (ld && nf > 1) qp1 = ld16<NC>(p1 + off);
+    }
+    const int ye = y - 1, yo = y - 2;
+    const bool e_in = r >= 2 && col_in && ye >= 0 && ye < H;
+    const bool o_in = r >= 4 && yo < H;
+    const int sh = (r - 4 < 16) ? 0 : 16;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int ta = 2 * q, tb = 2 * q + 1;
+      const uint4 pa = ta == 0 ? qp0 : qc[ta - 1];
+      const uint4 pb = F == 2 ? qp1 : qc[ta];
+      const uint32_t b = ld ? (motion_bits16(qc[ta], pa, add4) | (motion_bits16(qc[tb], pb, add4) << 16))
+                            : 0xffffffffu;
+      const uint32_t bl = __shfl_up_sync(0xffffffffu, b, 1);
+      const uint32_t br = __shfl_down_sync(0xffffffffu, b, 1);
+      const uint32_t hrow = b & left_nb(b, bl) & right_nb(b, br);
+      const uint32_t e = e_in ? (hb2[q] & hb1[q] & hrow) : 0u;
+      hb2[q] = hb1[q];
+      hb1[q] = hrow;
+      const uint32_t el = __shfl_up_sync(0xffffffffu, e, 1);
+      const uint32_t er = __shfl_down_sync(0xffffffffu, e, 1);
+      const uint32_t drow = e | left_nb(e, el) | right_nb(e, er);
+      if (o_in) {
+        const uint32_t o = he2[q] | he1[q] | drow;
+        cn[ta] += (uint32_t)__popc(o & 0xffffu) << sh;
+        cn[tb] += (uint32_t)__popc(o >> 16) << sh;
+      }
+      he2[q] = he1[q];
+      he1[q] = drow;
+    }
+  }
+  // two tile rows per lane and frame
+  const int ty0 = 2 * strip;
+  const bool second = ty0 + 1 < a.tiles_y;
+#pragma unroll
+  for (int t = 0; t < F; ++t) {
+    if (t >= nf) break;
+    const uint64_t j = j0 + t;
+    uint16_t* cnt = a.counts + j * a.n_tiles;
+    const uint32_t lo = cn[t] & 0xffffu, hi = cn[t] >> 16;
+    if (owned) {
+      cnt[(size_t)ty0 * a.tiles_x + col] = (uint16_t)lo;
+      if (second) cnt[(size_t)(ty0 + 1) * a.tiles_x + col] = (uint16_t)hi;
+    }
+    const uint32_t nz = __popc(__ballot_sync(0xffffffffu, owned && lo)) +
+                        __popc(__ballot_sync(0xffffffffu, owned && second && hi));
+    if (lane == 0 && nz) atomicAdd(&a.frame_tot[j], nz);
+  }
+}
+
+template <int F, bool NC>
+__device__ inline void md_main_dev(const MdArgs& a, Grid g) {
+  const int wpc = blockDim.x >> 5;                           // warps per CTA
+  const MdPlanHdr pl = *a.plan;
+  const uint64_t n = pl.n_cand;
+  if (n == 0) return;
+  const int cols = a.W / 16;
+  const int bands = (cols + kMdOwned - 1) / kMdOwned;
+  const int strips = (a.H + kMdRows - 1) / kMdRows;
+  const uint32_t pairs = (uint32_t)(strips * bands);
+  const uint64_t chunks = (n + F - 1) / F;
+  const uint64_t units = pairs * chunks;
+  const uint64_t G = (uint64_t)g.n * wpc;
+  const uint32_t add4 = 0x01010101u * (uint32_t)(127 - a.thr);
+  const uint64_t slot_cur0 = pl.rd_cur0 % a.cur.cap, slot_prev0 = pl.rd_prev0 % a.prev.cap;
+  for (uint64_t u = g.b * (uint64_t)wpc + (threadIdx.x >> 5); u < units; u += G) {
+    const uint32_t pair = (uint32_t)(u % pairs);
+    const uint64_t chunk = u / pairs;
+    const uint64_t j0 = chunk * F;
+    const uint64_t left = n - j0;
+    const int nf = left < (uint64_t)F ? (int)left : F;
+    md_unit<F, NC>(a, slot_cur0, slot_prev0, (int)(pair / bands), (int)(pair % bands), j0, nf, add4);
+  }
+}
+
+__device__ inline void md_finish_dev(const MdArgs& a) {
+  uint64_t* frame_off = a.frame_off;
+  __shared__ uint64_t sw[32];
+  __shared__ uint64_t s_n;
+  MdPlanHdr* pl = a.plan;
+  const uint64_t n_cand = pl->n_cand;
+  const uint64_t free_rec = pl->free_rec;
+  if (threadIdx.x == 0) s_n = n_cand;
+  __syncthreads();
+  uint64_t carry = 0;
+  for (uint64_t base = 0; base < n_cand; base += blockDim.x) {
+    const uint64_t i = base + threadIdx.x;
+    const uint64_t v = i < n_cand ? a.frame_tot[i] : 0;
+    // exclusive scan (block)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sw[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t s = lane < nw ? sw[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      if (lane < nw) sw[lane] = s;
+    }
+    __syncthreads();
+    const uint64_t off = carry + (wid ? sw[wid - 1] : 0) + x - v;
+    const uint64_t tot = sw[nw - 1];
+    __syncthreads();
+    if (i < n_cand) {
+      frame_off[i] = off;
+      // firing i is enabled iff r_max record slots are free before it
+      if (off + (uint64_t)a.n_tiles > free_rec) atomicMin((unsigned long long*)&s_n, i);
+    }
+    carry += tot;
+    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint64_t n = s_n;
+    const uint64_t used = n < n_cand ? frame_off[n] : carry;
+    frame_off[n] = used;
+    pl->n_cand = n;                 // the scatter kernel handles exactly n firings
+    uint64_t* ctr = a.ctr;
+    *rd_ptr(ctr, a.cur.id) = pl->rd_cur0 + n;
+    *rd_ptr(ctr, a.prev.id) = pl->rd_prev0 + n;
+    *wr_ptr(ctr, a.cnt.id) = pl->wr_cnt0 + n;
+    *wr_ptr(ctr, a.rec.id) = pl->wr_rec0 + used;
+    atomicAdd(&a.eng->fired_step, (unsigned long long)n);
+    atomicAdd(&a.eng->fired_total, (unsigned long long)n);
+  }
+}
+
+__device__ inline void md_scatter_frame(const MdArgs& a, uint64_t j) {
+  const uint64_t* frame_off = a.frame_off;
+  __shared__ uint32_t sw[32];
+  const MdPlanHdr pl = *a.plan;
+  const int nt = a.n_tiles;
+  const int per = (nt + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int t0 = threadIdx.x * per, t1 = min(nt, t0 + per);
+  const uint16_t* cnt = a.counts + j * nt;
+  uint32_t mine = 0;
+  for (int t = t0; t < t1; ++t) mine += cnt[t] > 0;
+  // exclusive scan of `mine` over the block
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sw[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t s = lane < nw ? sw[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) sw[lane] = s;
+  }
+  __syncthreads();
+  uint64_t pos = pl.wr_rec0 + frame_off[j] + (wid ? sw[wid - 1] : 0) + x - mine;
+  for (int t = t0; t < t1; ++t) {
+    const uint32_t c = cnt[t];
+    if (c > 0) {
+      const uint32_t tx = t % a.tiles_x, ty = t / a.tiles_x;
+      uint2 rec;
+      rec.x = (16u * tx) | ((16u * ty) << 16);
+      rec.y = c;
+      *reinterpret_cast<uint2*>(slot_ptr(a.rec, pos)) = rec;
+      ++pos;
+    }
+  }
+  if (threadIdx.x == 0)
+    *reinterpret_cast<uint32_t*>(slot_ptr(a.cnt, pl.wr_cnt0 + j)) = a.frame_tot[j];
+}
+
+// Scatter phase over a virtual grid: one CTA per frame.
+__device__ inline void md_scatter_dev(const MdArgs& a, Grid g) {
+  const uint64_t n = a.plan->n_cand;
+  for (uint64_t j = g.b; j < n; j += g.n) {
+    md_scatter_frame(a, j);
+    __syncthreads();
+  }
+}
+
+}  // namespace dfg

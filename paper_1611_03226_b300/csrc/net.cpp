@@ -84,6 +84,11 @@ struct df_net {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double prof_ms[4] = {0, 0, 0, 0};
   uint64_t prof_n[4] = {0, 0, 0, 0};
+  // persistent step kernel: device-side program (built on first use)
+  void* persist_mem = nullptr;
+  PersistOp* d_persist_ops = nullptr;
+  int persist_n_ops = 0, persist_mtmax = 16;
+  size_t persist_smem = 0;
 };
 
 namespace {
@@ -340,6 +345,63 @@ std::map<int, Scratch> g_scratch;       // per device: backward tap-gradient par
 
 }  // namespace
 
+// Device copy of the step program for the persistent kernel.
+df_status build_persistent(df_net* net) {
+  if (net->d_persist_ops) return DF_OK;
+  std::vector<PersistOp> ops;
+  size_t bytes = 0;
+  for (const Op& op : net->program) {
+    if (op.kind == kOpCopy) bytes += align256(sizeof(CopyArgs));
+    if (op.kind == kOpDyn) bytes += align256(sizeof(DynArgs));
+    if (op.kind == kOpMd) bytes += align256(sizeof(MdArgs));
+  }
+  bytes += align256(sizeof(PersistOp) * std::max<size_t>(1, net->program.size()));
+  if (cudaMalloc(&net->persist_mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    net->persist_mem = nullptr;
+    return DF_ENOMEM;
+  }
+  uint8_t* base = static_cast<uint8_t*>(net->persist_mem);
+  size_t off = 0;
+  int max_group = 1, mtmax = 1;
+  for (const Op& op : net->program) {
+    PersistOp p{};
+    if (op.kind == kOpCopy) {
+      DF_CUDA(cudaMemcpyAsync(base + off, &op.copy, sizeof(CopyArgs), cudaMemcpyHostToDevice, net->stream));
+      p.kind = kPersistCopy;
+      p.args = base + off;
+      off += align256(sizeof(CopyArgs));
+    } else if (op.kind == kOpDyn) {
+      DF_CUDA(cudaMemcpyAsync(base + off, &op.dyn, sizeof(DynArgs), cudaMemcpyHostToDevice, net->stream));
+      p.kind = kPersistDyn;
+      p.args = base + off;
+      off += align256(sizeof(DynArgs));
+    } else if (op.kind == kOpMd) {
+      DF_CUDA(cudaMemcpyAsync(base + off, &op.md, sizeof(MdArgs), cudaMemcpyHostToDevice, net->stream));
+      p.kind = kPersistMd;
+      p.args = base + off;
+      off += align256(sizeof(MdArgs));
+    } else {
+      p.kind = kPersistDpd;
+      p.n = op.dpd_n;
+      p.args = op.dpd_dev;
+      max_group = std::max(max_group, op.dpd_n);
+      mtmax = std::max(mtmax, op.max_mt);
+    }
+    ops.push_back(p);
+  }
+  net->d_persist_ops = reinterpret_cast<PersistOp*>(base + off);
+  if (!ops.empty())
+    DF_CUDA(cudaMemcpyAsync(net->d_persist_ops, ops.data(), sizeof(PersistOp) * ops.size(),
+                            cudaMemcpyHostToDevice, net->stream));
+  net->persist_n_ops = (int)ops.size();
+  net->persist_mtmax = mtmax <= 16 ? 16 : 32;
+  net->persist_smem = persistent_smem(net->persist_mtmax, max_group);
+  DF_CUDA(persistent_prepare(net->persist_smem));
+  DF_CUDA(cudaStreamSynchronize(net->stream));
+  return DF_OK;
+}
+
 df_status cuda_status(cudaError_t e) {
   return e == cudaSuccess ? DF_OK : record_cuda(e, "kernel launch");
 }
@@ -396,6 +458,7 @@ void df_net_destroy(df_net* net) {
     cudaEventDestroy(pe.second.second);
   }
   for (cudaEvent_t e : net->ev_free) cudaEventDestroy(e);
+  if (net->persist_mem) cudaFree(net->persist_mem);
   if (net->arena) cudaFree(net->arena);
   if (net->h_pin) cudaFreeHost(net->h_pin);
   if (net->own_stream) cudaStreamDestroy(net->stream);
@@ -802,7 +865,7 @@ df_status df_push(df_net* net, int32_t src_actor, const void* src, uint64_t n_to
 df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_firings) {
   if (!net) return DF_EINVAL;
   if (!net->finalized) return DF_ESTATE;
-  if (flags & DF_RUN_PERSISTENT) return DF_ENOTSUP;
+  if ((flags & DF_RUN_PERSISTENT) && (flags & (DF_RUN_GRAPH | DF_RUN_NO_BATCH))) return DF_ENOTSUP;
   DeviceGuard g(net->device);
   const bool no_batch = flags & DF_RUN_NO_BATCH;
   uint64_t before = 0;
@@ -812,7 +875,16 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
   } else if (n_steps < 0) {
     return DF_EINVAL;
   }
-  if (n_steps >= 0) {
+  if (flags & DF_RUN_PERSISTENT) {
+    df_status st = build_persistent(net);
+    if (st != DF_OK) return st;
+    const auto ev = prof_pair(net, DF_PROF_STEP, false);
+    if (ev.first) DF_CUDA(cudaEventRecord(ev.first, net->stream));
+    DF_CUDA(launch_persistent(net->d_persist_ops, net->persist_n_ops, net->d_eng, n_steps,
+                              net->wait_limit_ns, net->persist_mtmax, net->persist_smem, net->n_sm,
+                              net->stream));
+    if (ev.second) DF_CUDA(cudaEventRecord(ev.second, net->stream));
+  } else if (n_steps >= 0) {
     if (flags & DF_RUN_GRAPH) {
       auto key = std::make_pair(n_steps, flags & DF_RUN_NO_BATCH);
       auto it = net->graphs.find(key);
@@ -910,6 +982,29 @@ df_status df_channel_counters(df_net* net, int32_t ch, uint64_t* produced, uint6
   if (consumed) *consumed = r;
   if (occupancy) *occupancy = w - r;
   return DF_OK;
+}
+
+df_status df_set_wait_limit(df_net* net, int64_t limit_ns) {
+  if (!net || limit_ns <= 0) return DF_EINVAL;
+  net->wait_limit_ns = limit_ns;
+  for (Op& op : net->program)
+    if (op.kind == kOpMd) op.md.wait_limit_ns = limit_ns;
+  return DF_OK;
+}
+
+df_status df_selftest_wait_timeout(df_net* net, int64_t limit_ns) {
+  if (!net || limit_ns <= 0) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  DeviceGuard g(net->device);
+  df_status st = fail_if_device_error(net);
+  if (st != DF_OK) return st;
+  DF_CUDA(launch_barrier_selftest(net->d_eng, limit_ns, net->stream));
+  st = fail_if_device_error(net);
+  // leave the network usable: clear the status word and the barrier state
+  DF_CUDA(cudaMemsetAsync(&net->d_eng->status, 0, 2 * sizeof(int32_t), net->stream));
+  DF_CUDA(cudaMemsetAsync(&net->d_eng->barrier_count, 0, 2 * sizeof(unsigned int), net->stream));
+  DF_CUDA(cudaStreamSynchronize(net->stream));
+  return st;
 }
 
 df_status df_dpd_set_tile(df_net* net, int32_t actor, uint32_t tile, uint32_t threads) {

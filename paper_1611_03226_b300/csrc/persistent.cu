@@ -1,0 +1,159 @@
+// Persistent step kernel: one cooperative launch runs n steps of the whole
+// program (or steps until one fires nothing), with every rate decision, scan,
+// gather and scatter on the device and no host involvement between steps.
+//
+// Phases of one step follow the per-phase kernels exactly (plan -> body ->
+// finish -> scatter per actor, actors in insertion order); a grid barrier
+// separates phases that consume another CTA's results.  The barrier is a
+// counter plus a generation word in the engine state; a CTA that waits longer
+// than the limit records DF_ETIMEOUT in the status word, and every CTA leaves
+// at its next barrier once the status word is set, so a wait that cannot
+// complete ends the kernel instead of hanging it.
+#include "core_dev.cuh"
+#include "dpd_dev.cuh"
+#include "dyn_dev.cuh"
+#include "md_dev.cuh"
+
+namespace dfg {
+
+__device__ __forceinline__ long long timer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Returns false when the status word is set (own timeout or another CTA's).
+__device__ bool grid_barrier(EngineDev* e, unsigned int expected, long long limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &e->barrier_gen;
+    const unsigned int g0 = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&e->barrier_count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == expected) {
+      e->barrier_count = 0;
+      __threadfence();
+      atomicAdd(&e->barrier_gen, 1u);
+    } else {
+      const long long t0 = timer_ns();
+      while (*gen == g0) {
+        if (timer_ns() - t0 > limit_ns) {
+          set_status(e, DF_ETIMEOUT, kWhereGridBarrier);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok && *reinterpret_cast<volatile int32_t*>(&e->status) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int MTMAX>
+__global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp* __restrict__ ops,
+                                                               int n_ops, EngineDev* eng,
+                                                               int64_t n_steps, long long limit_ns) {
+  extern __shared__ float4 smem[];
+  const Grid g{blockIdx.x, gridDim.x};
+  const unsigned int nb = gridDim.x;
+  const bool lead = blockIdx.x == 0;
+  const int64_t max_steps = n_steps < 0 ? (int64_t)1 << 20 : n_steps;
+  volatile unsigned long long* total = &eng->fired_total;
+  for (int64_t step = 0; step < max_steps; ++step) {
+    if (lead && threadIdx.x == 0) eng->fired_step = 0;
+    if (!grid_barrier(eng, nb, limit_ns)) return;
+    const unsigned long long fired0 = *total;
+    for (int o = 0; o < n_ops; ++o) {
+      const PersistOp op = ops[o];
+      if (op.kind == kPersistCopy) {
+        const CopyArgs& a = *static_cast<const CopyArgs*>(op.args);
+        if (lead && threadIdx.x == 0) copy_plan_dev(a);
+        if (!grid_barrier(eng, nb, limit_ns)) return;
+        copy_body_dev(a, g);
+      } else if (op.kind == kPersistDpd) {
+        const DpdArgs* args = static_cast<const DpdArgs*>(op.args);
+        for (int i = blockIdx.x; i < op.n; i += gridDim.x) {
+          dpd_plan_dev(args[i]);
+          __syncthreads();
+        }
+        if (!grid_barrier(eng, nb, limit_ns)) return;
+        dpd_body_dev<8, MTMAX>(args, op.n, g, smem);
+      } else if (op.kind == kPersistDyn) {
+        const DynArgs& a = *static_cast<const DynArgs*>(op.args);
+        if (lead) dyn_plan_dev(a);
+        if (!grid_barrier(eng, nb, limit_ns)) return;
+        if (a.kind == DF_DPD_POLY) poly_body_dev(a, g);
+        else add_body_dev(a, g);
+      } else if (op.kind == kPersistMd) {
+        const MdArgs& a = *static_cast<const MdArgs*>(op.args);
+        if (lead) md_plan_dev(a);
+        if (!grid_barrier(eng, nb, limit_ns)) return;
+        if (a.shared_rows) md_main_dev<8, false>(a, g);
+        else md_main_dev<2, false>(a, g);
+        if (!grid_barrier(eng, nb, limit_ns)) return;
+        if (lead) md_finish_dev(a);
+        if (!grid_barrier(eng, nb, limit_ns)) return;
+        md_scatter_dev(a, g);
+      }
+      if (!grid_barrier(eng, nb, limit_ns)) return;
+    }
+    // every CTA reads the same totals: nothing changes them between these barriers
+    if (n_steps < 0 && *total == fired0) return;
+  }
+}
+
+// A barrier that waits for one more CTA than the grid has: it can only end by
+// its time limit, which must leave DF_ETIMEOUT in the status word.
+__global__ void k_barrier_selftest(EngineDev* eng, long long limit_ns) {
+  grid_barrier(eng, gridDim.x + 1, limit_ns);
+}
+
+static int g_persist_blocks[2] = {0, 0};
+
+cudaError_t persistent_prepare(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_persistent<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_persistent<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_persist_blocks[0], k_persistent<16>,
+                                                    kPersistThreads, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_persist_blocks[1], k_persistent<32>,
+                                                       kPersistThreads, smem);
+}
+
+size_t persistent_smem(int mtmax, int max_group) {
+  const size_t T = 8 * kPersistThreads;
+  const size_t W = T + mtmax - 1;
+  const size_t Wp = W + W / 8 + 2;
+  return 2 * W * sizeof(float2) + kBranchGroup * Wp * sizeof(float2) +
+         (size_t)kMaxBranches * mtmax * sizeof(float2) + (size_t)(max_group + 1) * sizeof(uint64_t);
+}
+
+cudaError_t launch_persistent(const PersistOp* ops, int n_ops, EngineDev* eng, int64_t n_steps,
+                              long long limit_ns, int mtmax, size_t smem, int n_sm, cudaStream_t s) {
+  const int idx = mtmax <= 16 ? 0 : 1;
+  const int per_sm = g_persist_blocks[idx];
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaMemsetAsync(&eng->barrier_count, 0, 2 * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&ops, (void*)&n_ops, (void*)&eng, (void*)&n_steps, (void*)&limit_ns};
+  const dim3 grid(n_sm * per_sm), block(kPersistThreads);
+  if (idx == 0) return cudaLaunchCooperativeKernel((void*)k_persistent<16>, grid, block, args, smem, s);
+  return cudaLaunchCooperativeKernel((void*)k_persistent<32>, grid, block, args, smem, s);
+}
+
+cudaError_t launch_barrier_selftest(EngineDev* eng, long long limit_ns, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&eng->barrier_count, 0, 2 * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&eng, (void*)&limit_ns};
+  return cudaLaunchCooperativeKernel((void*)k_barrier_selftest, dim3(4), dim3(32), args, 0, s);
+}
+
+}  // namespace dfg

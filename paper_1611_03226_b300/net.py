@@ -158,6 +158,13 @@ class Net:
                 "df_channel_counters")
         return p.value, c.value, o.value
 
+    def set_wait_limit(self, ns):
+        L.check(L.lib.df_set_wait_limit(self.h, int(ns)), "df_set_wait_limit")
+
+    def selftest_wait_timeout(self, ns):
+        """Status left by a grid barrier that can only end by its time limit."""
+        return L.lib.df_selftest_wait_timeout(self.h, int(ns))
+
     def profile(self, on=True):
         L.check(L.lib.df_profile_enable(self.h, 1 if on else 0), "df_profile_enable")
 

@@ -22,7 +22,7 @@ def Net():
     return Net
 
 
-def stream_both(Net, h, orders, L, d, cap, masks, blocks, chunk, rng=None, tile=None):
+def stream_both(Net, h, orders, L, d, cap, masks, blocks, chunk, rng=None, tile=None, flags=0):
     onet, oi = ON.dpd_fused(h, orders, L, d, cap)
     enet, ei = EN.dpd_fused(Net, h, orders, L, d, cap)
     if tile:
@@ -40,7 +40,7 @@ def stream_both(Net, h, orders, L, d, cap, masks, blocks, chunk, rng=None, tile=
             i += k
         steps = 1 if rng is None else int(rng.integers(1, 3))
         fo = onet.run(steps)
-        fe = enet.run(steps)
+        fe = enet.run(steps, flags)
         assert fo == fe
         for key in ("ch_ctrl", "ch_data", "ch_out"):
             assert onet.counters(oi[key]) == enet.counters(ei[key])
@@ -185,7 +185,8 @@ def test_stateless_forward_backward(Net):
 
 
 @pytest.mark.parametrize("L,M,K,d,bc", [(512, 10, 4, 1, 2), (3, 6, 3, 2, 1), (2000, 16, 8, 1, 3)])
-def test_expanded_network_step_by_step(Net, L, M, K, d, bc):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_expanded_network_step_by_step(Net, L, M, K, d, bc, persistent):
     """The paper's Poly -> FIR_k -> Adder network with dynamic per-firing branch
     rates: every channel's counters equal the oracle's after every step, and
     the output stream matches within 1e-5 per block."""
@@ -209,7 +210,8 @@ def test_expanded_network_step_by_step(Net, L, M, K, d, bc):
             enet.push(ei["ctrl"], np.ascontiguousarray(masks[i:i + k]))
             enet.push(ei["data"], np.ascontiguousarray(x[i:i + k]))
             i += k
-        fo, fe = onet.run(1), enet.run(1)
+        from paper_1611_03226_b300 import _lib as Lb
+        fo, fe = onet.run(1), enet.run(1, Lb.DF_RUN_PERSISTENT if persistent else 0)
         assert fo == fe, step
         for c in range(len(onet.channels)):
             assert onet.counters(c) == enet.counters(c), (step, c)
@@ -271,3 +273,58 @@ def test_batched_channels_match_oracle_and_per_channel_launches(Net):
     for c in range(C):
         np.testing.assert_array_equal(variants["batched"][c], variants["per_channel"][c])
         np.testing.assert_array_equal(variants["batched"][c], variants["graph"][c])
+
+
+def test_persistent_mode_streams_tiny_workload(Net):
+    """The 64 x 4096 workload through capacity-8 FIFOs, every step one
+    persistent-kernel launch."""
+    from paper_1611_03226_b300 import _lib as L
+    w = synth.dpd_tiny()
+    yo, ye = stream_both(Net, w.h, w.orders, w.block_len, w.delay, w.capacity, w.masks,
+                         w.blocks(), 3, flags=L.DF_RUN_PERSISTENT)
+    assert len(ye) == 64
+    check_blocks(yo, ye)
+
+
+def test_persistent_run_to_quiescence_on_device(Net):
+    """run(-1) in persistent mode: the quiescence test happens on the device."""
+    from paper_1611_03226_b300 import _lib as L
+    rng = np.random.default_rng(8)
+    L_, n, K, M = 300, 9, 4, 10
+    x = (rng.normal(0, .3, (n, L_)) + 1j * rng.normal(0, .3, (n, L_))).astype(np.complex64)
+    h = (rng.normal(0, .1, (K, M)) + 1j * rng.normal(0, .1, (K, M))).astype(np.complex64)
+    masks = rng.integers(0, 16, n).astype(np.uint32)
+    orders = (1, 3, 5, 7)
+    onet, oi = ON.dpd_expanded(h, orders, L_, 1, n + 1, branch_capacity=2)
+    enet, ei = EN.dpd_expanded(Net, h, orders, L_, 1, n + 1, branch_capacity=2)
+    onet.push(oi["ctrl"], ON.as_tokens_ctrl(masks))
+    onet.push(oi["data"], ON.as_tokens_blocks(x))
+    enet.push(ei["ctrl"], masks)
+    enet.push(ei["data"], x)
+    assert onet.run(-1) == enet.run(-1, L.DF_RUN_PERSISTENT)
+    for c in range(len(onet.channels)):
+        assert onet.counters(c) == enet.counters(c)
+    yo = np.array(onet.pop(oi["sink"])).reshape(-1, L_)
+    ye = enet.pop(ei["sink"], dtype=np.complex64).reshape(-1, L_)
+    enet.close()
+    check_blocks(yo, ye)
+
+
+def test_bounded_wait_times_out_and_network_stays_usable(Net):
+    """A grid barrier that waits for a CTA that never arrives ends by its
+    20 ms limit with DF_ETIMEOUT; the network then still computes correctly."""
+    from paper_1611_03226_b300 import _lib as L
+    w = synth.dpd_tiny()
+    net, ids = EN.dpd_fused(Net, w.h, w.orders, w.block_len, 0, 4)
+    assert net.selftest_wait_timeout(20_000_000) == L.DF_ETIMEOUT
+    x = w.blocks(0, 3)
+    net.push(ids["ctrl"], np.ascontiguousarray(w.masks[:3]))
+    net.push(ids["data"], x)
+    assert net.run(-1, L.DF_RUN_PERSISTENT) == 3
+    ye = net.pop(ids["sink"], dtype=np.complex64).reshape(3, -1)
+    net.close()
+    onet, oi = ON.dpd_fused(w.h, w.orders, w.block_len, 0, 4)
+    onet.push(oi["ctrl"], ON.as_tokens_ctrl(w.masks[:3]))
+    onet.push(oi["data"], ON.as_tokens_blocks(x))
+    onet.run(-1)
+    check_blocks(np.array(onet.pop(oi["sink"])), ye)

@@ -41,7 +41,10 @@ def build_chain(P, rates, caps, sizes, delays):
     ([4, 1, 2], [9, 3, 5], [16, 64, 32], [1, 0, 1]),
     ([3, 5], [7, 11], [5, 3], [2, 0]),
 ])
-def test_copy_chain_step_by_step(P, rates, caps, sizes, delays):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_copy_chain_step_by_step(P, rates, caps, sizes, delays, persistent):
+    from paper_1611_03226_b300 import _lib as L
+    flags = L.DF_RUN_PERSISTENT if persistent else 0
     onet, enet, src, osink, esink, chans = build_chain(P, rates, caps, sizes, delays)
     rng = np.random.default_rng(sum(rates))
     seq = 0
@@ -56,7 +59,7 @@ def test_copy_chain_step_by_step(P, rates, caps, sizes, delays):
             enet.push(src, np.concatenate(toks))
             seq += k
         steps = int(rng.integers(0, 3))
-        assert onet.run(steps) == enet.run(steps)
+        assert onet.run(steps) == enet.run(steps, flags)
         for oc, ec in chans:
             assert onet.counters(oc) == enet.counters(ec)
         m = int(rng.integers(0, 5))

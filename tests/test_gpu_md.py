@@ -16,7 +16,7 @@ def Net():
     return Net
 
 
-def stream_both(Net, frames, cap, chunk, rec_capacity=None, separate=False, prev_init=None):
+def stream_both(Net, frames, cap, chunk, rec_capacity=None, separate=False, prev_init=None, flags=0):
     T, H, W = frames.shape
     onet, oi = ON.motion_fused(H, W, cap, rec_capacity, prev_init=prev_init)
     enet, ei = EN.motion_fused(Net, H, W, cap, rec_capacity, prev_init=prev_init,
@@ -32,7 +32,7 @@ def stream_both(Net, frames, cap, chunk, rec_capacity=None, separate=False, prev
             if separate:
                 enet.push(ei["src_prev"], np.ascontiguousarray(frames[i:i + k]))
             i += k
-        fo, fe = onet.run(1), enet.run(1)
+        fo, fe = onet.run(1), enet.run(1, flags)
         assert fo == fe
         for key in ("ch_cur", "ch_prev", "ch_rec", "ch_cnt"):
             assert onet.counters(oi[key]) == enet.counters(ei[key]), key
@@ -110,3 +110,13 @@ def test_motion_full_workload(Net):
         prev = f[t]
     np.testing.assert_array_equal(cnt, np.array(want_c, np.uint32))
     np.testing.assert_array_equal(rec, np.concatenate(want_r))
+
+
+@pytest.mark.parametrize("separate", [False, True])
+def test_motion_persistent_mode(Net, separate):
+    from paper_1611_03226_b300 import _lib as L
+    w = synth.motion(n_frames=7, height=72, width=96)
+    f = w.frames()
+    ro, co, re_, ce = stream_both(Net, f, 3, 2, separate=separate, flags=L.DF_RUN_PERSISTENT)
+    np.testing.assert_array_equal(ce, co)
+    np.testing.assert_array_equal(re_, ro)
