@@ -10,7 +10,7 @@ large predistorter (512 blocks x 2^20 complex64, up to 8 branches, 16 taps),
 the tiny predistorter (64 x 4096, capacity 8) and the batched and
 differentiable forms.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--quick]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--quick] [--only LIST]
 
 The GPU arm prints one JSON line with the device-timed value, the end-to-end
 value through the C ABI from pinned host memory, the roofline of the dominant
@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "DPD Msamples/s & motion-detect frames/s on 1 B300; % of HBM roofline"
+SECONDARY = ("dpd_large", "dpd_tiny", "dpd_batch", "dpd_fit")
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (Blackwell)
 
 
@@ -48,6 +49,29 @@ def peaks():
         return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2032.0)),
                 "source": "measured"}
     return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0, "source": "fallback"}
+
+
+def profiled_traffic(summary):
+    """DRAM bytes per launch from a profiles/ summary, or None when the kernel
+    sources have changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    try:
+        h = hashlib.sha256()
+        for f in fields["sources"].split():
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest()[:16] != fields["source_sha256"]:
+            return None
+        return float(fields["traffic_bytes_per_launch"])
+    except (KeyError, OSError, ValueError):
+        return None
 
 
 # ---------------------------------------------------------------- clocks ----
@@ -228,7 +252,8 @@ def bench_motion(args, P, torch, pk, ws):
         "kernel_ms": {"md_main_avg": main_avg, "step_avg": step_ms / max(args.steps, 1)},
         "gpu_launches_per_step": 5,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "frac": achieved / pk["hbm_gbs"],
+                     "traffic": profiled_traffic("k_md_main__motion_300x1920x1080.md") if T == 300 else None,
                      "kernel": "k_md_main", "algorithmic_bytes_per_launch": alg_bytes,
                      "peak_source": pk["source"]},
         "e2e": {"value": ws * T / e2e_s, "unit": "frames/s",
@@ -336,7 +361,9 @@ def bench_dpd_large(args, P, torch, pk, ws):
         "unit": "Msamples/s", "ms_per_step": ms_step, "dtype": "f32",
         "kernel_ms": {"dpd_body_avg": body_avg},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved_tf / peak_tf, "traffic": None, "kernel": "k_dpd_body",
+                     "frac": achieved_tf / peak_tf,
+                     "traffic": profiled_traffic("k_dpd_body__dpd_large_512x1048576.md") if nb == 512 else None,
+                     "kernel": "k_dpd_body",
                      "algorithmic_flops_per_launch": flops,
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
                      "hbm": {"achieved": hbm_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -618,15 +645,17 @@ def gpu_arm(args):
     # recorded on the same stream.
     work = torch.cuda.Stream()
     extra = {}
+    want = set(args.only.split(",")) if args.only else set(SECONDARY)
     with torch.cuda.stream(work):
         md = bench_motion(args, P, torch, pk, ws)
-        if not args.only_motion:
-            dl = bench_dpd_large(args, P, torch, pk, ws)
-            extra["dpd_large"] = dl
-            if ws == 1:
+        if "dpd_large" in want:
+            extra["dpd_large"] = bench_dpd_large(args, P, torch, pk, ws)
+        if ws == 1:
+            if "dpd_tiny" in want:
                 extra["dpd_tiny"] = bench_dpd_tiny(args, P, torch, pk)
-                if not args.quick:
-                    extra["dpd_batch"] = bench_dpd_batch(args, P, torch, pk)
+            if "dpd_batch" in want and not args.quick:
+                extra["dpd_batch"] = bench_dpd_batch(args, P, torch, pk)
+            if "dpd_fit" in want:
                 extra["dpd_fit"] = bench_dpd_fit(args, P, torch, pk)
     clocks = sampler.stop() if rank == 0 else None
     if rank != 0:
@@ -696,7 +725,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--quick", action="store_true", help="smaller workloads (smoke runs)")
-    ap.add_argument("--only-motion", action="store_true")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated secondary workloads to run besides the motion headline "
+                         "(dpd_large, dpd_tiny, dpd_batch, dpd_fit; 'motion' = none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
