@@ -16,10 +16,9 @@ __global__ void __launch_bounds__(kMdWarpsPerCta * 32) k_md_main(MdArgs a) {
   md_main_dev<F, true>(a, Grid{blockIdx.x, gridDim.x});
 }
 
-__global__ void k_md_finish(MdArgs a) { md_finish_dev(a); }
-
-__global__ void __launch_bounds__(kMdThreads) k_md_scatter(MdArgs a) {
-  if (blockIdx.x < a.plan->n_cand) md_scatter_frame(a, blockIdx.x);
+__global__ void __launch_bounds__(kMdThreads) k_md_emit(MdArgs a) {
+  const uint64_t n = a.plan->n_cand;
+  if (blockIdx.x < (n > 0 ? n : 1)) md_emit_frame(a, blockIdx.x, blockIdx.x == 0);
 }
 
 static int g_md_blocks_per_sm[2] = {0, 0};
@@ -46,8 +45,7 @@ cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s, cudaEvent_
   else
     k_md_main<2><<<n_sm * std::max(g_md_blocks_per_sm[1], 1), kMdWarpsPerCta * 32, 0, s>>>(a);
   if (ev1) cudaEventRecord(ev1, s);
-  k_md_finish<<<1, 256, 0, s>>>(a);
-  k_md_scatter<<<a.n_max, kMdThreads, 0, s>>>(a);
+  k_md_emit<<<a.n_max, kMdThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

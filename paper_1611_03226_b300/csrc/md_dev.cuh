@@ -8,16 +8,16 @@
 // Kernels per step:
 //   plan    (1 CTA)   candidate firings n_cand from the frame / count channels
 //                     and the record space; zero the per-frame totals.
-//   main    (persistent warps)  each warp walks the rows of one 32-row strip
+//   main    (persistent warps)  each warp walks the rows of one 48-row strip
 //                     and 480-pixel column band for a chunk of 8 consecutive
 //                     frames, with the whole per-pixel pipeline in registers
 //                     (see md_unit).  When the previous-frame channel is the
 //                     current-frame channel delayed by one token, each frame
 //                     row is loaded once and serves both frames that use it.
-//   finish  (1 CTA)   exclusive scan of the per-frame record totals, the exact
-//                     number of enabled firings, counter commit.
-//   scatter (1 CTA per frame)  raster-order compaction of the tiles with
-//                     count > 0 into the record ring, and the count token.
+//   emit    (1 CTA per frame)  exclusive scan of the per-frame record totals,
+//                     the exact number of enabled firings, raster-order
+//                     compaction of the tiles with count > 0 into the record
+//                     ring, the count token; block 0 commits the counters.
 #pragma once
 #include <algorithm>
 #include "common.cuh"
@@ -25,7 +25,7 @@
 namespace dfg {
 
 
-constexpr int kMdThreads = 256;     // plan / finish / scatter kernels
+constexpr int kMdThreads = 256;     // plan and emit kernels
 
 // Motion bits of 4 pixels: bit i of the result is set iff |c_i - p_i| > thr,
 // with the threshold test done bytewise: for d = |c - p| (per byte), d > thr
@@ -65,7 +65,8 @@ __device__ inline void md_plan_dev(const MdArgs& a) {
 }
 
 
-constexpr int kMdRows = 32;               // strip height: two tile rows
+constexpr int kMdTileRows = 3;           // tile rows per strip
+constexpr int kMdRows = 16 * kMdTileRows; // strip height
 constexpr int kMdWalk = kMdRows + 4;      // rows walked per strip (2-row halo each side)
 constexpr int kMdOwned = 30;              // tile columns owned per warp (lanes 1..30)
 constexpr int kMdWarpsPerCta = 4;
@@ -106,7 +107,7 @@ __device__ __forceinline__ uint32_t right_nb(uint32_t v, uint32_t right) {   // 
   return ((v >> 1) & 0x7fff7fffu) | ((right << 15) & 0x80008000u);
 }
 
-// One warp = one worker.  Work unit = (32-row strip, band of 30 tile columns,
+// One warp = one worker.  Work unit = (48-row strip, band of 30 tile columns,
 // chunk of up to F consecutive frames, F even).  Lane l covers tile column
 // 30*band - 1 + l; lanes 0 and 31 are halo lanes that only supply neighbour
 // bits.  The warp walks the strip's rows plus a 2-row halo; for every row it
@@ -152,27 +153,34 @@ __device__ inline void md_unit(const MdArgs& a, uint64_t slot_cur0, uint64_t slo
   for (int q = 0; q < NP; ++q) hb1[q] = hb2[q] = he1[q] = he2[q] = 0;
 #pragma unroll
   for (int t = 0; t < F; ++t) cn[t] = 0;
+  // rows are software-pipelined: row r+1's loads are issued before row r is processed
+  uint4 qc[F], qp0, qp1, nc[F], np0, np1;
+  auto load_row = [&](int rr, uint4 (&c)[F], uint4& p0v, uint4& p1v) {
+    const int yy = y0 - 2 + rr;
+    const bool l = col_in && yy >= 0 && yy < H && rr < kMdWalk;
+    const size_t o = (size_t)yy * W + col_off;
+    const uint8_t* crow = cbase + o;
+#pragma unroll
+    for (int t = 0; t < F; ++t) {
+      c[t] = make_uint4(0, 0, 0, 0);
+      if (l && t < nf) c[t] = ld16<NC>(crow + coff[t]);
+    }
+    p0v = p1v = make_uint4(0, 0, 0, 0);
+    if (l) p0v = ld16<NC>(p0 + o);
+    if constexpr (F == 2) {
+      if (l && nf > 1) p1v = ld16<NC>(p1 + o);
+    }
+  };
+  load_row(0, qc, qp0, qp1);
 #pragma unroll 1
   for (int r = 0; r < kMdWalk; ++r) {
     const int y = y0 - 2 + r;
     const bool ld = col_in && y >= 0 && y < H;
-    const size_t off = (size_t)y * W + col_off;
-    uint4 qc[F], qp0, qp1;
-    qp0 = qp1 = make_uint4(0, 0, 0, 0);
-    const uint8_t* crow = cbase + off;
-#pragma unroll
-    for (int t = 0; t < F; ++t) {
-      qc[t] = make_uint4(0, 0, 0, 0);
-      if (ld && t < nf) qc[t] = ld16<NC>(crow + coff[t]);
-    }
-    if (ld) qp0 = ld16<NC>(p0 + off);
-    if constexpr (F == 2) {
-      if (ld && nf > 1) qp1 = ld16<NC>(p1 + off);
-    }
+    load_row(r + 1, nc, np0, np1);
     const int ye = y - 1, yo = y - 2;
     const bool e_in = r >= 2 && col_in && ye >= 0 && ye < H;
     const bool o_in = r >= 4 && yo < H;
-    const int sh = (r - 4 < 16) ? 0 : 16;
+    const int sh = 10 * ((r - 4) >> 4);              // 10-bit count field of this tile row
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
       const int ta = 2 * q, tb = 2 * q + 1;
@@ -197,22 +205,26 @@ __device__ inline void md_unit(const MdArgs& a, uint64_t slot_cur0, uint64_t slo
       he2[q] = he1[q];
       he1[q] = drow;
     }
+#pragma unroll
+    for (int t = 0; t < F; ++t) qc[t] = nc[t];
+    qp0 = np0;
+    qp1 = np1;
   }
-  // two tile rows per lane and frame
-  const int ty0 = 2 * strip;
-  const bool second = ty0 + 1 < a.tiles_y;
+  // kMdTileRows tile rows per lane and frame (counts <= 256 in 10-bit fields)
+  const int ty0 = kMdTileRows * strip;
 #pragma unroll
   for (int t = 0; t < F; ++t) {
     if (t >= nf) break;
     const uint64_t j = j0 + t;
     uint16_t* cnt = a.counts + j * a.n_tiles;
-    const uint32_t lo = cn[t] & 0xffffu, hi = cn[t] >> 16;
-    if (owned) {
-      cnt[(size_t)ty0 * a.tiles_x + col] = (uint16_t)lo;
-      if (second) cnt[(size_t)(ty0 + 1) * a.tiles_x + col] = (uint16_t)hi;
+    uint32_t nz = 0;
+#pragma unroll
+    for (int tr = 0; tr < kMdTileRows; ++tr) {
+      const uint32_t c = (cn[t] >> (10 * tr)) & 0x3ffu;
+      const bool in = owned && ty0 + tr < a.tiles_y;
+      if (in) cnt[(size_t)(ty0 + tr) * a.tiles_x + col] = (uint16_t)c;
+      nz += __popc(__ballot_sync(0xffffffffu, in && c));
     }
-    const uint32_t nz = __popc(__ballot_sync(0xffffffffu, owned && lo)) +
-                        __popc(__ballot_sync(0xffffffffu, owned && second && hi));
     if (lane == 0 && nz) atomicAdd(&a.frame_tot[j], nz);
   }
 }
@@ -242,21 +254,27 @@ __device__ inline void md_main_dev(const MdArgs& a, Grid g) {
   }
 }
 
-__device__ inline void md_finish_dev(const MdArgs& a) {
-  uint64_t* frame_off = a.frame_off;
+// Record emission for frame j (one CTA): the exclusive scan of the per-frame
+// record totals gives the frame's record offset and the exact number of enabled
+// firings n (firing i is enabled iff r_max record slots are free before it);
+// frames j < n scatter their records in raster order and their count token.
+// The CTA with lead = true commits the counters.
+__device__ inline void md_emit_frame(const MdArgs& a, uint64_t j, bool lead) {
   __shared__ uint64_t sw[32];
-  __shared__ uint64_t s_n;
-  MdPlanHdr* pl = a.plan;
-  const uint64_t n_cand = pl->n_cand;
-  const uint64_t free_rec = pl->free_rec;
-  if (threadIdx.x == 0) s_n = n_cand;
+  __shared__ unsigned long long s_n;
+  __shared__ uint64_t s_off, s_used;
+  const MdPlanHdr pl = *a.plan;
+  const uint64_t n_cand = pl.n_cand;
+  if (threadIdx.x == 0) {
+    s_n = n_cand;
+    s_off = 0;
+  }
   __syncthreads();
   uint64_t carry = 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (uint64_t base = 0; base < n_cand; base += blockDim.x) {
     const uint64_t i = base + threadIdx.x;
     const uint64_t v = i < n_cand ? a.frame_tot[i] : 0;
-    // exclusive scan (block)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint64_t x = v;
     for (int o = 1; o < 32; o <<= 1) {
       const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -265,70 +283,73 @@ __device__ inline void md_finish_dev(const MdArgs& a) {
     if (lane == 31) sw[wid] = x;
     __syncthreads();
     if (wid == 0) {
-      uint64_t s = lane < nw ? sw[lane] : 0;
+      uint64_t t = lane < nw ? sw[lane] : 0;
       for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += y;
+        const uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
       }
-      if (lane < nw) sw[lane] = s;
+      if (lane < nw) sw[lane] = t;
     }
     __syncthreads();
     const uint64_t off = carry + (wid ? sw[wid - 1] : 0) + x - v;
     const uint64_t tot = sw[nw - 1];
     __syncthreads();
     if (i < n_cand) {
-      frame_off[i] = off;
-      // firing i is enabled iff r_max record slots are free before it
-      if (off + (uint64_t)a.n_tiles > free_rec) atomicMin((unsigned long long*)&s_n, i);
+      if (off + (uint64_t)a.n_tiles > pl.free_rec) atomicMin(&s_n, (unsigned long long)i);
+      if (i == j) s_off = off;
+      if (lead) a.frame_off[i] = off;
     }
     carry += tot;
-    __syncthreads();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const uint64_t n = s_n;
-    const uint64_t used = n < n_cand ? frame_off[n] : carry;
-    frame_off[n] = used;
-    pl->n_cand = n;                 // the scatter kernel handles exactly n firings
+  const uint64_t n = s_n;
+  if (lead && threadIdx.x == 0) s_used = n < n_cand ? a.frame_off[n] : carry;   // records of frames < n
+  __syncthreads();
+  if (lead && threadIdx.x == 0) {
     uint64_t* ctr = a.ctr;
-    *rd_ptr(ctr, a.cur.id) = pl->rd_cur0 + n;
-    *rd_ptr(ctr, a.prev.id) = pl->rd_prev0 + n;
-    *wr_ptr(ctr, a.cnt.id) = pl->wr_cnt0 + n;
-    *wr_ptr(ctr, a.rec.id) = pl->wr_rec0 + used;
+    *rd_ptr(ctr, a.cur.id) = pl.rd_cur0 + n;
+    *rd_ptr(ctr, a.prev.id) = pl.rd_prev0 + n;
+    *wr_ptr(ctr, a.cnt.id) = pl.wr_cnt0 + n;
+    *wr_ptr(ctr, a.rec.id) = pl.wr_rec0 + s_used;
     atomicAdd(&a.eng->fired_step, (unsigned long long)n);
     atomicAdd(&a.eng->fired_total, (unsigned long long)n);
   }
-}
-
-__device__ inline void md_scatter_frame(const MdArgs& a, uint64_t j) {
-  const uint64_t* frame_off = a.frame_off;
-  __shared__ uint32_t sw[32];
-  const MdPlanHdr pl = *a.plan;
+  if (j >= n) return;
+  // raster-order compaction of the tiles of frame j with count > 0
+  __shared__ uint32_t sw32[32];
   const int nt = a.n_tiles;
   const int per = (nt + (int)blockDim.x - 1) / (int)blockDim.x;
   const int t0 = threadIdx.x * per, t1 = min(nt, t0 + per);
   const uint16_t* cnt = a.counts + j * nt;
   uint32_t mine = 0;
-  for (int t = t0; t < t1; ++t) mine += cnt[t] > 0;
-  // exclusive scan of `mine` over the block
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool vec = (per % 8) == 0 && (nt % 8) == 0;          // 16-byte aligned runs of 8 counts
+  if (vec) {
+    for (int t = t0; t < t1; t += 8) {
+      const uint4 q = *reinterpret_cast<const uint4*>(cnt + t);
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) mine += ((w[k] & 0xffffu) != 0) + ((w[k] >> 16) != 0);
+    }
+  } else {
+    for (int t = t0; t < t1; ++t) mine += cnt[t] > 0;
+  }
   uint32_t x = mine;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) sw[wid] = x;
+  if (lane == 31) sw32[wid] = x;
   __syncthreads();
   if (wid == 0) {
-    uint32_t s = lane < nw ? sw[lane] : 0;
+    uint32_t t = lane < nw ? sw32[lane] : 0;
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
     }
-    if (lane < nw) sw[lane] = s;
+    if (lane < nw) sw32[lane] = t;
   }
   __syncthreads();
-  uint64_t pos = pl.wr_rec0 + frame_off[j] + (wid ? sw[wid - 1] : 0) + x - mine;
+  uint64_t pos = pl.wr_rec0 + s_off + (wid ? sw32[wid - 1] : 0) + x - mine;
   for (int t = t0; t < t1; ++t) {
     const uint32_t c = cnt[t];
     if (c > 0) {
@@ -344,11 +365,12 @@ __device__ inline void md_scatter_frame(const MdArgs& a, uint64_t j) {
     *reinterpret_cast<uint32_t*>(slot_ptr(a.cnt, pl.wr_cnt0 + j)) = a.frame_tot[j];
 }
 
-// Scatter phase over a virtual grid: one CTA per frame.
-__device__ inline void md_scatter_dev(const MdArgs& a, Grid g) {
+// Emission phase over a virtual grid: one CTA per frame (block 0 commits).
+__device__ inline void md_emit_dev(const MdArgs& a, Grid g) {
   const uint64_t n = a.plan->n_cand;
-  for (uint64_t j = g.b; j < n; j += g.n) {
-    md_scatter_frame(a, j);
+  const uint64_t span = n > 0 ? n : 1;
+  for (uint64_t j = g.b; j < span; j += g.n) {
+    md_emit_frame(a, j, j == 0);
     __syncthreads();
   }
 }

@@ -96,9 +96,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp*
         if (a.shared_rows) md_main_dev<8, false>(a, g);
         else md_main_dev<2, false>(a, g);
         if (!grid_barrier(eng, nb, limit_ns)) return;
-        if (lead) md_finish_dev(a);
-        if (!grid_barrier(eng, nb, limit_ns)) return;
-        md_scatter_dev(a, g);
+        md_emit_dev(a, g);
       }
       if (!grid_barrier(eng, nb, limit_ns)) return;
     }
