@@ -130,26 +130,19 @@ class ClockSampler:
 
 # ----------------------------------------------------------- distributed ----
 def dist_setup(args):
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1611_03226_b300 import ranks
+    return ranks.world()
 
 
 def max_over_ranks(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1611_03226_b300 import ranks
+    return ranks.max_over_ranks(x) if ws > 1 else x
 
 
 def barrier(ws):
+    from paper_1611_03226_b300 import ranks
     if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+        ranks.barrier()
 
 
 # ------------------------------------------------------------ workloads ----
