@@ -7,6 +7,7 @@
 // free = cap - (wr - rd) are exact at any time.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/dfgpu.h"
@@ -179,9 +180,22 @@ cudaError_t dpd_prepare();     // one-time kernel attributes (outside graph capt
 
 cudaError_t launch_dyn(const DynArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                        cudaEvent_t ev1 = nullptr);
-cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                           cudaEvent_t ev1 = nullptr);
+struct MdTmaGeom {
+  int pitch;                 // staged bytes per row: panel pixels + 2 halo tile columns
+};
+struct MdTma {               // tensor maps of the frame rings for the TMA main kernel
+  CUtensorMap unit;          // current ring, all frames of a work unit per box
+  CUtensorMap cur, prev;     // one frame per box
+  MdTmaGeom geo;
+  size_t smem;               // dynamic shared memory of a CTA
+  int blocks_per_sm;
+  int ok;                    // 0: the register-staged main kernel runs instead
+};
+cudaError_t launch_md_step(const MdArgs& a, const MdTma* tma, int n_sm, cudaStream_t s,
+                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 cudaError_t md_prepare(int W);     // one-time kernel attributes (outside graph capture)
+cudaError_t md_tma_prepare(const MdArgs& a, MdTma* t);   // tensor maps + attributes
+void launch_md_main_tma(const MdArgs& a, const MdTma& t, int n_sm, cudaStream_t s);
 size_t md_smem_bytes(int W);
 
 cudaError_t persistent_prepare(size_t smem);

@@ -36,11 +36,13 @@ cudaError_t md_prepare(int W) {
   return cudaSuccess;
 }
 
-cudaError_t launch_md_step(const MdArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0,
-                           cudaEvent_t ev1) {
+cudaError_t launch_md_step(const MdArgs& a, const MdTma* tma, int n_sm, cudaStream_t s,
+                           cudaEvent_t ev0, cudaEvent_t ev1) {
   k_md_plan<<<1, 256, 0, s>>>(a);
   if (ev0) cudaEventRecord(ev0, s);
-  if (a.shared_rows)
+  if (tma && tma->ok)
+    launch_md_main_tma(a, *tma, n_sm, s);
+  else if (a.shared_rows)
     k_md_main<kMdFrames><<<n_sm * std::max(g_md_blocks_per_sm[0], 1), kMdWarpsPerCta * 32, 0, s>>>(a);
   else
     k_md_main<2><<<n_sm * std::max(g_md_blocks_per_sm[1], 1), kMdWarpsPerCta * 32, 0, s>>>(a);

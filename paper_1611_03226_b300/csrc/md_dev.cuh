@@ -27,14 +27,27 @@ namespace dfg {
 
 constexpr int kMdThreads = 256;     // plan and emit kernels
 
-// Motion bits of 4 pixels: bit i of the result is set iff |c_i - p_i| > thr,
-// with the threshold test done bytewise: for d = |c - p| (per byte), d > thr
-// iff d >= 128 or (d & 0x7f) + (127 - thr) carries into bit 7.  The four byte
-// MSBs (bits 7, 15, 23, 31) are then gathered into bits 28..31 by one multiply.
-__device__ __forceinline__ uint32_t motion_nibble_hi(uint32_t c, uint32_t p, uint32_t add4) {
-  const uint32_t d = __vabsdiffu4(c, p);
-  const uint32_t m = (d | ((d & 0x7f7f7f7fu) + add4)) & 0x80808080u;
-  return m * 0x00204081u;                 // bits 28..31 = pixels 0..3
+// Bytewise threshold test.  For d = |c - p| (per byte) and threshold t:
+//   t <= 127:  d > t  iff  d >= 128  or  (d & 0x7f) + (127 - t) carries into bit 7;
+//   t >= 128:  d > t  iff  d >= 128  and (d & 0x7f) + (255 - t) carries into bit 7.
+// add4 holds (127 - t) mod 128 in every byte; or4 is 0x80808080 when either
+// condition suffices (t <= 127) and 0 when both are needed (t >= 128).
+struct ThrCode {
+  uint32_t add4, or4;
+};
+__host__ __device__ inline ThrCode thr_code(int t) {
+  return {0x01010101u * (uint32_t)((127 - t) & 127), t <= 127 ? 0x80808080u : 0u};
+}
+// Byte MSBs (bits 7, 15, 23, 31) set where d > t, all other bits clear.
+__device__ __forceinline__ uint32_t over_thr_msb(uint32_t d, ThrCode k) {
+  const uint32_t s = (d & 0x7f7f7f7fu) + k.add4;
+  return ((d & s) | ((d | s) & k.or4)) & 0x80808080u;
+}
+
+// Motion bits of 4 pixels: the four byte MSBs of the threshold test are
+// gathered into bits 28..31 (pixels 0..3) by one multiply.
+__device__ __forceinline__ uint32_t motion_nibble_hi(uint32_t c, uint32_t p, ThrCode k) {
+  return over_thr_msb(__vabsdiffu4(c, p), k) * 0x00204081u;
 }
 
 __device__ inline void md_plan_dev(const MdArgs& a) {
@@ -73,12 +86,12 @@ constexpr int kMdWarpsPerCta = 4;
 constexpr int kMdFrames = 8;              // frames per work unit
 
 // 16 pixels (one tile column of one row) -> 16 motion bits, bit i = pixel i.
-__device__ __forceinline__ uint32_t motion_bits16(uint4 c, uint4 p, uint32_t add4) {
+__device__ __forceinline__ uint32_t motion_bits16(uint4 c, uint4 p, ThrCode tc) {
   uint32_t acc = 0;
-  acc = __funnelshift_l(motion_nibble_hi(c.w, p.w, add4), acc, 4);
-  acc = __funnelshift_l(motion_nibble_hi(c.z, p.z, add4), acc, 4);
-  acc = __funnelshift_l(motion_nibble_hi(c.y, p.y, add4), acc, 4);
-  acc = __funnelshift_l(motion_nibble_hi(c.x, p.x, add4), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.w, p.w, tc), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.z, p.z, tc), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.y, p.y, tc), acc, 4);
+  acc = __funnelshift_l(motion_nibble_hi(c.x, p.x, tc), acc, 4);
   return acc;
 }
 
@@ -121,7 +134,7 @@ __device__ __forceinline__ uint32_t right_nb(uint32_t v, uint32_t right) {   // 
 // frame.
 template <int F, bool NC>
 __device__ inline void md_unit(const MdArgs& a, uint64_t slot_cur0, uint64_t slot_prev0, int strip,
-                        int band, uint64_t j0, int nf, uint32_t add4) {
+                        int band, uint64_t j0, int nf, ThrCode tc) {
   static_assert(F % 2 == 0, "frames are processed in pairs");
   constexpr int NP = F / 2;
   const int W = a.W, H = a.H;
@@ -186,7 +199,7 @@ __device__ inline void md_unit(const MdArgs& a, uint64_t slot_cur0, uint64_t slo
       const int ta = 2 * q, tb = 2 * q + 1;
       const uint4 pa = ta == 0 ? qp0 : qc[ta - 1];
       const uint4 pb = F == 2 ? qp1 : qc[ta];
-      const uint32_t b = ld ? (motion_bits16(qc[ta], pa, add4) | (motion_bits16(qc[tb], pb, add4) << 16))
+      const uint32_t b = ld ? (motion_bits16(qc[ta], pa, tc) | (motion_bits16(qc[tb], pb, tc) << 16))
                             : 0xffffffffu;
       const uint32_t bl = __shfl_up_sync(0xffffffffu, b, 1);
       const uint32_t br = __shfl_down_sync(0xffffffffu, b, 1);
@@ -242,7 +255,7 @@ __device__ inline void md_main_dev(const MdArgs& a, Grid g) {
   const uint64_t chunks = (n + F - 1) / F;
   const uint64_t units = pairs * chunks;
   const uint64_t G = (uint64_t)g.n * wpc;
-  const uint32_t add4 = 0x01010101u * (uint32_t)(127 - a.thr);
+  const ThrCode tc = thr_code(a.thr);
   const uint64_t slot_cur0 = pl.rd_cur0 % a.cur.cap, slot_prev0 = pl.rd_prev0 % a.prev.cap;
   for (uint64_t u = g.b * (uint64_t)wpc + (threadIdx.x >> 5); u < units; u += G) {
     const uint32_t pair = (uint32_t)(u % pairs);
@@ -250,7 +263,7 @@ __device__ inline void md_main_dev(const MdArgs& a, Grid g) {
     const uint64_t j0 = chunk * F;
     const uint64_t left = n - j0;
     const int nf = left < (uint64_t)F ? (int)left : F;
-    md_unit<F, NC>(a, slot_cur0, slot_prev0, (int)(pair / bands), (int)(pair % bands), j0, nf, add4);
+    md_unit<F, NC>(a, slot_cur0, slot_prev0, (int)(pair / bands), (int)(pair % bands), j0, nf, tc);
   }
 }
 

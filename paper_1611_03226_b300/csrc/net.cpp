@@ -46,6 +46,7 @@ struct Op {
   OpKind kind;
   CopyArgs copy{};
   MdArgs md{};
+  MdTma md_tma{};
   DynArgs dyn{};
   DpdArgs* dpd_dev = nullptr;        // group args (device)
   int dpd_n = 0;                      // actors in the group
@@ -305,7 +306,7 @@ df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
       }
       case kOpMd: {
         const auto ev = prof_pair(net, DF_PROF_MD_MAIN, capturing);
-        DF_CUDA(launch_md_step(op.md, net->n_sm, s, ev.first, ev.second));
+        DF_CUDA(launch_md_step(op.md, &op.md_tma, net->n_sm, s, ev.first, ev.second));
         break;
       }
       case kOpDyn:
@@ -814,8 +815,11 @@ df_status df_net_finalize(df_net* net) {
   }
   flush_group();
   if (!dp.empty()) DF_CUDA(dpd_prepare());  // also covers branch FIR actors
-  for (const Op& op : net->program)
-    if (op.kind == kOpMd) DF_CUDA(md_prepare(op.md.W));
+  for (Op& op : net->program)
+    if (op.kind == kOpMd) {
+      DF_CUDA(md_prepare(op.md.W));
+      DF_CUDA(md_tma_prepare(op.md, &op.md_tma));
+    }
   DF_CUDA(cudaStreamSynchronize(s));
   net->finalized = true;
   return DF_OK;
@@ -1064,7 +1068,7 @@ df_status df_autotune(df_net* net, uint64_t* n_firings) {
     if (op.kind == kOpCopy) {
       DF_CUDA(launch_copy(op.copy, net->n_sm, s));
     } else if (op.kind == kOpMd) {
-      DF_CUDA(launch_md_step(op.md, net->n_sm, s));
+      DF_CUDA(launch_md_step(op.md, &op.md_tma, net->n_sm, s));
     } else if (op.kind == kOpDyn) {
       DF_CUDA(launch_dyn(op.dyn, net->n_sm, s));
     } else {

@@ -264,3 +264,20 @@ def flat_with_rect(height: int, width: int, n_frames: int, rect_w: int, rect_h: 
         x = x0 + dx * t
         out[t, y0:y0 + rect_h, max(x, 0):max(x + rect_w, 0)] = fg
     return out
+
+
+def uniform_frames(n_frames: int, height: int, width: int, seed: int = BASE_SEED + 5) -> np.ndarray:
+    """Frames of independent uniform bytes: pixel differences cover 0..255, so
+    every threshold has pixels just below, at and just above it."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 256, size=(n_frames, height, width), dtype=np.uint8)
+
+
+def blocky_frames(n_frames: int, height: int, width: int, block: int = 4,
+                  seed: int = BASE_SEED + 6) -> np.ndarray:
+    """Frames of uniform random bytes constant over block x block squares: with
+    high thresholds the motion mask keeps areas that survive the 3x3 erosion."""
+    rng = np.random.default_rng(seed)
+    hb, wb = -(-height // block), -(-width // block)
+    small = rng.integers(0, 256, size=(n_frames, hb, wb), dtype=np.uint8)
+    return np.repeat(np.repeat(small, block, axis=1), block, axis=2)[:, :height, :width].copy()

@@ -16,10 +16,11 @@ def Net():
     return Net
 
 
-def stream_both(Net, frames, cap, chunk, rec_capacity=None, separate=False, prev_init=None, flags=0):
+def stream_both(Net, frames, cap, chunk, rec_capacity=None, separate=False, prev_init=None, flags=0,
+                t=25):
     T, H, W = frames.shape
-    onet, oi = ON.motion_fused(H, W, cap, rec_capacity, prev_init=prev_init)
-    enet, ei = EN.motion_fused(Net, H, W, cap, rec_capacity, prev_init=prev_init,
+    onet, oi = ON.motion_fused(H, W, cap, rec_capacity, t=t, prev_init=prev_init)
+    enet, ei = EN.motion_fused(Net, H, W, cap, rec_capacity, t=t, prev_init=prev_init,
                                separate_prev_source=separate)
     ro, co, re_, ce = [], [], [], []
     i, idle = 0, 0
@@ -54,6 +55,9 @@ def stream_both(Net, frames, cap, chunk, rec_capacity=None, separate=False, prev
     (16, 32, 5, 2, 1),          # one strip, one word
     (37, 64, 6, 4, 3),
     (1080, 1920, 6, 4, 4),      # full-size frames
+    (100, 544, 23, 11, 9),      # two bands (the second partial), units across the ring's end, odd chunks
+    (50, 1024, 17, 17, 17),     # three bands, 8-frame units from the first frame on
+    (1080, 1920, 19, 10, 10),   # full-size frames, 8-frame units across the ring's end
 ])
 def test_motion_parity(Net, H, W, T, cap, chunk):
     w = synth.motion(n_frames=T, height=H, width=W)
@@ -62,6 +66,22 @@ def test_motion_parity(Net, H, W, T, cap, chunk):
     np.testing.assert_array_equal(ce, co)
     np.testing.assert_array_equal(re_, ro)
     assert ce.sum() == len(re_)
+
+
+@pytest.mark.parametrize("t", [0, 1, 126, 127, 128, 129, 200, 254, 255])
+@pytest.mark.parametrize("separate,flags", [(False, 0), (True, 0), (False, "persistent")])
+def test_motion_thresholds(Net, t, separate, flags):
+    """Every threshold class of the bytewise compare (below, at and above 128),
+    on frames whose pixel differences span 0..255, through the shared-row
+    kernel, the separate-previous-frame kernel and the persistent kernel."""
+    from paper_1611_03226_b300 import _lib as L
+    f = synth.blocky_frames(10, 40, 96) if t >= 120 else synth.uniform_frames(10, 40, 96)
+    fl = L.DF_RUN_PERSISTENT if flags == "persistent" else 0
+    ro, co, re_, ce = stream_both(Net, f, 9, 9, separate=separate, flags=fl, t=t)
+    np.testing.assert_array_equal(ce, co)
+    np.testing.assert_array_equal(re_, ro)
+    if t <= 127:
+        assert len(re_) > 0
 
 
 def test_motion_without_dedup(Net):
