@@ -255,8 +255,8 @@ def bench_motion(args, P, torch, pk, ws):
         "launch_mode": "CUDA graph replay of one engine step",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
-                     "traffic": profiled_traffic("k_md_main__motion_300x1920x1080.md") if T == 300 else None,
-                     "kernel": "k_md_main", "algorithmic_bytes_per_launch": alg_bytes,
+                     "traffic": profiled_traffic("k_md_main_tma__motion_300x1920x1080.md") if T == 300 else None,
+                     "kernel": "k_md_main_tma", "algorithmic_bytes_per_launch": alg_bytes,
                      "peak_source": pk["source"]},
         "e2e": {"value": ws * T / e2e_s, "unit": "frames/s",
                 "h2d_bytes_per_step": T * W * H,
