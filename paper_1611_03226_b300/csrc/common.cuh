@@ -165,6 +165,33 @@ struct PersistOp {            // one entry of the device-side step program
   const void* args;           // CopyArgs / DpdArgs[n] / DynArgs / MdArgs in device memory
 };
 
+// --------------------------------------- programmatic dependent launch ----
+// A kernel launched with programmatic stream serialisation may start while
+// the previous kernel of the stream is still running; it must wait for that
+// kernel's completion and memory (griddep_wait) before it touches any data an
+// earlier kernel writes.  griddep_launch lets the next such kernel start.
+// Both are no-ops for a kernel launched the ordinary way.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // ----------------------------------------------------------- launchers ----
 cudaError_t launch_set_u64(uint64_t* p, uint64_t v, cudaStream_t s);
 cudaError_t launch_add_u64(uint64_t* p, uint64_t v, cudaStream_t s);
@@ -195,7 +222,7 @@ cudaError_t launch_md_step(const MdArgs& a, const MdTma* tma, int n_sm, cudaStre
                            cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 cudaError_t md_prepare(int W);     // one-time kernel attributes (outside graph capture)
 cudaError_t md_tma_prepare(const MdArgs& a, MdTma* t);   // tensor maps + attributes
-void launch_md_main_tma(const MdArgs& a, const MdTma& t, int n_sm, cudaStream_t s);
+cudaError_t launch_md_main_tma(const MdArgs& a, const MdTma& t, int n_sm, cudaStream_t s, bool pdl);
 size_t md_smem_bytes(int W);
 
 cudaError_t persistent_prepare(size_t smem);

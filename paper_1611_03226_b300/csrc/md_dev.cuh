@@ -245,7 +245,11 @@ __device__ inline void md_unit(const MdArgs& a, uint64_t slot_cur0, uint64_t slo
 template <int F, bool NC>
 __device__ inline void md_main_dev(const MdArgs& a, Grid g) {
   const int wpc = blockDim.x >> 5;                           // warps per CTA
-  const MdPlanHdr pl = *a.plan;
+  __shared__ MdPlanHdr s_pl;
+  __syncthreads();                    // s_pl may still be read by a previous phase
+  if (threadIdx.x == 0) s_pl = *a.plan;
+  __syncthreads();
+  const MdPlanHdr pl = s_pl;
   const uint64_t n = pl.n_cand;
   if (n == 0) return;
   const int cols = a.W / 16;
@@ -274,21 +278,72 @@ __device__ inline void md_main_dev(const MdArgs& a, Grid g) {
 // The CTA with lead = true commits the counters.
 __device__ inline void md_emit_frame(const MdArgs& a, uint64_t j, bool lead) {
   __shared__ uint64_t sw[32];
+  __shared__ uint32_t sw32[32];
   __shared__ unsigned long long s_n;
   __shared__ uint64_t s_off, s_used;
-  const MdPlanHdr pl = *a.plan;
-  const uint64_t n_cand = pl.n_cand;
+  __shared__ MdPlanHdr s_pl;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+  // The loads of this frame's tile counts and of the first frame totals are
+  // issued first: neither depends on the plan (frames past the candidates are
+  // masked later), so their latency overlaps the plan's.
+  // Tiles: warp w takes a contiguous run, 8 per lane per step (one 16-byte
+  // load); the first kCache steps stay in registers for both passes.
+  const int nt = a.n_tiles;
+  const uint16_t* cnt = a.counts + j * nt;
+  const bool vec = (nt % 8) == 0;                          // 16-byte aligned groups of 8 counts
+  const int per_lane = vec ? 8 : 1;
+  const int step = 32 * per_lane;                          // tiles per warp and step
+  const int run = ((nt + nw * step - 1) / (nw * step)) * step;
+  const int r0 = wid * run, r1 = min(nt, r0 + run);
+  constexpr int kCache = 4;
+  auto load_q = [&](int t) {
+    uint4 q = make_uint4(0, 0, 0, 0);
+    if (t < r1) {
+      if (vec) q = *reinterpret_cast<const uint4*>(cnt + t);
+      else q.x = cnt[t];
+    }
+    return q;
+  };
+  uint4 qc[kCache];
+#pragma unroll
+  for (int i = 0; i < kCache; ++i) qc[i] = load_q(r0 + i * step + lane * per_lane);
+  // Frame totals: thread t takes kFr consecutive frames per pass.
+  constexpr int kFr = 4;
+  const uint64_t chunk = (uint64_t)kFr * blockDim.x;
+  uint32_t tv[kFr];
+#pragma unroll
+  for (int q = 0; q < kFr; ++q) {
+    const uint64_t i = (uint64_t)threadIdx.x * kFr + q;
+    tv[q] = i < a.n_max ? a.frame_tot[i] : 0u;
+  }
+  // one load of the plan per CTA (every CTA of the phase reads the same line)
   if (threadIdx.x == 0) {
-    s_n = n_cand;
+    s_pl = *a.plan;
+    s_n = s_pl.n_cand;
     s_off = 0;
   }
   __syncthreads();
+  const MdPlanHdr pl = s_pl;
+  const uint64_t n_cand = pl.n_cand;
+  if (j > 0 && j >= n_cand) return;                        // no such candidate frame
+
+  // Exclusive scan of the frame totals: frame i's first record, and the
+  // enabled firings (firing i needs r_max free record slots before it).
   uint64_t carry = 0;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (uint64_t base = 0; base < n_cand; base += blockDim.x) {
-    const uint64_t i = base + threadIdx.x;
-    const uint64_t v = i < n_cand ? a.frame_tot[i] : 0;
-    uint64_t x = v;
+  for (uint64_t base = 0; base < n_cand; base += chunk) {
+    if (base > 0) {
+#pragma unroll
+      for (int q = 0; q < kFr; ++q) {
+        const uint64_t i = base + (uint64_t)threadIdx.x * kFr + q;
+        tv[q] = i < a.n_max ? a.frame_tot[i] : 0u;
+      }
+    }
+    const uint64_t i0 = base + (uint64_t)threadIdx.x * kFr;
+    uint64_t mine = 0;
+#pragma unroll
+    for (int q = 0; q < kFr; ++q) mine += i0 + q < n_cand ? tv[q] : 0u;
+    uint64_t x = mine;
     for (int o = 1; o < 32; o <<= 1) {
       const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
@@ -304,13 +359,18 @@ __device__ inline void md_emit_frame(const MdArgs& a, uint64_t j, bool lead) {
       if (lane < nw) sw[lane] = t;
     }
     __syncthreads();
-    const uint64_t off = carry + (wid ? sw[wid - 1] : 0) + x - v;
+    uint64_t off = carry + (wid ? sw[wid - 1] : 0) + x - mine;
     const uint64_t tot = sw[nw - 1];
     __syncthreads();
-    if (i < n_cand) {
-      if (off + (uint64_t)a.n_tiles > pl.free_rec) atomicMin(&s_n, (unsigned long long)i);
-      if (i == j) s_off = off;
-      if (lead) a.frame_off[i] = off;
+#pragma unroll
+    for (int q = 0; q < kFr; ++q) {
+      const uint64_t i = i0 + q;
+      if (i < n_cand) {
+        if (off + (uint64_t)a.n_tiles > pl.free_rec) atomicMin(&s_n, (unsigned long long)i);
+        if (i == j) s_off = off;
+        if (lead) a.frame_off[i] = off;
+        off += tv[q];
+      }
     }
     carry += tot;
   }
@@ -328,30 +388,34 @@ __device__ inline void md_emit_frame(const MdArgs& a, uint64_t j, bool lead) {
     atomicAdd(&a.eng->fired_total, (unsigned long long)n);
   }
   if (j >= n) return;
-  // raster-order compaction of the tiles of frame j with count > 0
-  __shared__ uint32_t sw32[32];
-  const int nt = a.n_tiles;
-  const int per = (nt + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int t0 = threadIdx.x * per, t1 = min(nt, t0 + per);
-  const uint16_t* cnt = a.counts + j * nt;
-  uint32_t mine = 0;
-  const bool vec = (per % 8) == 0 && (nt % 8) == 0;          // 16-byte aligned runs of 8 counts
-  if (vec) {
-    for (int t = t0; t < t1; t += 8) {
-      const uint4 q = *reinterpret_cast<const uint4*>(cnt + t);
-      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+
+  // Raster-order compaction of the tiles of frame j with count > 0: pass 1
+  // counts each warp's records, a block scan gives each warp its first record,
+  // pass 2 writes the records (a lane's in order after those of the lanes
+  // below it).
+  auto counts8 = [&](const uint4 q, uint32_t (&c)[8]) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) mine += ((w[k] & 0xffffu) != 0) + ((w[k] >> 16) != 0);
-    }
-  } else {
-    for (int t = t0; t < t1; ++t) mine += cnt[t] > 0;
-  }
-  uint32_t x = mine;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sw32[wid] = x;
+    for (int k = 0; k < 8; ++k) c[k] = (w[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+  };
+  // step i's counts: registers for the first kCache steps, else a new load
+  // (the cached loop is unrolled so that qc is indexed by constants)
+  auto for_steps = [&](auto&& f) {
+    const int steps = r1 > r0 ? (r1 - r0 + step - 1) / step : 0;
+#pragma unroll
+    for (int i = 0; i < kCache; ++i)
+      if (i < steps) f(i, qc[i]);
+    for (int i = kCache; i < steps; ++i) f(i, load_q(r0 + i * step + lane * per_lane));
+  };
+  uint32_t mine = 0;
+  for_steps([&](int, const uint4 q) {
+    uint32_t c[8];
+    counts8(q, c);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) mine += c[k] != 0;
+  });
+  const uint32_t warp_tot = __reduce_add_sync(0xffffffffu, mine);
+  if (lane == 0) sw32[wid] = warp_tot;
   __syncthreads();
   if (wid == 0) {
     uint32_t t = lane < nw ? sw32[lane] : 0;
@@ -359,21 +423,47 @@ __device__ inline void md_emit_frame(const MdArgs& a, uint64_t j, bool lead) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += y;
     }
-    if (lane < nw) sw32[lane] = t;
+    if (lane < nw) sw32[lane] = t;                         // inclusive
   }
   __syncthreads();
-  uint64_t pos = pl.wr_rec0 + s_off + (wid ? sw32[wid - 1] : 0) + x - mine;
-  for (int t = t0; t < t1; ++t) {
-    const uint32_t c = cnt[t];
-    if (c > 0) {
-      const uint32_t tx = t % a.tiles_x, ty = t / a.tiles_x;
-      uint2 rec;
-      rec.x = (16u * tx) | ((16u * ty) << 16);
-      rec.y = c;
-      *reinterpret_cast<uint2*>(slot_ptr(a.rec, pos)) = rec;
-      ++pos;
+  // ring slot of the frame's first record (records of one frame fit the ring,
+  // so one subtraction wraps every slot below)
+  const uint64_t slot0 = (pl.wr_rec0 + s_off) % a.rec.cap;
+  uint64_t next = (wid ? sw32[wid - 1] : 0);               // records before this step
+  for_steps([&](int i, const uint4 q) {
+    uint32_t c[8];
+    counts8(q, c);
+    const int t0 = r0 + i * step + lane * per_lane;
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m += c[k] != 0;
+    uint32_t incl = m;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-  }
+    uint64_t idx = next + incl - m;
+    next += __shfl_sync(0xffffffffu, incl, 31);
+    if (m) {
+      uint32_t ty = (uint32_t)t0 / (uint32_t)a.tiles_x, tx = (uint32_t)t0 - ty * (uint32_t)a.tiles_x;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (c[k]) {
+          uint64_t slot = slot0 + idx;
+          if (slot >= a.rec.cap) slot -= a.rec.cap;
+          uint2 rec;
+          rec.x = (16u * tx) | ((16u * ty) << 16);
+          rec.y = c[k];
+          *reinterpret_cast<uint2*>(a.rec.ring + slot * a.rec.tok) = rec;
+          ++idx;
+        }
+        if (++tx == (uint32_t)a.tiles_x) {
+          tx = 0;
+          ++ty;
+        }
+      }
+    }
+  });
   if (threadIdx.x == 0)
     *reinterpret_cast<uint32_t*>(slot_ptr(a.cnt, pl.wr_cnt0 + j)) = a.frame_tot[j];
 }

@@ -241,14 +241,12 @@ __global__ void __launch_bounds__(kTThreads)
                   const __grid_constant__ CUtensorMap tm_cur,
                   const __grid_constant__ CUtensorMap tm_prev) {
   extern __shared__ __align__(128) uint8_t smem[];
-  const MdPlanHdr pl = *a.plan;
-  const uint64_t n = pl.n_cand;
-  if (n == 0) return;
   const int pitch = geo.pitch;                         // bytes per staged row
   const int slot_bytes = kTRows * pitch;               // one frame's rows in a stage
   const int stage_bytes = kTSlots * slot_bytes;
   uint8_t* stages = smem + kTBarBytes;
   const uint32_t full0 = smem_addr(smem), empty0 = full0 + 8 * kTStages;
+  __shared__ MdPlanHdr s_pl;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTStages; ++s) {
       mbar_init(full0 + 8 * s, 1);
@@ -257,8 +255,13 @@ __global__ void __launch_bounds__(kTThreads)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  griddep_wait();
+  // one load of the plan per CTA (every CTA reads the same line)
+  if (threadIdx.x == 0) s_pl = *a.plan;
   __syncthreads();
-
+  const MdPlanHdr pl = s_pl;
+  const uint64_t n = pl.n_cand;
+  if (n == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cols = a.W / 16;
   const uint32_t bands = (uint32_t)((cols + kMdOwned - 1) / kMdOwned);
@@ -420,12 +423,20 @@ cudaError_t md_tma_prepare(const MdArgs& a, MdTma* t) {
   const int px = pb * kTBand + 32;                       // staged pixels per row
   t->geo.pitch = px;
   t->smem = (size_t)kTBarBytes + (size_t)kTStages * kTSlots * kTRows * px;
-  if (t->smem > 227 * 1024) return cudaSuccess;
   if (!encode_frames(&t->unit, a.cur, a.W, a.H, px, kTSlots) ||
       !encode_frames(&t->cur, a.cur, a.W, a.H, px, 1) || !encode_frames(&t->prev, a.prev, a.W, a.H, px, 1))
     return cudaSuccess;                                  // the register-staged kernel serves
   auto k = g_kern[a.thr >= 128 ? 1 : 0];
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  // allow the largest dynamic size this device gives a block next to the
+  // kernel's static shared memory
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+  if (e != cudaSuccess) return e;
+  if (t->smem + fa.sharedSizeBytes > (size_t)optin) return cudaSuccess;   // the register-staged kernel serves
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTThreads, t->smem);
@@ -435,9 +446,9 @@ cudaError_t md_tma_prepare(const MdArgs& a, MdTma* t) {
   return cudaSuccess;
 }
 
-void launch_md_main_tma(const MdArgs& a, const MdTma& t, int n_sm, cudaStream_t s) {
-  g_kern[a.thr >= 128 ? 1 : 0]<<<n_sm * t.blocks_per_sm, kTThreads, t.smem, s>>>(a, t.geo, t.unit,
-                                                                              t.cur, t.prev);
+cudaError_t launch_md_main_tma(const MdArgs& a, const MdTma& t, int n_sm, cudaStream_t s, bool pdl) {
+  return launch_k(pdl, g_kern[a.thr >= 128 ? 1 : 0], dim3(n_sm * t.blocks_per_sm), dim3(kTThreads), t.smem,
+                  s, a, t.geo, t.unit, t.cur, t.prev);
 }
 
 }  // namespace dfg
