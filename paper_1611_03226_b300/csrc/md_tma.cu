@@ -50,7 +50,11 @@ constexpr int kTBarBytes = 128;                    // barriers, ahead of the sta
 static_assert(kMdWalk % kTRows == 0 && 4 % kTRows == 0,
               "row groups tile the walk and the first 4 walk rows");
 static_assert(2 * kTStages * sizeof(uint64_t) <= kTBarBytes, "barrier area");
-static_assert(kTRows == 4, "4 rows of (480 p + 32) bytes keep every slot 128-byte aligned");
+static_assert(4 % kTRows == 0 && kMdWalk % kTRows == 0, "row groups tile the walk and its first 4 rows");
+
+// Bytes of one frame's rows in a stage: kTRows rows of `pitch` bytes, padded
+// to the 128-byte alignment a TMA destination needs.
+__host__ __device__ constexpr int tma_slot_bytes(int pitch) { return (kTRows * pitch + 127) & ~127; }
 
 __device__ __forceinline__ long long globaltimer_ns() {
   long long t;
@@ -152,9 +156,9 @@ struct PairState {
 // Outside the image every pixel counts as motion for the erosion and as no
 // motion for the dilation.
 template <bool HI, bool ROWS, bool COLS, int W0>
-__device__ __forceinline__ void pair_rows(const uint8_t* st, int step, int y_start, int dir, int H,
-                                          bool col_in, uint32_t add4, uint32_t mul, PairState& p) {
-  const int slot = kTRows * (step < 0 ? -step : step);
+__device__ __forceinline__ void pair_rows(const uint8_t* st, int step, int slot, int y_start, int dir,
+                                          int H, bool col_in, uint32_t add4, uint32_t mul,
+                                          PairState& p) {
 #pragma unroll
   for (int rr = 0; rr < kTRows; ++rr) {
     const uint8_t* row = st + rr * step;             // rows in walk order
@@ -191,14 +195,14 @@ __device__ __forceinline__ void pair_rows(const uint8_t* st, int step, int y_sta
 
 template <bool HI, int W0>
 __device__ __forceinline__ void pair_rows_any(bool rows, bool cols, const uint8_t* st, int step,
-                                              int y_start, int dir, int H, bool col_in,
+                                              int slot, int y_start, int dir, int H, bool col_in,
                                               uint32_t add4, uint32_t mul, PairState& p) {
   if (rows) {
-    if (cols) pair_rows<HI, true, true, W0>(st, step, y_start, dir, H, col_in, add4, mul, p);
-    else pair_rows<HI, true, false, W0>(st, step, y_start, dir, H, col_in, add4, mul, p);
+    if (cols) pair_rows<HI, true, true, W0>(st, step, slot, y_start, dir, H, col_in, add4, mul, p);
+    else pair_rows<HI, true, false, W0>(st, step, slot, y_start, dir, H, col_in, add4, mul, p);
   } else {
-    if (cols) pair_rows<HI, false, true, W0>(st, step, y_start, dir, H, col_in, add4, mul, p);
-    else pair_rows<HI, false, false, W0>(st, step, y_start, dir, H, col_in, add4, mul, p);
+    if (cols) pair_rows<HI, false, true, W0>(st, step, slot, y_start, dir, H, col_in, add4, mul, p);
+    else pair_rows<HI, false, false, W0>(st, step, slot, y_start, dir, H, col_in, add4, mul, p);
   }
 }
 
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(kTThreads)
                   const __grid_constant__ CUtensorMap tm_prev) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int pitch = geo.pitch;                         // bytes per staged row
-  const int slot_bytes = kTRows * pitch;               // one frame's rows in a stage
+  const int slot_bytes = tma_slot_bytes(pitch);        // one frame's rows in a stage
   const int stage_bytes = kTSlots * slot_bytes;
   uint8_t* stages = smem + kTBarBytes;
   const uint32_t full0 = smem_addr(smem), empty0 = full0 + 8 * kTStages;
@@ -284,9 +288,12 @@ __global__ void __launch_bounds__(kTThreads)
       // otherwise (a short last unit, a wrap, or j0 = 0, where frame -1 is the
       // previous channel's initial token) one copy per frame.
       const uint64_t z0 = (t.j0 == 0) ? 0 : (slot_cur0 + t.j0 - 1) % a.cur.cap;
-      const bool whole = t.j0 >= 1 && t.nf == kTFrames && z0 + (uint64_t)t.nf + 1 <= a.cur.cap;
+      const bool whole = t.j0 >= 1 && t.nf == kTFrames && z0 + (uint64_t)t.nf + 1 <= a.cur.cap &&
+                         slot_bytes == kTRows * pitch;   // one box fills the slots without gaps
       const int copies = whole ? 1 : t.nf + 1;
-      const uint32_t bytes = whole ? (uint32_t)stage_bytes : (uint32_t)(t.nf + 1) * slot_bytes;
+      // bytes the copies deliver: kTRows rows of `pitch` per frame (the slot
+      // padding is not written)
+      const uint32_t bytes = (uint32_t)(whole ? kTSlots : t.nf + 1) * (uint32_t)(kTRows * pitch);
       const CUtensorMap* map = &tm_unit;
       int z = (int)z0;
       if (!whole) {                                  // this lane's frame j0 - 1 + lane
@@ -364,10 +371,17 @@ __global__ void __launch_bounds__(kTThreads)
         uint32_t mul;                                  // 1 << (10 * field)
         asm("mov.b32 %0, %1;" : "=r"(mul) : "r"(1u << (10 * (up ? kMdTileRows - 1 - tr : tr))));
         const int step = up ? -pitch : pitch;
-        if (grp == 0)
-          pair_rows_any<HI, 0>(edge_rows, edge_cols, st, step, y_start, dir, a.H, col_in, add4, mul, p);
-        else
-          pair_rows_any<HI, 4>(edge_rows, edge_cols, st, step, y_start, dir, a.H, col_in, add4, mul, p);
+        const int w0 = grp * kTRows;                   // walk row of the group's first row
+        if (w0 >= 4)
+          pair_rows_any<HI, 4>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
+        else if (w0 == 0)
+          pair_rows_any<HI, 0>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
+        else if (w0 == 2 && kTRows <= 2)
+          pair_rows_any<HI, 2>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
+        else if (w0 == 1 && kTRows == 1)
+          pair_rows_any<HI, 1>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
+        else if (kTRows == 1)
+          pair_rows_any<HI, 3>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty0 + 8 * s);
@@ -422,7 +436,7 @@ cudaError_t md_tma_prepare(const MdArgs& a, MdTma* t) {
   const int pb = std::min(bands, kTPanel);               // bands per panel
   const int px = pb * kTBand + 32;                       // staged pixels per row
   t->geo.pitch = px;
-  t->smem = (size_t)kTBarBytes + (size_t)kTStages * kTSlots * kTRows * px;
+  t->smem = (size_t)kTBarBytes + (size_t)kTStages * kTSlots * tma_slot_bytes(px);
   if (!encode_frames(&t->unit, a.cur, a.W, a.H, px, kTSlots) ||
       !encode_frames(&t->cur, a.cur, a.W, a.H, px, 1) || !encode_frames(&t->prev, a.prev, a.W, a.H, px, 1))
     return cudaSuccess;                                  // the register-staged kernel serves
