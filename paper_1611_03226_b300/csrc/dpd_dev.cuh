@@ -168,6 +168,48 @@ __device__ __forceinline__ void fir_branch(float2 (&acc)[R], const float2* zs, i
   }
 }
 
+// Packed form for the body kernel: two-lane FMAs (one instruction updates
+// the real and imaginary parts).  With taps staged as {hx, hx, hy, hy}, the
+// output is split into A = sum hx * z and B = sum hy * z (both lanes of z), so
+// that every product has the same tap value in both lanes; the complex result
+// is (A.x - B.y, A.y + B.x), formed once after all branches.
+template <int R, int MC>
+__device__ __forceinline__ void fir_causal_x2(float2 (&A)[R], float2 (&B)[R], const float2* __restrict__ zs,
+                                              int p, int shift, const float4* __restrict__ h4,
+                                              int m_valid) {
+  float2 hxx[MC], hyy[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const float4 t = m < m_valid ? h4[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+    hxx[m] = make_float2(t.x, t.y);
+    hyy[m] = make_float2(t.z, t.w);
+  }
+  const float2* zb = zs + p * (R + 1) + shift + shift / R;
+#pragma unroll
+  for (int s = 0; s < R + MC - 1; ++s) {
+    const float2 z = zb[s + s / R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = r + MC - 1 - s;
+      if (m >= 0 && m < MC) {
+        A[r] = __ffma2_rn(hxx[m], z, A[r]);
+        B[r] = __ffma2_rn(hyy[m], z, B[r]);
+      }
+    }
+  }
+}
+
+template <int R, int MT>
+__device__ __forceinline__ void fir_branch_x2(float2 (&A)[R], float2 (&B)[R], const float2* zs, int p,
+                                              const float4* h4, int M) {
+  if constexpr (MT <= 16) {
+    fir_causal_x2<R, MT>(A, B, zs, p, 0, h4, M);
+  } else {
+    fir_causal_x2<R, 16>(A, B, zs, p, 16, h4, M);
+    fir_causal_x2<R, 16>(A, B, zs, p, 0, h4 + 16, M - 16);
+  }
+}
+
 #define DPD_MT_CASES(X) X(4) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(32)
 
 // ----------------------------------------------------------------- plan ----
@@ -360,10 +402,10 @@ __device__ inline void zpass_any(const float2* __restrict__ xs, float2* __restri
 
 // Shared memory of one body CTA (T = R * blockDim.x samples per tile, W = T + MTmax - 1):
 //   xs[2][W] float2 | zb[kBranchGroup][Wp] float2 (Wp = W + W / R + 2) |
-//   hs[kMaxBranches * MTmax] float2
+//   hs[kMaxBranches * MTmax] float4 {hx, hx, hy, hy}
 template <int R, int MT>
 __device__ inline void dpd_compute(const DpdArgs& a, const ItemRef& it, const float2* xs, float2* zb,
-                            int Wp, const float2* hs, int* s_k, int* s_q) {
+                            int Wp, const float4* hs, int* s_k, int* s_q) {
   const int P = blockDim.x, p = threadIdx.x;
   const uint32_t T = R * P;
   const DpdPlanHdr& pl = *a.plan;
@@ -388,9 +430,9 @@ __device__ inline void dpd_compute(const DpdArgs& a, const ItemRef& it, const fl
     }
   }
   __syncthreads();
-  float2 acc[R];
+  float2 A[R], B[R];                      // sums of hx * z and hy * z (see fir_causal_x2)
 #pragma unroll
-  for (int r = 0; r < R; ++r) acc[r] = make_float2(0.f, 0.f);
+  for (int r = 0; r < R; ++r) A[r] = B[r] = make_float2(0.f, 0.f);
   for (int g0 = 0; g0 < nk; g0 += kBranchGroup) {
     const int ng = min(kBranchGroup, nk - g0);
     // branch signals z = u^q x of this group for the whole window, one tight loop per branch
@@ -413,11 +455,11 @@ __device__ inline void dpd_compute(const DpdArgs& a, const ItemRef& it, const fl
     }
     __syncthreads();
 #pragma unroll 1
-    for (int g = 0; g < ng; ++g) fir_branch<R, MT>(acc, zb + g * Wp, p, hs + s_k[g0 + g] * MT, MT);
+    for (int g = 0; g < ng; ++g) fir_branch_x2<R, MT>(A, B, zb + g * Wp, p, hs + s_k[g0 + g] * MT, MT);
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < R; ++r) zb[p * (R + 1) + r] = acc[r];
+  for (int r = 0; r < R; ++r) zb[p * (R + 1) + r] = make_float2(A[r].x - B[r].y, A[r].y + B[r].x);
   __syncthreads();
   for (int o = p; o < it.len; o += P) yb[o] = zb[o + o / R];
 }
@@ -432,9 +474,11 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, int G, Gri
   const uint32_t T = R * blockDim.x;
   const int Wm = (int)T + MTMAX - 1;
   const int Wpm = Wm + Wm / R + 2;
-  // work-list offsets of the group's actors live after the tile buffers
-  uint64_t* s_off = reinterpret_cast<uint64_t*>(reinterpret_cast<float2*>(smem_raw) + 2 * Wm +
-                                                kBranchGroup * Wpm + kMaxBranches * MTMAX);
+  // taps (float4, 16-byte aligned) follow the tile buffers; then the work-list
+  // offsets of the group's actors
+  const int hs_off = (2 * Wm + kBranchGroup * Wpm + 1) & ~1;          // in float2 units
+  uint64_t* s_off = reinterpret_cast<uint64_t*>(reinterpret_cast<float2*>(smem_raw) + hs_off +
+                                                2 * kMaxBranches * MTMAX);
   uint64_t carry = 0;
   for (int base = 0; base < G; base += blockDim.x) {
     const int g = base + threadIdx.x;
@@ -455,7 +499,7 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, int G, Gri
   const int Wp = W + W / R + 2;
   float2* xsb = reinterpret_cast<float2*>(smem_raw);          // [2][W]
   float2* zb = xsb + 2 * W;
-  float2* hs = zb + kBranchGroup * Wp;
+  float4* hs = reinterpret_cast<float4*>(xsb + hs_off);              // taps {hx, hx, hy, hy}
   int taps_of = -1;                                            // actor whose taps are in hs
   uint64_t item = grid.b;
   ItemRef cur = locate(args, s_off, G, item, total, T);
@@ -469,7 +513,10 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, int G, Gri
     cp_async_commit();
     if (cur.g != taps_of) {
       const DpdArgs& a = args[cur.g];
-      for (int e = threadIdx.x; e < a.K * a.MT; e += blockDim.x) hs[e] = a.h[e];
+      for (int e = threadIdx.x; e < a.K * a.MT; e += blockDim.x) {
+        const float2 h = a.h[e];
+        hs[e] = make_float4(h.x, h.x, h.y, h.y);
+      }
       taps_of = cur.g;
     }
     cp_async_wait1();

@@ -31,7 +31,7 @@ static size_t body_smem(uint32_t T, int R, int mtmax, int G) {
   const size_t W = T + mtmax - 1;
   const size_t Wp = W + W / R + 2;
   return 2 * W * sizeof(float2) + kBranchGroup * Wp * sizeof(float2) +
-         (size_t)kMaxBranches * mtmax * sizeof(float2) + (size_t)(G + 1) * sizeof(uint64_t);
+         (size_t)kMaxBranches * mtmax * sizeof(float4) + sizeof(float2) + (size_t)(G + 1) * sizeof(uint64_t);
 }
 
 constexpr int kBodySmemMax = 200 * 1024;

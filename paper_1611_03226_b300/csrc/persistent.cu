@@ -131,7 +131,7 @@ size_t persistent_smem(int mtmax, int max_group) {
   const size_t W = T + mtmax - 1;
   const size_t Wp = W + W / 8 + 2;
   return 2 * W * sizeof(float2) + kBranchGroup * Wp * sizeof(float2) +
-         (size_t)kMaxBranches * mtmax * sizeof(float2) + (size_t)(max_group + 1) * sizeof(uint64_t);
+         (size_t)kMaxBranches * mtmax * sizeof(float4) + sizeof(float2) + (size_t)(max_group + 1) * sizeof(uint64_t);
 }
 
 cudaError_t launch_persistent(const PersistOp* ops, int n_ops, EngineDev* eng, int64_t n_steps,
