@@ -17,6 +17,7 @@ import numpy as np
 
 from . import dpd as D
 from . import motion as MD
+from . import motion_paper as MP
 from .network import Actor, NetworkError
 
 
@@ -194,3 +195,41 @@ class Md(Actor):
             recs.extend(r[i:i + 1] for i in range(len(r)))
             cnts.append(np.array([len(r)], np.uint32))
         return {0: recs, 1: cnts}
+
+
+# ---- the paper's own motion pipeline (Sec. 4.1): Gauss -> Thres -> Med ----
+class Gauss5(Actor):
+    """Static: in 0 = frames; every output gets the filtered frames (the paper's
+    Gauss feeds Thres over two channels, one with the delay token)."""
+
+    def fire(self, ctrl, inputs):
+        g = [MP.gauss5(f) for f in inputs[0]]
+        return {p: [x.copy() for x in g] for p in self._outs}
+
+    def validate(self, in_ch, out_ch):
+        if len(in_ch) != 1 or not out_ch:
+            raise NetworkError("gauss: one input, >= 1 outputs")
+        self._outs = tuple(out_ch)
+
+
+class Thres(Actor):
+    """Static: in 0 = current filtered frame, in 1 = previous filtered frame; out 0 = motion map."""
+
+    def __init__(self, t=MP.THRESHOLD):
+        self.t = t
+
+    def fire(self, ctrl, inputs):
+        return {0: [MP.thres(c, p, self.t) for c, p in zip(inputs[0], inputs[1])]}
+
+
+class Med5(Actor):
+    """Static: in 0 = motion map; every output gets the median-filtered map."""
+
+    def fire(self, ctrl, inputs):
+        m = [MP.med5(f) for f in inputs[0]]
+        return {p: [x.copy() for x in m] for p in self._outs}
+
+    def validate(self, in_ch, out_ch):
+        if len(in_ch) != 1 or not out_ch:
+            raise NetworkError("med: one input, >= 1 outputs")
+        self._outs = tuple(out_ch)

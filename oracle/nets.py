@@ -123,3 +123,25 @@ def records_of(tokens):
     if not tokens:
         return np.empty(0, RECORD_DTYPE)
     return np.concatenate([np.asarray(t, RECORD_DTYPE).reshape(-1) for t in tokens])
+
+
+def motion_paper(height, width, capacity, rate=1, t=20, initial=None, record_history=False):
+    """The paper's motion pipeline (Sec. 4.1): Src -> Gauss -> {Thres in 0, Thres in 1 with one
+    initial frame} -> Med -> Sink, every channel carrying `rate` frames per firing."""
+    net = Network(record_history)
+    ids = {}
+    ids["src"] = net.add_actor(Source())
+    ids["gauss"] = net.add_actor(A.Gauss5())
+    ids["thres"] = net.add_actor(A.Thres(t))
+    ids["med"] = net.add_actor(A.Med5())
+    ids["sink"] = net.add_actor(Sink())
+    fb = height * width
+    init = np.zeros((height, width), np.uint8) if initial is None else np.asarray(initial, np.uint8)
+    ids["ch_in"] = net.connect(ids["src"], 0, ids["gauss"], 0, rate, capacity, token_bytes=fb)
+    ids["ch_cur"] = net.connect(ids["gauss"], 0, ids["thres"], 0, rate, capacity, token_bytes=fb)
+    ids["ch_prev"] = net.connect(ids["gauss"], 1, ids["thres"], 1, rate, capacity, [init.copy()],
+                                 token_bytes=fb)
+    ids["ch_map"] = net.connect(ids["thres"], 0, ids["med"], 0, rate, capacity, token_bytes=fb)
+    ids["ch_out"] = net.connect(ids["med"], 0, ids["sink"], 0, rate, capacity, token_bytes=fb)
+    net.finalize()
+    return net, ids
