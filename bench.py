@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "DPD Msamples/s & motion-detect frames/s on 1 B300; % of HBM roofline"
-SECONDARY = ("dpd_large", "dpd_tiny", "dpd_batch", "dpd_fit")
+SECONDARY = ("dpd_large", "dpd_tiny", "dpd_batch", "dpd_fit", "md_paper")
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (Blackwell)
 
 
@@ -437,6 +437,90 @@ def bench_dpd_tiny(args, P, torch, pk):
             "note": "device time of the 10 engine steps that stream 64 blocks through capacity-8 FIFOs"}
 
 
+def bench_md_paper(args, P, torch, pk):
+    """The paper's own motion pipeline (Sec. 4.1: Gauss -> Thres -> Med) on 320x240 frames at
+    rate 4, all frames pushed before the step; one step fires every actor over all of them."""
+    from paper_1611_03226_b300 import _lib as L
+    T = 4096 if not args.quick else 512
+    H, W, rate, thr = 240, 320, 4, 20
+    w = synth.motion(n_frames=T, height=H, width=W)
+    frames = np.stack(gen_parallel(w.frame, T))
+    host = torch.from_numpy(frames).pin_memory()
+    dev = host.to("cuda")
+    out_dev = torch.empty_like(dev)
+    net = P.Net(stream=torch.cuda.current_stream().cuda_stream)
+    fb = H * W
+    src, g, t, m, snk = (net.add_source(), net.add_gauss5(W, H), net.add_thres(W, H, thr),
+                         net.add_med5(W, H), net.add_sink())
+    cap = T + 1
+    net.connect(src, 0, g, 0, fb, rate, cap)
+    net.connect(g, 0, t, 0, fb, rate, cap)
+    net.connect(g, 1, t, 1, fb, rate, cap, 1)
+    net.connect(t, 0, m, 0, fb, rate, cap)
+    net.connect(m, 0, snk, 0, fb, rate, cap)
+    net.finalize()
+    l2 = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(timed, evs, flags):
+        net.push(src, dev)
+        flush_l2(l2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        net.run_async(1, flags)
+        e1.record(stream)
+        fired = net.sync()
+        _, n = net.pop(snk, out=out_dev)
+        if timed:
+            evs.append((e0, e1))
+        return n
+
+    modes = {"graph": L.DF_RUN_GRAPH, "eager": 0}
+    ms_mode = {}
+    for name, flags in modes.items():
+        for _ in range(args.warmup):
+            step(False, None, flags)
+        evs = []
+        for _ in range(args.steps):
+            assert step(True, evs, flags) == (T // rate) * rate
+        torch.cuda.synchronize()
+        ms_mode[name] = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    ms = min(ms_mode.values())
+    frames_done = (T // rate) * rate
+    bytes_per_frame = 8 * fb          # Gauss r + 2w, Thres 2r + w, Med r + w
+    achieved = bytes_per_frame * frames_done / (ms / 1e3) / 1e9
+    # end to end: pinned host frames in, motion maps out to pinned host memory
+    out_h = torch.empty_like(host).pin_memory()
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.push(src, host)
+        net.run(1)
+        net.pop(snk, out=out_h.numpy())
+        if i >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    net.close()
+    # oracle on a bounded sample (64 frames)
+    from oracle import motion_paper as MP
+    ns = 64 if not args.quick else 16
+    t0 = time.perf_counter()
+    MP.pipeline(frames[:ns], thr)
+    cpu_s = time.perf_counter() - t0
+    return {"workload": f"md_paper_{T}x{W}x{H}_rate{rate}", "value": frames_done / (ms / 1e3),
+            "unit": "frames/s", "ms_per_step": ms, "dtype": "u8", "launch_modes_ms": ms_mode,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                         "algorithmic_bytes_per_frame": bytes_per_frame,
+                         "note": "whole step (6 kernels + step begin) against its channel traffic"},
+            "e2e": {"value": frames_done / statistics.mean(e2e), "unit": "frames/s",
+                    "h2d_bytes_per_step": T * fb, "d2h_bytes_per_step": frames_done * fb},
+            "cpu_baseline": {"value": ns / cpu_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {ns} frames, numpy single thread"},
+            "paper_table3_context": {"i7_gpu_fps": 6063, "carrizo_gpu_fps": 4614,
+                                     "note": "Sec. 4.1, Table 3, other hardware (context only)"}}
+
+
 def bench_dpd_batch(args, P, torch, pk):
     """256 independent channels (uneven lengths, taps and branch sets) with 16
     resident blocks each; one engine step fires all of them."""
@@ -659,6 +743,8 @@ def gpu_arm(args):
                 extra["dpd_batch"] = bench_dpd_batch(args, P, torch, pk)
             if "dpd_fit" in want:
                 extra["dpd_fit"] = bench_dpd_fit(args, P, torch, pk)
+            if "md_paper" in want:
+                extra["md_paper"] = bench_md_paper(args, P, torch, pk)
     clocks = sampler.stop() if rank == 0 else None
     if rank != 0:
         return
@@ -730,7 +816,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="smaller workloads (smoke runs)")
     ap.add_argument("--only", default=None,
                     help="comma-separated secondary workloads to run besides the motion headline "
-                         "(dpd_large, dpd_tiny, dpd_batch, dpd_fit; 'motion' = none)")
+                         "(dpd_large, dpd_tiny, dpd_batch, dpd_fit, md_paper; 'motion' = none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -70,9 +70,20 @@ enum {
     DF_DPD_POLY = 5,  /* dynamic (Sec. 4.2 "P"): in 0 ctrl, in 1 data -> out k = branch k signal */
     DF_DPD_FIR = 6,   /* static FIR of one branch: in 0 -> out 0, rate 1 */
     DF_DPD_ADD = 7,   /* dynamic (Sec. 4.2 "A"): in 0 ctrl, in k+1 branch k -> out 0 */
-    DF_MD = 8         /* fused motion detector: in 0 current frame, in 1 previous frame;
+    DF_MD = 8,        /* fused motion detector: in 0 current frame, in 1 previous frame;
                          out 0 tile records (variable rate, r_max = tiles per frame),
                          out 1 per-frame record count (u32); params df_md_params */
+    /* The paper's own motion pipeline (Sec. 4.1): static image actors on
+     * u8 frames (token_bytes = width*height), params df_img_params, every
+     * port of an actor at the same rate r (r frames per firing). */
+    DF_GAUSS5 = 9,    /* "Gauss": in 0 -> every out port: 5x5 binomial filter (weights
+                         (1,4,6,4,1) x (1,4,6,4,1) / 256, rounded half up, columns clamped
+                         at the edges) of rows 2..height-3; rows 0, 1, height-2, height-1
+                         copied unfiltered */
+    DF_THRES = 10,    /* "Thres": in 0 current frame, in 1 previous frame -> out 0:
+                         255 where |cur - prev| > threshold, else 0 */
+    DF_MED5 = 11      /* "Med": in 0 -> every out port: median of each pixel and its 4
+                         nearest neighbours; the outermost rows and columns copied */
 };
 
 #define DF_MAX_BRANCHES 16
@@ -108,6 +119,14 @@ typedef struct {
     int32_t threshold;                  /* 25 in the benchmark */
     int32_t tile;                       /* must be 16 */
 } df_md_params;
+
+/* Image-actor parameters (DF_GAUSS5, DF_THRES, DF_MED5).  width must be a
+ * multiple of 16 and at most 2048; threshold (DF_THRES) in 0..255. */
+typedef struct {
+    int32_t width;
+    int32_t height;
+    int32_t threshold;                  /* DF_THRES only; 20 in the paper-pipeline workload */
+} df_img_params;
 
 typedef struct df_net df_net;
 

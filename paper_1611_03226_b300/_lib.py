@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdfgpu.so
 DF_OK, DF_EINVAL, DF_ENOMEM, DF_EFULL, DF_EEMPTY, DF_ESTATE = 0, -1, -2, -3, -4, -5
 DF_EDEADLOCK, DF_ETIMEOUT, DF_ECUDA, DF_ENOTSUP = -6, -7, -8, -9
 DF_SOURCE, DF_SINK, DF_COPY, DF_DPD, DF_DPD_POLY, DF_DPD_FIR, DF_DPD_ADD, DF_MD = range(1, 9)
+DF_GAUSS5, DF_THRES, DF_MED5 = 9, 10, 11
 DF_RUN_ASYNC, DF_RUN_GRAPH, DF_RUN_PERSISTENT, DF_RUN_NO_BATCH = 1, 2, 4, 8
 DF_MAX_BRANCHES, DF_MAX_TAPS = 16, 32
 DF_PROF_STEP, DF_PROF_DPD_BODY, DF_PROF_MD_MAIN, DF_PROF_COPY_BODY = 0, 1, 2, 3
@@ -27,6 +28,10 @@ class DpdParams(C.Structure):
 class MdParams(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("threshold", C.c_int32),
                 ("tile", C.c_int32)]
+
+
+class ImgParams(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("threshold", C.c_int32)]
 
 
 class DfError(RuntimeError):

@@ -68,6 +68,32 @@ struct CopyArgs {
   CopyPlan* plan;
 };
 
+// ---------------------------------------------------------- image actors ----
+// The paper's motion pipeline (Sec. 4.1) as three static actors on u8 frames.
+struct ImgPlan { uint64_t n; uint64_t rd0[2]; uint64_t wr0[kMaxPorts]; };
+
+struct ImgArgs {
+  int kind;                 // DF_GAUSS5, DF_THRES, DF_MED5
+  ChanDesc in[2];
+  int n_in;
+  ChanDesc out[kMaxPorts];
+  int n_out;
+  int W, H, thr;
+  uint64_t* ctr;
+  EngineDev* eng;
+  ImgPlan* plan;
+};
+
+constexpr int kImgBand = 16;        // output rows per work item
+constexpr int kImgThreads = 256;
+constexpr int kImgMaxWidth = 2048;
+// shared memory of one image work item: staged input rows (band + 2-row halo
+// each side) and, for the Gaussian, the vertical sums as u16 with 2 clamped
+// columns each side
+__host__ __device__ constexpr size_t img_smem_bytes(int W) {
+  return (size_t)(kImgBand + 4) * W + (size_t)kImgBand * (W + 4) * 2 + 16;
+}
+
 // --------------------------------------------------- fused predistorter ----
 constexpr int kMaxBranches = DF_MAX_BRANCHES;
 constexpr int kMaxTaps = DF_MAX_TAPS;
@@ -157,7 +183,7 @@ struct MdArgs {
 
 // ------------------------------------------------ persistent step kernel ----
 constexpr int kPersistThreads = 256;
-enum : int { kPersistCopy = 1, kPersistDpd = 2, kPersistDyn = 3, kPersistMd = 4 };
+enum : int { kPersistCopy = 1, kPersistDpd = 2, kPersistDyn = 3, kPersistMd = 4, kPersistImg = 5 };
 
 struct PersistOp {            // one entry of the device-side step program
   int kind;
@@ -221,6 +247,8 @@ struct MdTma {               // tensor maps of the frame rings for the TMA main 
 cudaError_t launch_md_step(const MdArgs& a, const MdTma* tma, int n_sm, cudaStream_t s,
                            cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 cudaError_t md_prepare(int W);     // one-time kernel attributes (outside graph capture)
+cudaError_t launch_img(const ImgArgs& a, int n_sm, cudaStream_t s);
+cudaError_t img_prepare();         // one-time kernel attributes (outside graph capture)
 cudaError_t md_tma_prepare(const MdArgs& a, MdTma* t);   // tensor maps + attributes
 cudaError_t launch_md_main_tma(const MdArgs& a, const MdTma& t, int n_sm, cudaStream_t s, bool pdl);
 size_t md_smem_bytes(int W);

@@ -30,6 +30,7 @@ struct ActorH {
   df_dpd_params dpd{};
   std::vector<float> h;               // K*M complex taps (host copy)
   df_md_params md{};
+  df_img_params img{};
   uint32_t tile = 0, threads = 0;     // predistorter body configuration (0 = default)
 };
 
@@ -40,7 +41,7 @@ struct ChanH {
   ChanDesc desc{};
 };
 
-enum OpKind { kOpCopy = 1, kOpDpd = 2, kOpMd = 3, kOpDyn = 4 };
+enum OpKind { kOpCopy = 1, kOpDpd = 2, kOpMd = 3, kOpDyn = 4, kOpImg = 5 };
 
 struct Op {
   OpKind kind;
@@ -48,6 +49,7 @@ struct Op {
   MdArgs md{};
   MdTma md_tma{};
   DynArgs dyn{};
+  ImgArgs img{};
   DpdArgs* dpd_dev = nullptr;        // group args (device)
   int dpd_n = 0;                      // actors in the group
   int dpd_first_actor = -1;           // actor id of the first member
@@ -152,6 +154,20 @@ df_status validate_actor(const df_net* net, int a) {
     case DF_SINK:
       if (A.in.size() != 1 || !A.out.empty()) return DF_EINVAL;
       return DF_OK;
+    case DF_GAUSS5:
+    case DF_THRES:
+    case DF_MED5: {
+      const size_t n_in = A.kind == DF_THRES ? 2 : 1;
+      if (A.in.size() != n_in || A.out.empty() || (int)A.out.size() > kMaxPorts) return DF_EINVAL;
+      if (A.kind == DF_THRES && A.out.size() != 1) return DF_EINVAL;
+      const uint64_t fb = (uint64_t)A.img.width * A.img.height;
+      const uint32_t r = ch(A.in[0]).rate;
+      for (int32_t c : A.in)
+        if (ch(c).tok != fb || ch(c).rate != r) return DF_EINVAL;
+      for (int32_t c : A.out)
+        if (ch(c).tok != fb || ch(c).rate != r) return DF_EINVAL;
+      return DF_OK;
+    }
     case DF_COPY: {
       if (A.in.size() != 1 || A.out.empty() || (int)A.out.size() > kMaxPorts) return DF_EINVAL;
       const ChanH& i = ch(A.in[0]);
@@ -312,6 +328,9 @@ df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
       case kOpDyn:
         DF_CUDA(launch_dyn(op.dyn, net->n_sm, s));
         break;
+      case kOpImg:
+        DF_CUDA(launch_img(op.img, net->n_sm, s));
+        break;
       case kOpDpd: {
         const ActorH& A0 = net->actors[op.dpd_first_actor];
         uint32_t tile = A0.tile, threads = A0.threads;
@@ -355,6 +374,7 @@ df_status build_persistent(df_net* net) {
     if (op.kind == kOpCopy) bytes += align256(sizeof(CopyArgs));
     if (op.kind == kOpDyn) bytes += align256(sizeof(DynArgs));
     if (op.kind == kOpMd) bytes += align256(sizeof(MdArgs));
+    if (op.kind == kOpImg) bytes += align256(sizeof(ImgArgs));
   }
   bytes += align256(sizeof(PersistOp) * std::max<size_t>(1, net->program.size()));
   if (cudaMalloc(&net->persist_mem, bytes) != cudaSuccess) {
@@ -365,6 +385,7 @@ df_status build_persistent(df_net* net) {
   uint8_t* base = static_cast<uint8_t*>(net->persist_mem);
   size_t off = 0;
   int max_group = 1, mtmax = 1;
+  size_t img_smem = 0;
   for (const Op& op : net->program) {
     PersistOp p{};
     if (op.kind == kOpCopy) {
@@ -382,6 +403,12 @@ df_status build_persistent(df_net* net) {
       p.kind = kPersistMd;
       p.args = base + off;
       off += align256(sizeof(MdArgs));
+    } else if (op.kind == kOpImg) {
+      DF_CUDA(cudaMemcpyAsync(base + off, &op.img, sizeof(ImgArgs), cudaMemcpyHostToDevice, net->stream));
+      p.kind = kPersistImg;
+      p.args = base + off;
+      off += align256(sizeof(ImgArgs));
+      if (op.img.kind != DF_THRES) img_smem = std::max(img_smem, img_smem_bytes(op.img.W));
     } else {
       p.kind = kPersistDpd;
       p.n = op.dpd_n;
@@ -397,7 +424,7 @@ df_status build_persistent(df_net* net) {
                             cudaMemcpyHostToDevice, net->stream));
   net->persist_n_ops = (int)ops.size();
   net->persist_mtmax = mtmax <= 16 ? 16 : 32;
-  net->persist_smem = persistent_smem(net->persist_mtmax, max_group);
+  net->persist_smem = std::max(persistent_smem(net->persist_mtmax, max_group), img_smem);
   DF_CUDA(persistent_prepare(net->persist_smem));
   DF_CUDA(cudaStreamSynchronize(net->stream));
   return DF_OK;
@@ -492,6 +519,17 @@ df_status df_actor_add(df_net* net, int32_t kind, const void* params, size_t par
       A.dpd.h = nullptr;
       break;
     }
+    case DF_GAUSS5:
+    case DF_THRES:
+    case DF_MED5: {
+      if (!params || params_bytes != sizeof(df_img_params)) return DF_EINVAL;
+      std::memcpy(&A.img, params, sizeof(df_img_params));
+      const df_img_params& m = A.img;
+      if (m.width < 16 || m.width % 16 || m.width > kImgMaxWidth || m.height < 1 || m.height > 65536)
+        return DF_EINVAL;
+      if (kind == DF_THRES && (m.threshold < 0 || m.threshold > 255)) return DF_EINVAL;
+      break;
+    }
     case DF_MD: {
       if (!params || params_bytes != sizeof(df_md_params)) return DF_EINVAL;
       std::memcpy(&A.md, params, sizeof(df_md_params));
@@ -574,6 +612,8 @@ df_status df_net_finalize(df_net* net) {
   std::vector<Piece> cp;
   net->dpd_index.assign(net->actors.size(), -1);
   std::vector<int> md_index(net->actors.size(), -1), copy_index(net->actors.size(), -1);
+  std::vector<Piece> ip;
+  std::vector<int> img_index(net->actors.size(), -1);
   struct DynPieces { Piece plan, masks, rank; };
   std::vector<DynPieces> yp;
   std::vector<int> dyn_index(net->actors.size(), -1);
@@ -621,6 +661,9 @@ df_status df_net_finalize(df_net* net) {
     } else if (A.kind == DF_COPY) {
       copy_index[a] = (int)cp.size();
       cp.push_back(take(sizeof(CopyPlan)));
+    } else if (A.kind == DF_GAUSS5 || A.kind == DF_THRES || A.kind == DF_MED5) {
+      img_index[a] = (int)ip.size();
+      ip.push_back(take(sizeof(ImgPlan)));
     }
   }
   const Piece p_dpd_args = take(sizeof(DpdArgs) * std::max<size_t>(1, dp.size()));
@@ -777,6 +820,22 @@ df_status df_net_finalize(df_net* net) {
       c.eng = net->d_eng;
       c.plan = reinterpret_cast<CopyPlan*>(base + cp[copy_index[a]].off);
       net->program.push_back(op);
+    } else if (A.kind == DF_GAUSS5 || A.kind == DF_THRES || A.kind == DF_MED5) {
+      Op op{};
+      op.kind = kOpImg;
+      ImgArgs& m = op.img;
+      m.kind = A.kind;
+      m.n_in = (int)A.in.size();
+      for (int i = 0; i < m.n_in; ++i) m.in[i] = net->chans[A.in[i]].desc;
+      m.n_out = (int)A.out.size();
+      for (int p = 0; p < m.n_out; ++p) m.out[p] = net->chans[A.out[p]].desc;
+      m.W = A.img.width;
+      m.H = A.img.height;
+      m.thr = A.img.threshold;
+      m.ctr = net->d_ctr;
+      m.eng = net->d_eng;
+      m.plan = reinterpret_cast<ImgPlan*>(base + ip[img_index[a]].off);
+      net->program.push_back(op);
     } else if (A.kind == DF_MD) {
       Op op{};
       op.kind = kOpMd;
@@ -815,6 +874,11 @@ df_status df_net_finalize(df_net* net) {
   }
   flush_group();
   if (!dp.empty()) DF_CUDA(dpd_prepare());  // also covers branch FIR actors
+  for (const Op& op : net->program)
+    if (op.kind == kOpImg) {
+      DF_CUDA(img_prepare());
+      break;
+    }
   for (Op& op : net->program)
     if (op.kind == kOpMd) {
       DF_CUDA(md_prepare(op.md.W));
@@ -1071,6 +1135,8 @@ df_status df_autotune(df_net* net, uint64_t* n_firings) {
       DF_CUDA(launch_md_step(op.md, &op.md_tma, net->n_sm, s));
     } else if (op.kind == kOpDyn) {
       DF_CUDA(launch_dyn(op.dyn, net->n_sm, s));
+    } else if (op.kind == kOpImg) {
+      DF_CUDA(launch_img(op.img, net->n_sm, s));
     } else {
       // one plan, then the (idempotent) body once per candidate; keep the fastest
       DF_CUDA(launch_dpd_plan(op.dpd_dev, op.dpd_n, s));

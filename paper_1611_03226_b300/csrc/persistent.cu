@@ -13,6 +13,7 @@
 #include "dpd_dev.cuh"
 #include "dyn_dev.cuh"
 #include "md_dev.cuh"
+#include "img_dev.cuh"
 
 namespace dfg {
 
@@ -89,6 +90,11 @@ __global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp*
         if (!grid_barrier(eng, nb, limit_ns)) return;
         if (a.kind == DF_DPD_POLY) poly_body_dev(a, g);
         else add_body_dev(a, g);
+      } else if (op.kind == kPersistImg) {
+        const ImgArgs& a = *static_cast<const ImgArgs*>(op.args);
+        if (lead && threadIdx.x == 0) img_plan_dev(a);
+        if (!grid_barrier(eng, nb, limit_ns)) return;
+        img_body_dev(a, g, reinterpret_cast<uint8_t*>(smem));
       } else if (op.kind == kPersistMd) {
         const MdArgs& a = *static_cast<const MdArgs*>(op.args);
         if (lead) md_plan_dev(a);

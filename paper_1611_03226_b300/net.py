@@ -88,6 +88,16 @@ class Net:
         p = L.MdParams(width, height, threshold, tile)
         return self._add(L.DF_MD, p)
 
+    # the paper's motion pipeline (Sec. 4.1): Gauss -> Thres -> Med on u8 frames
+    def add_gauss5(self, width, height):
+        return self._add(L.DF_GAUSS5, L.ImgParams(width, height, 0))
+
+    def add_thres(self, width, height, threshold=20):
+        return self._add(L.DF_THRES, L.ImgParams(width, height, threshold))
+
+    def add_med5(self, width, height):
+        return self._add(L.DF_MED5, L.ImgParams(width, height, 0))
+
     def connect(self, src, src_port, dst, dst_port, token_bytes, rate, capacity, initial=0,
                 initial_data=None):
         ch = C.c_int32()

@@ -90,3 +90,21 @@ def dpd_batch(Net, chans, capacity, stream=None):
         ids.append(d)
     net.finalize()
     return net, ids
+
+
+def motion_paper(Net, height, width, capacity, rate=1, t=20, initial=None, stream=None):
+    """The paper's motion pipeline through the engine: Src -> Gauss -> {Thres in 0, Thres in 1
+    with one initial frame} -> Med -> Sink, `rate` frames per firing on every channel."""
+    net = Net(stream=stream) if stream is not None else Net()
+    fb = height * width
+    ids = {"src": net.add_source(), "gauss": net.add_gauss5(width, height),
+           "thres": net.add_thres(width, height, t), "med": net.add_med5(width, height),
+           "sink": net.add_sink()}
+    init = None if initial is None else np.ascontiguousarray(initial, np.uint8)
+    ids["ch_in"] = net.connect(ids["src"], 0, ids["gauss"], 0, fb, rate, capacity)
+    ids["ch_cur"] = net.connect(ids["gauss"], 0, ids["thres"], 0, fb, rate, capacity)
+    ids["ch_prev"] = net.connect(ids["gauss"], 1, ids["thres"], 1, fb, rate, capacity, 1, init)
+    ids["ch_map"] = net.connect(ids["thres"], 0, ids["med"], 0, fb, rate, capacity)
+    ids["ch_out"] = net.connect(ids["med"], 0, ids["sink"], 0, fb, rate, capacity)
+    net.finalize()
+    return net, ids

@@ -1,0 +1,90 @@
+"""Bit-exact parity of the paper's motion pipeline (Gauss -> Thres -> Med,
+Sec. 4.1) through the engine with the integer oracle, step by step, with the
+channel counters compared after every step."""
+import numpy as np
+import pytest
+
+import engine_nets as EN
+import synth
+from oracle import motion_paper as MP
+from oracle import nets as ON
+
+pytestmark = pytest.mark.gpu
+
+CHANNELS = ("ch_in", "ch_cur", "ch_prev", "ch_map", "ch_out")
+
+
+@pytest.fixture(scope="module")
+def Net():
+    from paper_1611_03226_b300 import Net
+    return Net
+
+
+def stream_both(Net, frames, cap, rate, chunk, t=20, initial=None, flags=0):
+    T, H, W = frames.shape
+    onet, oi = ON.motion_paper(H, W, cap, rate, t, initial)
+    enet, ei = EN.motion_paper(Net, H, W, cap, rate, t, initial)
+    got, want = [], []
+    i, idle = 0, 0
+    while True:
+        k = min(chunk, T - i, onet.channels[oi["ch_in"]].free)
+        if k > 0:
+            onet.push(oi["src"], list(frames[i:i + k]))
+            enet.push(ei["src"], np.ascontiguousarray(frames[i:i + k]))
+            i += k
+        fo, fe = onet.run(1), enet.run(1, flags)
+        assert fo == fe
+        for key in CHANNELS:
+            assert onet.counters(oi[key]) == enet.counters(ei[key]), key
+        want += onet.pop(oi["sink"])
+        got.append(enet.pop(ei["sink"], dtype=np.uint8))
+        if i >= T and fo == 0:
+            idle += 1
+            if idle > 1:
+                break
+    enet.close()
+    got = np.concatenate(got).reshape(-1, H, W)
+    return got, np.array(want, np.uint8).reshape(-1, H, W)
+
+
+@pytest.mark.parametrize("H,W,T,cap,rate,chunk", [
+    (240, 320, 21, 9, 4, 8),     # the paper's frame size at rate 4; 20 of 21 frames fire
+    (37, 48, 11, 5, 1, 2),       # ragged band (37 = 2*16 + 5), rate 1
+    (18, 16, 9, 7, 3, 6),        # one 16-pixel column group, rate 3
+    (5, 32, 6, 4, 1, 3),         # one filtered row
+    (4, 16, 5, 4, 1, 2),         # no filtered rows
+    (2, 16, 4, 3, 1, 1),         # median copies everything
+])
+def test_parity(Net, H, W, T, cap, rate, chunk):
+    f = synth.motion(n_frames=T, height=H, width=W).frames() if H >= 16 else synth.uniform_frames(T, H, W)
+    got, want = stream_both(Net, f, cap, rate, chunk)
+    assert len(want) == (T // rate) * rate
+    np.testing.assert_array_equal(got, want)
+    np.testing.assert_array_equal(want, MP.pipeline(f[:len(want)]))
+
+
+@pytest.mark.parametrize("t", [0, 1, 128, 254, 255])
+def test_thresholds_and_initial_frame(Net, t):
+    f = synth.uniform_frames(8, 40, 64)
+    init = synth.uniform_frames(1, 40, 64, seed=7)[0]
+    got, want = stream_both(Net, f, 10, 2, 4, t=t, initial=init)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_persistent_mode(Net):
+    from paper_1611_03226_b300 import _lib as L
+    f = synth.motion(n_frames=12, height=48, width=64).frames()
+    got, want = stream_both(Net, f, 9, 4, 8, flags=L.DF_RUN_PERSISTENT)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_whole_video_in_one_run(Net):
+    """All frames pushed at once and run to quiescence (the bench configuration)."""
+    T, H, W, rate = 64, 240, 320, 4
+    f = synth.motion(n_frames=T, height=H, width=W).frames()
+    net, ids = EN.motion_paper(Net, H, W, T + 1, rate)
+    net.push(ids["src"], f)
+    assert net.run(-1) == 3 * (T // rate)
+    got = net.pop(ids["sink"], dtype=np.uint8).reshape(-1, H, W)
+    net.close()
+    np.testing.assert_array_equal(got, MP.pipeline(f))
