@@ -70,7 +70,11 @@ struct CopyArgs {
 
 // ---------------------------------------------------------- image actors ----
 // The paper's motion pipeline (Sec. 4.1) as three static actors on u8 frames.
-struct ImgPlan { uint64_t n; uint64_t rd0[2]; uint64_t wr0[kMaxPorts]; };
+struct ImgPlan {
+  uint64_t n;
+  uint64_t rd0[2], wr0[kMaxPorts];          // token index of this step's first frame
+  uint64_t slot_in[2], slot_out[kMaxPorts];  // its ring slot (index mod capacity)
+};
 
 struct ImgArgs {
   int kind;                 // DF_GAUSS5, DF_THRES, DF_MED5
@@ -87,11 +91,11 @@ struct ImgArgs {
 constexpr int kImgBand = 16;        // output rows per work item
 constexpr int kImgThreads = 256;
 constexpr int kImgMaxWidth = 2048;
-// shared memory of one image work item: staged input rows (band + 2-row halo
-// each side) and, for the Gaussian, the vertical sums as u16 with 2 clamped
-// columns each side
+// shared memory of an image body CTA: two staging buffers of input rows
+// (band + 2-row halo each side) and, for the Gaussian, the vertical sums as
+// u16 with 2 clamped columns each side
 __host__ __device__ constexpr size_t img_smem_bytes(int W) {
-  return (size_t)(kImgBand + 4) * W + (size_t)kImgBand * (W + 4) * 2 + 16;
+  return 2 * (size_t)(kImgBand + 4) * W + (size_t)kImgBand * (W + 4) * 2 + 16;
 }
 
 // --------------------------------------------------- fused predistorter ----

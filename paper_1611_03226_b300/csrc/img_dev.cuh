@@ -10,7 +10,8 @@
 // body  (any grid)    work items over the n*r frames of the step: Thres by
 //                     16-byte vectors, Gauss and Med by bands of 16 output
 //                     rows whose input rows (plus a 2-row halo) are staged in
-//                     shared memory with 16-byte loads.
+//                     shared memory by 16-byte asynchronous copies, the next
+//                     band's while the current one is computed.
 #pragma once
 #include "common.cuh"
 
@@ -35,27 +36,65 @@ __device__ inline void img_plan_dev(const ImgArgs& a) {
   a.plan->n = n;
   for (int i = 0; i < a.n_in; ++i) {
     a.plan->rd0[i] = rd[i];
+    a.plan->slot_in[i] = rd[i] % a.in[i].cap;
     *rd_ptr(ctr, a.in[i].id) = rd[i] + n * r;
   }
   for (int p = 0; p < a.n_out; ++p) {
     const uint64_t w = *wr_ptr(ctr, a.out[p].id);
     a.plan->wr0[p] = w;
+    a.plan->slot_out[p] = w % a.out[p].cap;
     *wr_ptr(ctr, a.out[p].id) = w + n * r;
   }
   atomicAdd(&a.eng->fired_step, (unsigned long long)n);
   atomicAdd(&a.eng->fired_total, (unsigned long long)n);
 }
 
-// Frame f of this step's window of a channel.
-__device__ __forceinline__ uint8_t* img_frame(const ChanDesc& c, uint64_t t0, uint64_t f) {
-  return c.ring + ((t0 + f) % c.cap) * c.tok;
+// Frame f of this step's window of a channel whose first frame is in ring
+// slot slot0 (f < capacity: a step never moves more frames than a ring holds).
+__device__ __forceinline__ uint8_t* img_frame(const ChanDesc& c, uint64_t slot0, uint64_t f) {
+  uint64_t s = slot0 + f;
+  if (s >= c.cap) s -= c.cap;
+  return c.ring + s * c.tok;
 }
 
-// Median of five bytewise (per byte lane): med3(e, max(min(a,b), min(c,d)), min(max(a,b), max(c,d))).
+// q = it / d, r = it % d, with 32-bit arithmetic whenever it fits.
+__device__ __forceinline__ void div_item(uint64_t it, uint32_t d, uint64_t& q, uint32_t& r) {
+  if (it <= 0xffffffffull) {
+    const uint32_t i = (uint32_t)it, qq = i / d;
+    q = qq;
+    r = i - qq * d;
+  } else {
+    q = it / d;
+    r = (uint32_t)(it - q * d);
+  }
+}
+
+// Median of five, per 16-bit lane, with the 3-input min/max instructions:
+// med3(e, max(min(a,b), min(c,d)), min(max(a,b), max(c,d))).
+__device__ __forceinline__ uint32_t med5_u16x2(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e) {
+  const uint32_t f = __vimax3_u16x2(__vimin3_u16x2(a, b, b), __vimin3_u16x2(c, d, d), 0u);
+  const uint32_t g = __vimin3_u16x2(__vimax3_u16x2(a, b, 0u), __vimax3_u16x2(c, d, 0u),
+                                    __vimax3_u16x2(c, d, 0u));
+  return __vimax3_u16x2(__vimin3_u16x2(e, f, f), __vimin3_u16x2(e, g, g), __vimin3_u16x2(f, g, g));
+}
+
+// True when every byte of w is 0x00 or 0xff (bits 1..7 of each byte equal
+// its bits 0..6).
+__device__ __forceinline__ bool bytes_binary(uint32_t w) { return ((w ^ (w << 1)) & 0xfefefefeu) == 0; }
+
+// Bitwise majority of five words (at least 3 of 5 bits set): for bytes that
+// are 0x00 or 0xff this is the median of five.
+__device__ __forceinline__ uint32_t maj5(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e) {
+  const uint32_t any3 = c | d | e, two3 = (c & d) | (c & e) | (d & e), all3 = c & d & e;
+  return (a & b & any3) | ((a ^ b) & two3) | (~(a | b) & all3);
+}
+
+// Median of five per byte: even and odd bytes in 16-bit lanes.
 __device__ __forceinline__ uint32_t med5_bytes(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e) {
-  const uint32_t f = __vmaxu4(__vminu4(a, b), __vminu4(c, d));
-  const uint32_t g = __vminu4(__vmaxu4(a, b), __vmaxu4(c, d));
-  return __vmaxu4(__vminu4(e, f), __vminu4(__vmaxu4(e, f), g));
+  const uint32_t m = 0x00ff00ffu;
+  const uint32_t lo = med5_u16x2(a & m, b & m, c & m, d & m, e & m);
+  const uint32_t hi = med5_u16x2((a >> 8) & m, (b >> 8) & m, (c >> 8) & m, (d >> 8) & m, (e >> 8) & m);
+  return lo | (hi << 8);
 }
 
 // Thres over whole frames: 255 where |cur - prev| > thr.
@@ -67,32 +106,116 @@ __device__ inline void thres_body(const ImgArgs& a, const ImgPlan& pl, Grid g) {
   const uint64_t items = frames * ipf;
   const uint32_t thr4 = 0x01010101u * (uint32_t)a.thr;
   for (uint64_t it = g.b; it < items; it += g.n) {
-    const uint64_t f = it / ipf;
-    const uint32_t v0 = (uint32_t)(it - f * ipf) * per_item;
-    const uint4* c = reinterpret_cast<const uint4*>(img_frame(a.in[0], pl.rd0[0], f));
-    const uint4* p = reinterpret_cast<const uint4*>(img_frame(a.in[1], pl.rd0[1], f));
-    uint4* o = reinterpret_cast<uint4*>(img_frame(a.out[0], pl.wr0[0], f));
-    for (uint32_t v = v0 + threadIdx.x; v < min(vpf, v0 + per_item); v += blockDim.x) {
-      const uint4 x = c[v], y = p[v];
-      uint4 m;
-      m.x = __vcmpgtu4(__vabsdiffu4(x.x, y.x), thr4);
-      m.y = __vcmpgtu4(__vabsdiffu4(x.y, y.y), thr4);
-      m.z = __vcmpgtu4(__vabsdiffu4(x.z, y.z), thr4);
-      m.w = __vcmpgtu4(__vabsdiffu4(x.w, y.w), thr4);
-      o[v] = m;
+    uint64_t f;
+    uint32_t ci;
+    div_item(it, ipf, f, ci);
+    const uint32_t v0 = ci * per_item;
+    const uint4* c = reinterpret_cast<const uint4*>(img_frame(a.in[0], pl.slot_in[0], f));
+    const uint4* p = reinterpret_cast<const uint4*>(img_frame(a.in[1], pl.slot_in[1], f));
+    uint4* o = reinterpret_cast<uint4*>(img_frame(a.out[0], pl.slot_out[0], f));
+    // 4 vectors per thread, all loads issued before the first use
+    uint4 x[4], y[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t v = v0 + threadIdx.x + k * blockDim.x;
+      if (v < vpf) {
+        x[k] = c[v];
+        y[k] = p[v];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t v = v0 + threadIdx.x + k * blockDim.x;
+      if (v < vpf) {
+        uint4 m;
+        m.x = __vcmpgtu4(__vabsdiffu4(x[k].x, y[k].x), thr4);
+        m.y = __vcmpgtu4(__vabsdiffu4(x[k].y, y[k].y), thr4);
+        m.z = __vcmpgtu4(__vabsdiffu4(x[k].z, y[k].z), thr4);
+        m.w = __vcmpgtu4(__vabsdiffu4(x[k].w, y[k].w), thr4);
+        o[v] = m;
+      }
     }
   }
 }
 
-// Stage input rows y0-2 .. y0+kImgBand+1 (those inside the frame) of one
-// frame into s (row y at s + (y - y0 + 2) * W).
+// Start copying input rows y0-2 .. y0+kImgBand+1 (those inside the frame) of
+// one frame into s (row y at s + (y - y0 + 2) * W) with 16-byte asynchronous
+// copies; the caller commits and waits.
 __device__ __forceinline__ void stage_rows(const uint8_t* frame, uint8_t* s, int W, int H, int y0) {
   const int ya = max(y0 - 2, 0), yb = min(y0 + kImgBand + 2, H);
   const int vpr = W / 16;
   const int nv = (yb - ya) * vpr;
-  const uint4* src = reinterpret_cast<const uint4*>(frame + (size_t)ya * W);
-  uint4* dst = reinterpret_cast<uint4*>(s + (size_t)(ya - y0 + 2) * W);
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) dst[v] = src[v];
+  const uint8_t* src = frame + (size_t)ya * W;
+  uint8_t* dst = s + (size_t)(ya - y0 + 2) * W;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + 16 * v));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + 16 * v) : "memory");
+  }
+}
+__device__ __forceinline__ void img_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void img_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Calls f(y, x) for every row y in [ya, yb) and 4-pixel group x = 0, 4, ..
+// of a W-pixel row, spread over the CTA's threads (flat index tid + k *
+// blockDim.x, advanced without a division per step).
+template <typename F>
+__device__ __forceinline__ void for_groups(int ya, int yb, int W, F&& f) {
+  const int q = W / 4;
+  const int n = (yb - ya) * q;
+  if (n <= 0) return;
+  int e = threadIdx.x;
+  int y = ya + e / q, c = e % q;
+  const int dy = (int)blockDim.x / q, dc = (int)blockDim.x % q;
+  for (; e < n; e += blockDim.x) {
+    f(y, 4 * c);
+    y += dy;
+    c += dc;
+    if (c >= q) {
+      c -= q;
+      ++y;
+    }
+  }
+}
+
+// Band items (frame, band of kImgBand rows) of this CTA with the input rows of
+// the next item staged while the current one is computed (two buffers).
+template <typename F>
+__device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem,
+                                               F&& compute) {
+  const int W = a.W, H = a.H;
+  const uint64_t frames = pl.n * a.in[0].rate;
+  const int bands = (H + kImgBand - 1) / kImgBand;
+  const uint64_t items = frames * bands;
+  const size_t sb = (size_t)(kImgBand + 4) * W;                    // one staging buffer
+  auto stage = [&](uint64_t it, int buf) {
+    uint64_t f;
+    uint32_t b;
+    div_item(it, (uint32_t)bands, f, b);
+    stage_rows(img_frame(a.in[0], pl.slot_in[0], f), smem + buf * sb, W, H, (int)b * kImgBand);
+  };
+  __shared__ uint8_t* out_frames[kMaxPorts];
+  int buf = 0;
+  if ((uint64_t)g.b < items) stage(g.b, 0);
+  img_commit();
+  for (uint64_t it = g.b; it < items; it += g.n) {
+    if (it + g.n < items) stage(it + g.n, buf ^ 1);
+    img_commit();
+    uint64_t f;
+    uint32_t b;
+    div_item(it, (uint32_t)bands, f, b);
+    const int y0 = (int)b * kImgBand;
+    // this item's output frames, one per port
+    if (threadIdx.x < a.n_out) {
+      const int p = threadIdx.x;
+      out_frames[p] = img_frame(a.out[p], pl.slot_out[p], f);
+    }
+    img_wait_prev();
+    __syncthreads();
+    compute(y0, min(y0 + kImgBand, H), smem + buf * sb, out_frames);
+    __syncthreads();
+    buf ^= 1;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Gauss over bands of kImgBand rows.  Vertical sums of the 5 rows (weights
@@ -101,23 +224,13 @@ __device__ __forceinline__ void stage_rows(const uint8_t* frame, uint8_t* s, int
 // neighbouring sums, adds 128 and shifts right by 8.
 __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
-  const uint64_t frames = pl.n * a.in[0].rate;
-  const int bands = (H + kImgBand - 1) / kImgBand;
-  const uint64_t items = frames * bands;
-  uint8_t* s = smem;                                                // (kImgBand + 4) rows
-  uint16_t* v = reinterpret_cast<uint16_t*>(smem + (size_t)(kImgBand + 4) * W);   // 16-byte aligned (W % 16 == 0)
+  // after the two staging buffers: vertical sums, u16, 2 clamped columns each side
+  uint16_t* v = reinterpret_cast<uint16_t*>(smem + 2 * (size_t)(kImgBand + 4) * W);
   const int vw = W + 4;                                             // u16 per vertical-sum row
-  const int q = W / 4;                                              // 4-pixel groups per row
-  for (uint64_t it = g.b; it < items; it += g.n) {
-    const uint64_t f = it / bands;
-    const int y0 = (int)(it - f * bands) * kImgBand;
-    const int y1 = min(y0 + kImgBand, H);
-    stage_rows(img_frame(a.in[0], pl.rd0[0], f), s, W, H, y0);
-    __syncthreads();
+  for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
     // vertical pass over the band's filtered rows (2 <= y < H-2)
     const int fa = max(y0, 2), fb = min(y1, H - 2);
-    for (int e = threadIdx.x; e < (fb > fa ? (fb - fa) * q : 0); e += blockDim.x) {
-      const int yr = fa + e / q, x = (e % q) * 4;
+    for_groups(fa, fb, W, [&](int yr, int x) {
       uint32_t lo = 0, hi = 0;                                      // pixels x, x+2 / x+1, x+3 in 16-bit lanes
       const uint8_t* col = s + (size_t)(yr - y0) * W + x;           // row yr-2
 #pragma unroll
@@ -129,55 +242,41 @@ __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, u
       }
       uint16_t* vr = v + (size_t)(yr - y0) * vw + 2;
       const uint32_t p01 = __byte_perm(lo, hi, 0x5410), p23 = __byte_perm(lo, hi, 0x7632);
-      vr[x] = (uint16_t)p01;
-      vr[x + 1] = (uint16_t)(p01 >> 16);
-      vr[x + 2] = (uint16_t)p23;
-      vr[x + 3] = (uint16_t)(p23 >> 16);
+      *reinterpret_cast<uint32_t*>(vr + x) = p01;                   // 4-byte aligned: vw, x even
+      *reinterpret_cast<uint32_t*>(vr + x + 2) = p23;
       if (x == 0) vr[-1] = vr[-2] = (uint16_t)p01;                  // clamped columns -1, -2
       if (x + 4 == W) vr[W] = vr[W + 1] = (uint16_t)(p23 >> 16);    // clamped columns W, W+1
-    }
+    });
     __syncthreads();
     // horizontal pass and the unfiltered rows; 4 pixels per thread
-    for (int e = threadIdx.x; e < (y1 - y0) * q; e += blockDim.x) {
-      const int y = y0 + e / q, x = (e % q) * 4;
+    for_groups(y0, y1, W, [&](int y, int x) {
       uint32_t out;
       if (y < 2 || y >= H - 2) {
         out = *reinterpret_cast<const uint32_t*>(s + (size_t)(y - y0 + 2) * W + x);
       } else {
-        const uint16_t* vr = v + (size_t)(y - y0) * vw + x;         // v[x-2] .. v[x+5]
-        uint32_t t[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) t[i] = vr[i];
-        out = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t h = t[j] + 4 * t[j + 1] + 6 * t[j + 2] + 4 * t[j + 3] + t[j + 4];
-          out |= ((h + 128) >> 8) << (8 * j);
-        }
+        // v[x-2] .. v[x+5] as four u16 pairs (8-byte aligned: vw = W + 4, x % 4 == 0)
+        const uint16_t* vr = v + (size_t)(y - y0) * vw + x;
+        const uint2 q0 = *reinterpret_cast<const uint2*>(vr), q1 = *reinterpret_cast<const uint2*>(vr + 4);
+        const uint32_t w01 = q0.x, w23 = q0.y, w45 = q1.x, w67 = q1.y;
+        // pairs (v_i, v_{i+2}) for the even pixels x, x+2 and the odd pixels x+1, x+3;
+        // each 16-bit lane of the weighted sum stays below 65536 (16 * 16 * 255)
+        const uint32_t s02 = __byte_perm(w01, w23, 0x5410), s13 = __byte_perm(w01, w23, 0x7632);
+        const uint32_t s24 = __byte_perm(w23, w45, 0x5410), s35 = __byte_perm(w23, w45, 0x7632);
+        const uint32_t s46 = __byte_perm(w45, w67, 0x5410), s57 = __byte_perm(w45, w67, 0x7632);
+        const uint32_t he = s02 + 4 * s13 + 6 * s24 + 4 * s35 + s46 + 0x00800080u;
+        const uint32_t ho = s13 + 4 * s24 + 6 * s35 + 4 * s46 + s57 + 0x00800080u;
+        out = ((he >> 8) & 0x00ff00ffu) | (((ho >> 8) & 0x00ff00ffu) << 8);
       }
-      for (int p = 0; p < a.n_out; ++p)
-        *reinterpret_cast<uint32_t*>(img_frame(a.out[p], pl.wr0[p], f) + (size_t)y * W + x) = out;
-    }
-    __syncthreads();
-  }
+      for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint32_t*>(of[p] + (size_t)y * W + x) = out;
+    });
+  });
 }
 
 // Med over bands of kImgBand rows; 4 pixels per thread with bytewise min/max.
 __device__ inline void med_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
-  const uint64_t frames = pl.n * a.in[0].rate;
-  const int bands = (H + kImgBand - 1) / kImgBand;
-  const uint64_t items = frames * bands;
-  uint8_t* s = smem;
-  const int q = W / 4;
-  for (uint64_t it = g.b; it < items; it += g.n) {
-    const uint64_t f = it / bands;
-    const int y0 = (int)(it - f * bands) * kImgBand;
-    const int y1 = min(y0 + kImgBand, H);
-    stage_rows(img_frame(a.in[0], pl.rd0[0], f), s, W, H, y0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < (y1 - y0) * q; e += blockDim.x) {
-      const int y = y0 + e / q, x = (e % q) * 4;
+  for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
+    for_groups(y0, y1, W, [&](int y, int x) {
       const uint8_t* row = s + (size_t)(y - y0 + 2) * W;
       const uint32_t c = *reinterpret_cast<const uint32_t*>(row + x);
       uint32_t out = c;
@@ -188,15 +287,17 @@ __device__ inline void med_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uin
         const uint32_t nw = x + 4 < W ? *reinterpret_cast<const uint32_t*>(row + x + 4) : 0u;
         const uint32_t lf = __funnelshift_l(pw, c, 8);              // pixels x-1 .. x+2
         const uint32_t rt = __funnelshift_r(c, nw, 8);              // pixels x+1 .. x+4
-        out = med5_bytes(up, dn, lf, rt, c);
+        // motion maps hold only 0 and 255: there the median is a bitwise majority
+        out = bytes_binary(up) && bytes_binary(dn) && bytes_binary(lf) && bytes_binary(rt) &&
+                      bytes_binary(c)
+                  ? maj5(up, dn, lf, rt, c)
+                  : med5_bytes(up, dn, lf, rt, c);
         if (x == 0) out = (out & 0xffffff00u) | (c & 0xffu);        // column 0 copied
         if (x + 4 == W) out = (out & 0x00ffffffu) | (c & 0xff000000u);   // column W-1 copied
       }
-      for (int p = 0; p < a.n_out; ++p)
-        *reinterpret_cast<uint32_t*>(img_frame(a.out[p], pl.wr0[p], f) + (size_t)y * W + x) = out;
-    }
-    __syncthreads();
-  }
+      for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint32_t*>(of[p] + (size_t)y * W + x) = out;
+    });
+  });
 }
 
 __device__ inline void img_body_dev(const ImgArgs& a, Grid g, uint8_t* smem) {
