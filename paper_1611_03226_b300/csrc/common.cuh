@@ -31,6 +31,7 @@ struct EngineDev {          // device-resident engine state
   int32_t status_where;     // which kernel / wait reported it
   unsigned int barrier_count;   // persistent-kernel grid barrier
   unsigned int barrier_gen;
+  unsigned long long total_snap;  // fired_total as the last CTA saw it when releasing a barrier
 };
 
 // where-codes for EngineDev::status_where

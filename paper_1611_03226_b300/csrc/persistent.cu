@@ -24,7 +24,11 @@ __device__ __forceinline__ long long timer_ns() {
 }
 
 // Returns false when the status word is set (own timeout or another CTA's).
-__device__ bool grid_barrier(EngineDev* e, unsigned int expected, long long limit_ns) {
+// With snap, the CTA that releases the barrier records fired_total in
+// total_snap first, so every CTA reads the same value after the barrier (a
+// CTA that reads fired_total itself may already see the next phase's commits).
+__device__ bool grid_barrier(EngineDev* e, unsigned int expected, long long limit_ns,
+                             bool snap = false) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -35,6 +39,7 @@ __device__ bool grid_barrier(EngineDev* e, unsigned int expected, long long limi
     int ok = 1;
     if (arrived == expected) {
       e->barrier_count = 0;
+      if (snap) e->total_snap = *reinterpret_cast<volatile unsigned long long*>(&e->fired_total);
       __threadfence();
       atomicAdd(&e->barrier_gen, 1u);
     } else {
@@ -64,11 +69,14 @@ __global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp*
   const unsigned int nb = gridDim.x;
   const bool lead = blockIdx.x == 0;
   const int64_t max_steps = n_steps < 0 ? (int64_t)1 << 20 : n_steps;
-  volatile unsigned long long* total = &eng->fired_total;
+  volatile unsigned long long* snap = &eng->total_snap;
+  if (n_ops == 0) return;
+  // fired_step counts the firings of the whole launch here (the host reads
+  // fired_total); the first barrier records the total before any commit
+  if (lead && threadIdx.x == 0) eng->fired_step = 0;
+  if (!grid_barrier(eng, nb, limit_ns, true)) return;
+  unsigned long long fired0 = *snap;
   for (int64_t step = 0; step < max_steps; ++step) {
-    if (lead && threadIdx.x == 0) eng->fired_step = 0;
-    if (!grid_barrier(eng, nb, limit_ns)) return;
-    const unsigned long long fired0 = *total;
     for (int o = 0; o < n_ops; ++o) {
       const PersistOp op = ops[o];
       if (op.kind == kPersistCopy) {
@@ -104,10 +112,13 @@ __global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp*
         if (!grid_barrier(eng, nb, limit_ns)) return;
         md_emit_dev(a, g);
       }
-      if (!grid_barrier(eng, nb, limit_ns)) return;
+      // the step's last barrier records the total that ends the step
+      if (!grid_barrier(eng, nb, limit_ns, o == n_ops - 1)) return;
     }
-    // every CTA reads the same totals: nothing changes them between these barriers
-    if (n_steps < 0 && *total == fired0) return;
+    // every CTA reads the same recorded total, so all take the same decision
+    const unsigned long long fired1 = *snap;
+    if (n_steps < 0 && fired1 == fired0) return;
+    fired0 = fired1;
   }
 }
 
