@@ -9,6 +9,7 @@ small-signal gain; the trained P is then used as the predistorter.  The loss
 is mean |P(y/G) - x|^2 over the whole signal, minimised with Adam starting
 from the identity (h[0,0] = 1).  P's forward and gradient run in the
 engine's kernels (DPDFunction); everything else is plain torch.
+ila_fit_iterative repeats the procedure with the predistorter in the loop.
 """
 from __future__ import annotations
 
@@ -44,6 +45,22 @@ def nmse_db(a: torch.Tensor, ref: torch.Tensor) -> float:
     return float(10 * torch.log10(num / den))
 
 
+def adam_fit(u: torch.Tensor, target: torch.Tensor, h0: torch.Tensor, orders, steps=200, lr=1e-3):
+    """Adam on the predistorter taps so that P(u) ~ target (loss mean |P(u) - target|^2);
+    P's forward and gradient run in the engine's kernels.  Returns (h, losses)."""
+    h = h0.detach().clone().requires_grad_(True)
+    opt = torch.optim.Adam([h], lr=lr)
+    losses = []
+    for _ in range(steps):
+        opt.zero_grad(set_to_none=True)
+        out = dpd(u, h, orders)
+        loss = (out - target).abs().pow(2).mean()
+        loss.backward()
+        opt.step()
+        losses.append(loss.detach())
+    return h.detach(), torch.stack(losses).cpu().numpy()
+
+
 def ila_fit(x: torch.Tensor, K=4, M=10, orders=(1, 3, 5, 7), steps=200, lr=1e-3,
             saleh=(2.1587, 1.1517, 4.0033, 9.1040), memory=(1.0, 0.1, -0.05)):
     """Returns (h, losses) for complex64 CUDA input x."""
@@ -51,14 +68,26 @@ def ila_fit(x: torch.Tensor, K=4, M=10, orders=(1, 3, 5, 7), steps=200, lr=1e-3,
     u = (saleh_pa(x, saleh, memory) / G).to(torch.complex64).contiguous()
     h = torch.zeros((K, M), dtype=torch.complex64, device=x.device)
     h[0, 0] = 1
-    h.requires_grad_(True)
-    opt = torch.optim.Adam([h], lr=lr)
-    losses = []
-    for _ in range(steps):
-        opt.zero_grad(set_to_none=True)
-        out = dpd(u, h, orders)
-        loss = (out - x).abs().pow(2).mean()
-        loss.backward()
-        opt.step()
-        losses.append(loss.detach())
-    return h.detach(), torch.stack(losses).cpu().numpy()
+    return adam_fit(u, x, h, orders, steps, lr)
+
+
+def ila_fit_iterative(x: torch.Tensor, iterations=3, K=4, M=10, orders=(1, 3, 5, 7), steps=200,
+                      lr=1e-3, saleh=(2.1587, 1.1517, 4.0033, 9.1040), memory=(1.0, 0.1, -0.05)):
+    """Iterative indirect learning: in iteration i the current predistorter P_i
+    drives the amplifier with z = P_i(x) (forward kernel); a postdistorter started
+    from P_i's taps is trained so that P(PA(z)/G) ~ z and becomes P_{i+1}; P_0 is
+    the identity.  Returns (h, loss curves per iteration, NMSE in dB of
+    PA(P_{i+1}(x))/G against x after each iteration)."""
+    G = small_signal_gain(saleh, memory)
+    h = torch.zeros((K, M), dtype=torch.complex64, device=x.device)
+    h[0, 0] = 1
+    curves, nmse = [], []
+    for _ in range(iterations):
+        with torch.no_grad():
+            z = dpd(x, h, orders).contiguous()
+            u = (saleh_pa(z, saleh, memory) / G).to(torch.complex64).contiguous()
+        h, losses = adam_fit(u, z, h, orders, steps, lr)
+        curves.append(losses)
+        with torch.no_grad():
+            nmse.append(nmse_db(saleh_pa(dpd(x, h, orders), saleh, memory) / G, x))
+    return h, curves, nmse

@@ -100,3 +100,38 @@ def test_error_paths(P):
         net.connect(a, 0, d, 0, 4, 2, 4)              # control rate must be 1
     assert e.value.status == L.DF_EINVAL
     net.close()
+
+
+@pytest.mark.parametrize("delay,cap,persistent", [(3, 4, False), (1, 2, False), (5, 8, True)])
+def test_feedback_cycle_with_delay_tokens(P, delay, cap, persistent):
+    """A cycle A -> B -> A whose only tokens are the `delay` initial tokens on the
+    edge B -> A (the feedback use of initial tokens, Sec. 2.2); A also copies every
+    token to a sink, which must receive the initial tokens over and over in order."""
+    from paper_1611_03226_b300 import _lib as L
+    flags = L.DF_RUN_PERSISTENT if persistent else 0
+    tok = 12
+    init = [np.arange(i * tok, (i + 1) * tok, dtype=np.uint8) for i in range(delay)]
+    onet, enet = Network(), P.Net()
+    oa, ob, os_ = onet.add_actor(A.Copy()), onet.add_actor(A.Copy()), onet.add_actor(Sink())
+    ea, eb, es = enet.add_copy(), enet.add_copy(), enet.add_sink()
+    chans = [
+        (onet.connect(ob, 0, oa, 0, 1, cap, init, tok),
+         enet.connect(eb, 0, ea, 0, tok, 1, cap, delay, np.concatenate(init))),
+        (onet.connect(oa, 0, ob, 0, 1, cap, [], tok), enet.connect(ea, 0, eb, 0, tok, 1, cap)),
+        (onet.connect(oa, 1, os_, 0, 1, 4 * delay, [], tok), enet.connect(ea, 1, es, 0, tok, 1, 4 * delay)),
+    ]
+    onet.finalize()
+    enet.finalize()
+    got = []
+    for step in range(6):
+        assert onet.run(1) == enet.run(1, flags)
+        for oc, ec in chans:
+            assert onet.counters(oc) == enet.counters(ec)
+        want = np.concatenate(onet.pop(os_))
+        e = enet.pop(es)
+        np.testing.assert_array_equal(e, want)
+        got.append(e)
+    stream = np.concatenate(got).reshape(-1, tok)
+    assert len(stream) == 6 * delay
+    np.testing.assert_array_equal(stream, np.tile(np.concatenate(init).reshape(delay, tok), (6, 1)))
+    enet.close()

@@ -46,3 +46,18 @@ def test_ila_fit_tracks_float64_oracle():
     assert np.max(np.abs(losses - losses64) / losses64) < 1e-3
     assert losses[-1] < 0.9 * losses[0]
     assert np.linalg.norm(h.cpu().numpy() - h64) / np.linalg.norm(h64) < 1e-3
+
+
+def test_iterative_ila_tracks_float64_oracle():
+    """Two iterations of indirect learning with the predistorter in the loop
+    (20 Adam steps each on 2^14 samples): every loss curve and the NMSE after
+    each iteration follow the float64 oracle."""
+    import torch
+    from paper_1611_03226_b300 import fit as F
+    w = synth.dpd_fit(n=1 << 14)
+    h, curves, nmse = F.ila_fit_iterative(torch.from_numpy(w.x).cuda(), iterations=2, steps=20)
+    h64, curves64, nmse64 = OF.ila_fit_iterative(w.x, iterations=2, steps=20)
+    for c, c64 in zip(curves, curves64):
+        assert np.max(np.abs(c - c64) / c64) < 1e-3
+    assert np.max(np.abs(np.array(nmse) - nmse64)) < 1e-3
+    assert np.linalg.norm(h.cpu().numpy() - h64) / np.linalg.norm(h64) < 1e-3
