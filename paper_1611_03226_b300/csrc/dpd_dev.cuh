@@ -298,7 +298,7 @@ __device__ __forceinline__ float2 hist_sample(const DpdArgs& a, const DpdPlanHdr
   return a.hist[((size_t)pl.parity_in * a.K + k) * H1 + (H1 + pos)];
 }
 
-constexpr int kBranchGroup = 2;           // branch signals staged at once
+constexpr int kBranchGroup = 1;           // branch signals staged at once
 
 // u^q from the squares u, u^2, u^4, u^8 (q < 16), else by repeated products.
 __device__ __forceinline__ float pow_sq(float u, float u2, float u4, float u8, int q) {
