@@ -424,7 +424,7 @@ def bench_dpd_tiny(args, P, torch, pk):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs)
 
-    modes = {"per_phase_kernels": 0, "persistent_kernel": L.DF_RUN_PERSISTENT}
+    modes = {"per_phase_kernels": 0, "graph_replay": L.DF_RUN_GRAPH, "persistent_kernel": L.DF_RUN_PERSISTENT}
     ms_mode = {}
     for name, flags in modes.items():
         for _ in range(args.warmup):

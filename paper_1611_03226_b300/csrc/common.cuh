@@ -230,9 +230,9 @@ cudaError_t launch_step_begin(EngineDev* e, cudaStream_t s);
 cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                         cudaEvent_t ev1 = nullptr);
 
-cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t s);
+cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t s, bool pdl = false);
 cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile,
-                            uint32_t threads, int max_mt, int n_sm, cudaStream_t s);
+                            uint32_t threads, int max_mt, int n_sm, cudaStream_t s, bool pdl = false);
 int dpd_supported_mt(int M);   // padded tap count used for M (0 = unsupported)
 cudaError_t dpd_prepare();     // one-time kernel attributes (outside graph capture)
 

@@ -13,18 +13,25 @@ int dpd_supported_mt(int M) {
 }
 
 
-__global__ void __launch_bounds__(256) k_dpd_plan(const DpdArgs* args) { dpd_plan_dev(args[blockIdx.x]); }
+// Both kernels may be launched as programmatic dependents (griddep_wait
+// before touching anything an earlier kernel wrote); the plan lets the body
+// launch at once, so the body's launch overlaps the plan.
+__global__ void __launch_bounds__(256) k_dpd_plan(const DpdArgs* args) {
+  griddep_wait();
+  griddep_launch();
+  dpd_plan_dev(args[blockIdx.x]);
+}
 
 template <int R, int MTMAX>
 __global__ void __launch_bounds__(256) k_dpd_body(const DpdArgs* __restrict__ args, int G) {
   extern __shared__ float4 smem_raw[];
+  griddep_wait();
   dpd_body_dev<R, MTMAX>(args, G, Grid{blockIdx.x, gridDim.x}, smem_raw);
 }
 
-cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t s) {
+cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t s, bool pdl) {
   if (n_actors <= 0) return cudaSuccess;
-  k_dpd_plan<<<n_actors, 256, 0, s>>>(args_dev);
-  return cudaGetLastError();
+  return launch_k(pdl, k_dpd_plan, dim3(n_actors), dim3(256), 0, s, args_dev);
 }
 
 static size_t body_smem(uint32_t T, int R, int mtmax, int G) {
@@ -52,15 +59,15 @@ cudaError_t dpd_prepare() {
 
 template <int R, int MTMAX>
 static cudaError_t body_launch(const DpdArgs* args_dev, int n_actors, uint32_t threads, size_t smem,
-                               int n_sm, cudaStream_t s) {
+                               int n_sm, cudaStream_t s, bool pdl) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dpd_body<R, MTMAX>, threads, smem);
-  k_dpd_body<R, MTMAX><<<n_sm * std::max(per_sm, 1), threads, smem, s>>>(args_dev, n_actors);
-  return cudaGetLastError();
+  return launch_k(pdl, k_dpd_body<R, MTMAX>, dim3(n_sm * std::max(per_sm, 1)), dim3(threads), smem, s,
+                  args_dev, n_actors);
 }
 
 cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile, uint32_t threads,
-                            int max_mt, int n_sm, cudaStream_t s) {
+                            int max_mt, int n_sm, cudaStream_t s, bool pdl) {
   if (n_actors <= 0) return cudaSuccess;
   if (n_actors > kMaxGroup) return cudaErrorInvalidValue;
   const int R = (int)(tile / threads);
@@ -68,12 +75,12 @@ cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile
   const size_t smem = body_smem(tile, R, mtmax, n_actors);
   if (smem > (size_t)kBodySmemMax) return cudaErrorInvalidValue;
   if (R == 8) {
-    return mtmax == 16 ? body_launch<8, 16>(args_dev, n_actors, threads, smem, n_sm, s)
-                       : body_launch<8, 32>(args_dev, n_actors, threads, smem, n_sm, s);
+    return mtmax == 16 ? body_launch<8, 16>(args_dev, n_actors, threads, smem, n_sm, s, pdl)
+                       : body_launch<8, 32>(args_dev, n_actors, threads, smem, n_sm, s, pdl);
   }
   if (R == 16) {
-    return mtmax == 16 ? body_launch<16, 16>(args_dev, n_actors, threads, smem, n_sm, s)
-                       : body_launch<16, 32>(args_dev, n_actors, threads, smem, n_sm, s);
+    return mtmax == 16 ? body_launch<16, 16>(args_dev, n_actors, threads, smem, n_sm, s, pdl)
+                       : body_launch<16, 32>(args_dev, n_actors, threads, smem, n_sm, s, pdl);
   }
   return cudaErrorInvalidValue;
 }

@@ -342,10 +342,12 @@ df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
         const int n_launch = no_batch ? op.dpd_n : 1;
         const int per = no_batch ? 1 : op.dpd_n;
         for (int i = 0; i < n_launch; ++i) {
-          DF_CUDA(launch_dpd_plan(op.dpd_dev + i, per, s));
           const auto ev = prof_pair(net, DF_PROF_DPD_BODY, capturing);
+          // without timing events the plan and body are programmatic dependents
+          const bool pdl = !ev.first;
+          DF_CUDA(launch_dpd_plan(op.dpd_dev + i, per, s, pdl));
           if (ev.first) DF_CUDA(cudaEventRecord(ev.first, s));
-          DF_CUDA(launch_dpd_body(op.dpd_dev + i, per, tile, threads, op.max_mt, net->n_sm, s));
+          DF_CUDA(launch_dpd_body(op.dpd_dev + i, per, tile, threads, op.max_mt, net->n_sm, s, pdl));
           if (ev.second) DF_CUDA(cudaEventRecord(ev.second, s));
         }
         break;
