@@ -501,6 +501,32 @@ def bench_md_paper(args, P, torch, pk):
         if i >= args.warmup:
             e2e.append(time.perf_counter() - t0)
     net.close()
+    # the paper's concurrent host actors: a producer thread pushes 64-frame
+    # chunks from pinned memory and a consumer thread pops motion maps into
+    # pinned memory, through channels of 256 frames, while steps run
+    from paper_1611_03226_b300.stream import stream
+    net = P.Net(stream=torch.cuda.current_stream().cuda_stream)
+    src, g, t, m, snk = (net.add_source(), net.add_gauss5(W, H), net.add_thres(W, H, thr),
+                         net.add_med5(W, H), net.add_sink())
+    cap_s, chunk = 256, 64
+    net.connect(src, 0, g, 0, fb, rate, cap_s)
+    net.connect(g, 0, t, 0, fb, rate, cap_s)
+    net.connect(g, 1, t, 1, fb, rate, cap_s, 1)
+    net.connect(t, 0, m, 0, fb, rate, cap_s)
+    net.connect(m, 0, snk, 0, fb, rate, cap_s)
+    net.finalize()
+    pop_buf = torch.empty((chunk, H, W), dtype=torch.uint8).pin_memory()
+    st_s = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got, _ = stream(net, {src: [host[j:j + chunk] for j in range(0, T, chunk)]},
+                        {snk: (chunk, pop_buf)}, flags=L.DF_RUN_GRAPH)
+        dt = time.perf_counter() - t0
+        assert got[snk] == frames_done
+        if i >= args.warmup:
+            st_s.append(dt)
+    net.close()
     # oracle on a bounded sample (64 frames)
     from oracle import motion_paper as MP
     ns = 64 if not args.quick else 16
@@ -515,6 +541,9 @@ def bench_md_paper(args, P, torch, pk):
                          "note": "whole step (6 kernels + step begin) against its channel traffic"},
             "e2e": {"value": frames_done / statistics.mean(e2e), "unit": "frames/s",
                     "h2d_bytes_per_step": T * fb, "d2h_bytes_per_step": frames_done * fb},
+            "e2e_streamed": {"value": frames_done / statistics.mean(st_s), "unit": "frames/s",
+                             "note": "producer and consumer host threads beside the running steps "
+                                     "(DF_IO_CONCURRENT), 256-frame channels, 64-frame chunks"},
             "cpu_baseline": {"value": ns / cpu_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
                              "sample": f"first {ns} frames, numpy single thread"},
             "paper_table3_context": {"i7_gpu_fps": 6063, "carrizo_gpu_fps": 4614,

@@ -192,6 +192,25 @@ df_status df_sync(df_net *net, uint64_t *total_firings);
 df_status df_pop(df_net *net, int32_t sink_actor, void *dst, uint64_t max_tokens,
                  uint64_t *n_popped);
 
+/* Concurrent host I/O: the paper's host actors (Sec. 3.3, 4) run in threads of
+ * their own beside the GPU actors.  With DF_IO_CONCURRENT a push (pop) runs on
+ * a stream of its own, so that its copies overlap df_run's kernels and the
+ * other direction's copies; without the flag these equal df_push / df_pop.
+ * The free space (tokens present) is taken from a snapshot of the channel's
+ * counters, which a concurrent consumer (producer) can only have increased,
+ * so the call may see less than there is but never more.  The tokens are
+ * copied before the counter moves, on the same stream.  At most one thread
+ * may push to a given source and one pop from a given sink at a time; calls
+ * with the flag may run concurrently with df_run, df_sync and each other
+ * (different sources and sinks from different threads).  df_push/df_pop and
+ * df_channel_counters stay on the network's stream and belong to the thread
+ * that runs it. */
+enum { DF_IO_CONCURRENT = 1 };
+df_status df_push_ex(df_net *net, int32_t src_actor, const void *src, uint64_t n_tokens,
+                     uint32_t flags, uint64_t *n_pushed);
+df_status df_pop_ex(df_net *net, int32_t sink_actor, void *dst, uint64_t max_tokens,
+                    uint32_t flags, uint64_t *n_popped);
+
 /* Counters of channel `ch`: tokens produced (excluding initial tokens),
  * consumed, and currently held.  produced + initial == consumed + occupancy. */
 df_status df_channel_counters(df_net *net, int32_t ch, uint64_t *produced, uint64_t *consumed,

@@ -16,6 +16,7 @@ DF_EDEADLOCK, DF_ETIMEOUT, DF_ECUDA, DF_ENOTSUP = -6, -7, -8, -9
 DF_SOURCE, DF_SINK, DF_COPY, DF_DPD, DF_DPD_POLY, DF_DPD_FIR, DF_DPD_ADD, DF_MD = range(1, 9)
 DF_GAUSS5, DF_THRES, DF_MED5 = 9, 10, 11
 DF_RUN_ASYNC, DF_RUN_GRAPH, DF_RUN_PERSISTENT, DF_RUN_NO_BATCH = 1, 2, 4, 8
+DF_IO_CONCURRENT = 1
 DF_MAX_BRANCHES, DF_MAX_TAPS = 16, 32
 DF_PROF_STEP, DF_PROF_DPD_BODY, DF_PROF_MD_MAIN, DF_PROF_COPY_BODY = 0, 1, 2, 3
 
@@ -55,6 +56,8 @@ _PROTOS = {
     "df_run_ex": (C.c_int32, [_P, C.c_int64, C.c_uint32, C.POINTER(C.c_uint64)]),
     "df_sync": (C.c_int32, [_P, C.POINTER(C.c_uint64)]),
     "df_pop": (C.c_int32, [_P, C.c_int32, _P, C.c_uint64, C.POINTER(C.c_uint64)]),
+    "df_push_ex": (C.c_int32, [_P, C.c_int32, _P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
+    "df_pop_ex": (C.c_int32, [_P, C.c_int32, _P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
     "df_channel_counters": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint64),
                                         C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "df_dpd_set_tile": (C.c_int32, [_P, C.c_int32, C.c_uint32, C.c_uint32]),

@@ -32,6 +32,13 @@ struct EngineDev {          // device-resident engine state
   unsigned int barrier_count;   // persistent-kernel grid barrier
   unsigned int barrier_gen;
   unsigned long long total_snap;  // fired_total as the last CTA saw it when releasing a barrier
+  // Published counters for concurrent host I/O: a copy of the counter array
+  // taken when a step has finished (all its bodies done).  Plans commit a
+  // step's counters before its bodies move the data, so a push or pop that
+  // runs beside the steps takes the other side's counter from here.
+  uint64_t* ctr;
+  uint64_t* pub;            // null until concurrent I/O is used
+  uint32_t n_words;         // 2 per channel
 };
 
 // where-codes for EngineDev::status_where
@@ -227,6 +234,7 @@ cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_
 cudaError_t launch_set_u64(uint64_t* p, uint64_t v, cudaStream_t s);
 cudaError_t launch_add_u64(uint64_t* p, uint64_t v, cudaStream_t s);
 cudaError_t launch_step_begin(EngineDev* e, cudaStream_t s);
+cudaError_t launch_publish(EngineDev* e, cudaStream_t s);   // pub = ctr after a step
 cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                         cudaEvent_t ev1 = nullptr);
 

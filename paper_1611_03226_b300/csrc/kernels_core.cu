@@ -20,6 +20,18 @@ cudaError_t launch_step_begin(EngineDev* e, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Publish the counters of a finished step (stream order: every body of the
+// step has completed when this runs).
+__global__ void k_publish(const EngineDev* e) {
+  if (!e->pub) return;
+  for (uint32_t i = threadIdx.x; i < e->n_words; i += blockDim.x) e->pub[i] = e->ctr[i];
+}
+
+cudaError_t launch_publish(EngineDev* e, cudaStream_t s) {
+  k_publish<<<1, 256, 0, s>>>(e);
+  return cudaGetLastError();
+}
+
 __global__ void k_copy_plan(CopyArgs a) { copy_plan_dev(a); }
 __global__ void k_copy_body(CopyArgs a) { copy_body_dev(a, Grid{blockIdx.x, gridDim.x}); }
 

@@ -10,6 +10,7 @@
 // body launch.  A step never returns to the host: rate decisions, scans,
 // gathers and scatters are all device kernels reading the device counters.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -73,12 +74,20 @@ struct df_net {
   uint8_t* arena = nullptr;
   size_t arena_bytes = 0;
   uint64_t* d_ctr = nullptr;
+  uint64_t* d_pub = nullptr;          // counters published after each step (concurrent I/O)
+  std::atomic<bool> io_used{false};   // a concurrent push or pop happened: publish every step
   EngineDev* d_eng = nullptr;
   std::vector<DpdArgs> dpd_host;      // one per predistorter actor (by dpd index)
   std::vector<int> dpd_index;         // actor id -> index in dpd_host (-1)
   DpdArgs* d_dpd = nullptr;           // device copy of dpd_host
   std::vector<Op> program;
   uint64_t* h_pin = nullptr;          // pinned staging (counters, status)
+  // concurrent host I/O (DF_IO_CONCURRENT): [0] pushes, [1] pops, each on a
+  // stream of its own, created on first use (counters are staged in pinned
+  // memory of the calling thread, so several sources or sinks can be served
+  // by threads of their own)
+  cudaStream_t io_stream[2] = {nullptr, nullptr};
+  std::mutex io_mu;
   std::map<std::pair<int64_t, uint32_t>, cudaGraphExec_t> graphs;
   long long wait_limit_ns = 1000000000LL;
   // kernel timing (df_profile_*)
@@ -236,36 +245,37 @@ df_status fail_if_device_error(df_net* net) {
   return st;
 }
 
-df_status read_counters(df_net* net, int32_t ch, uint64_t* wr, uint64_t* rd) {
-  DF_CUDA(cudaMemcpyAsync(net->h_pin, net->d_ctr + 2 * ch, 2 * sizeof(uint64_t),
-                          cudaMemcpyDeviceToHost, net->stream));
-  DF_CUDA(cudaStreamSynchronize(net->stream));
-  *wr = net->h_pin[0];
-  *rd = net->h_pin[1];
+df_status read_counters(df_net* net, int32_t ch, uint64_t* wr, uint64_t* rd,
+                        cudaStream_t s = nullptr, uint64_t* pin = nullptr) {
+  if (!s) s = net->stream;
+  if (!pin) pin = net->h_pin;
+  DF_CUDA(cudaMemcpyAsync(pin, net->d_ctr + 2 * ch, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  *wr = pin[0];
+  *rd = pin[1];
   return DF_OK;
 }
 
 // Copy `bytes` bytes between a linear buffer and a ring starting at token `t`.
 df_status ring_copy(df_net* net, const ChanDesc& c, uint64_t t, void* lin, uint64_t n_tok,
-                    bool to_ring) {
+                    bool to_ring, cudaStream_t s = nullptr) {
+  if (!s) s = net->stream;
   const uint64_t slot = t % c.cap;
   const uint64_t first = std::min<uint64_t>(n_tok, c.cap - slot);
   uint8_t* ring0 = c.ring + slot * c.tok;
   uint8_t* l = static_cast<uint8_t*>(lin);
   if (first) {
     if (to_ring)
-      DF_CUDA(cudaMemcpyAsync(ring0, l, first * c.tok, cudaMemcpyDefault, net->stream));
+      DF_CUDA(cudaMemcpyAsync(ring0, l, first * c.tok, cudaMemcpyDefault, s));
     else
-      DF_CUDA(cudaMemcpyAsync(l, ring0, first * c.tok, cudaMemcpyDefault, net->stream));
+      DF_CUDA(cudaMemcpyAsync(l, ring0, first * c.tok, cudaMemcpyDefault, s));
   }
   if (n_tok > first) {
     const uint64_t rest = n_tok - first;
     if (to_ring)
-      DF_CUDA(cudaMemcpyAsync(c.ring, l + first * c.tok, rest * c.tok, cudaMemcpyDefault,
-                              net->stream));
+      DF_CUDA(cudaMemcpyAsync(c.ring, l + first * c.tok, rest * c.tok, cudaMemcpyDefault, s));
     else
-      DF_CUDA(cudaMemcpyAsync(l + first * c.tok, c.ring, rest * c.tok, cudaMemcpyDefault,
-                              net->stream));
+      DF_CUDA(cudaMemcpyAsync(l + first * c.tok, c.ring, rest * c.tok, cudaMemcpyDefault, s));
   }
   return DF_OK;
 }
@@ -354,6 +364,7 @@ df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
       }
     }
   }
+  if (net->io_used) DF_CUDA(launch_publish(net->d_eng, s));
   if (step_ev.second) DF_CUDA(cudaEventRecord(step_ev.second, s));
   return DF_OK;
 }
@@ -491,6 +502,12 @@ void df_net_destroy(df_net* net) {
   if (net->persist_mem) cudaFree(net->persist_mem);
   if (net->arena) cudaFree(net->arena);
   if (net->h_pin) cudaFreeHost(net->h_pin);
+  for (int i = 0; i < 2; ++i) {
+    if (net->io_stream[i]) {
+      cudaStreamSynchronize(net->io_stream[i]);
+      cudaStreamDestroy(net->io_stream[i]);
+    }
+  }
   if (net->own_stream) cudaStreamDestroy(net->stream);
   delete net;
 }
@@ -606,6 +623,7 @@ df_status df_net_finalize(df_net* net) {
   for (size_t c = 0; c < net->chans.size(); ++c)
     ring[c] = take((size_t)net->chans[c].cap * net->chans[c].tok);
   const Piece p_ctr = take(2 * sizeof(uint64_t) * std::max<size_t>(1, net->chans.size()));
+  const Piece p_pub = take(2 * sizeof(uint64_t) * std::max<size_t>(1, net->chans.size()));
   const Piece p_eng = take(sizeof(EngineDev));
   struct DpdPieces { Piece plan, masks, rank, act, cnt, hist, parity, h; };
   struct MdPieces { Piece plan, counts, tot, off; };
@@ -694,8 +712,19 @@ df_status df_net_finalize(df_net* net) {
                               cudaMemcpyHostToDevice, s));
     ctr0[2 * c] = C.init;
   }
-  if (!ctr0.empty())
+  if (!ctr0.empty()) {
     DF_CUDA(cudaMemcpyAsync(net->d_ctr, ctr0.data(), ctr0.size() * 8, cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaMemcpyAsync(base + p_pub.off, ctr0.data(), ctr0.size() * 8, cudaMemcpyHostToDevice, s));
+  }
+  net->d_pub = reinterpret_cast<uint64_t*>(base + p_pub.off);
+  {
+    // engine word: where the counters and their published copy are
+    uint64_t* ptrs[2] = {net->d_ctr, net->d_pub};
+    const uint32_t words = (uint32_t)(2 * net->chans.size());
+    DF_CUDA(cudaMemcpyAsync(&net->d_eng->ctr, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaMemcpyAsync(&net->d_eng->n_words, &words, sizeof(words), cudaMemcpyHostToDevice, s));
+    DF_CUDA(cudaStreamSynchronize(s));
+  }
   // ---- per-actor device state and the step program ----
   net->dpd_host.assign(dp.size(), DpdArgs{});
   std::vector<std::vector<float2>> hpad(dp.size());
@@ -891,18 +920,60 @@ df_status df_net_finalize(df_net* net) {
   return DF_OK;
 }
 
-df_status df_push(df_net* net, int32_t src_actor, const void* src, uint64_t n_tokens,
-                  uint64_t* n_pushed) {
+namespace {
+
+// Counters of a channel for a push (writer) or pop (reader) beside running
+// steps: the caller's own counter from the live array, the other side's from
+// the copy published after the last finished step.
+df_status read_io_counters(df_net* net, int32_t ch, bool writer, uint64_t* wr, uint64_t* rd,
+                           cudaStream_t s, uint64_t* pin) {
+  DF_CUDA(cudaMemcpyAsync(pin, net->d_ctr + 2 * ch, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(pin + 2, net->d_pub + 2 * ch, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  *wr = writer ? pin[0] : pin[2];
+  *rd = writer ? pin[3] : pin[1];
+  return DF_OK;
+}
+
+// Pinned staging of the calling thread (freed when the thread ends).
+struct ThreadPin {
+  uint64_t* p = nullptr;
+  ~ThreadPin() {
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local ThreadPin t_pin;
+
+// Stream of concurrent pushes (which = 0) or pops (1) and the caller's staging.
+df_status io_channel(df_net* net, int which, cudaStream_t* s, uint64_t** pin) {
+  if (!t_pin.p) DF_CUDA(cudaMallocHost(&t_pin.p, 64));
+  std::lock_guard<std::mutex> lk(net->io_mu);
+  net->io_used = true;
+  if (!net->io_stream[which])
+    DF_CUDA(cudaStreamCreateWithFlags(&net->io_stream[which], cudaStreamNonBlocking));
+  *s = net->io_stream[which];
+  *pin = t_pin.p;
+  return DF_OK;
+}
+
+// Push on stream s.  The free space comes from a snapshot of the counters: on
+// a concurrent stream the consumer may have read more since, so the snapshot
+// only understates it.  The tokens are copied first and wr advanced after
+// them on the same stream, so a plan that sees the new wr sees the data.
+df_status push_on(df_net* net, int32_t src_actor, const void* src, uint64_t n_tokens,
+                  uint64_t* n_pushed, cudaStream_t s, uint64_t* pin) {
   if (!net || (!src && n_tokens)) return DF_EINVAL;
   if (!net->finalized) return DF_ESTATE;
   if (src_actor < 0 || src_actor >= (int)net->actors.size()) return DF_EINVAL;
   const ActorH& A = net->actors[src_actor];
   if (A.kind != DF_SOURCE) return DF_EINVAL;
   DeviceGuard g(net->device);
+  const bool concurrent = s != net->stream;
   std::vector<uint64_t> wr(A.out.size());
   for (size_t p = 0; p < A.out.size(); ++p) {
     uint64_t w, r;
-    const df_status st = read_counters(net, A.out[p], &w, &r);
+    const df_status st = concurrent ? read_io_counters(net, A.out[p], true, &w, &r, s, pin)
+                                    : read_counters(net, A.out[p], &w, &r, s, pin);
     if (st != DF_OK) return st;
     if (net->chans[A.out[p]].cap - (w - r) < n_tokens) return DF_EFULL;
     wr[p] = w;
@@ -917,19 +988,65 @@ df_status df_push(df_net* net, int32_t src_actor, const void* src, uint64_t n_to
           const uint64_t s0 = (wr[0] + done) % c0.cap, s1 = (wr[p] + done) % c.cap;
           const uint64_t run = std::min({n_tokens - done, c0.cap - s0, c.cap - s1});
           DF_CUDA(cudaMemcpyAsync(c.ring + s1 * c.tok, c0.ring + s0 * c0.tok, run * c.tok,
-                                  cudaMemcpyDeviceToDevice, net->stream));
+                                  cudaMemcpyDeviceToDevice, s));
           done += run;
         }
       } else {
-        const df_status st = ring_copy(net, c, wr[p], const_cast<void*>(src), n_tokens, true);
+        const df_status st = ring_copy(net, c, wr[p], const_cast<void*>(src), n_tokens, true, s);
         if (st != DF_OK) return st;
       }
-      DF_CUDA(launch_set_u64(net->d_ctr + 2 * A.out[p], wr[p] + n_tokens, net->stream));
+      DF_CUDA(launch_set_u64(net->d_ctr + 2 * A.out[p], wr[p] + n_tokens, s));
     }
-    DF_CUDA(cudaStreamSynchronize(net->stream));
+    DF_CUDA(cudaStreamSynchronize(s));
   }
   if (n_pushed) *n_pushed = n_tokens;
   return DF_OK;
+}
+
+// Pop on stream s (snapshot of wr: a concurrent producer may have written
+// more since); rd advances after the copy on the same stream.
+df_status pop_on(df_net* net, int32_t sink_actor, void* dst, uint64_t max_tokens,
+                 uint64_t* n_popped, cudaStream_t s, uint64_t* pin) {
+  if (!net || (!dst && max_tokens)) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  if (sink_actor < 0 || sink_actor >= (int)net->actors.size()) return DF_EINVAL;
+  const ActorH& A = net->actors[sink_actor];
+  if (A.kind != DF_SINK) return DF_EINVAL;
+  DeviceGuard g(net->device);
+  const int32_t ch = A.in[0];
+  uint64_t w, r;
+  df_status st = s != net->stream ? read_io_counters(net, ch, false, &w, &r, s, pin)
+                                  : read_counters(net, ch, &w, &r, s, pin);
+  if (st != DF_OK) return st;
+  const uint64_t n = std::min(max_tokens, w - r);
+  if (n) {
+    st = ring_copy(net, net->chans[ch].desc, r, dst, n, false, s);
+    if (st != DF_OK) return st;
+    DF_CUDA(launch_set_u64(net->d_ctr + 2 * ch + 1, r + n, s));
+    DF_CUDA(cudaStreamSynchronize(s));
+  }
+  if (n_popped) *n_popped = n;
+  return DF_OK;
+}
+
+}  // namespace
+
+df_status df_push(df_net* net, int32_t src_actor, const void* src, uint64_t n_tokens,
+                  uint64_t* n_pushed) {
+  if (!net) return DF_EINVAL;
+  return push_on(net, src_actor, src, n_tokens, n_pushed, net->stream, net->h_pin);
+}
+
+df_status df_push_ex(df_net* net, int32_t src_actor, const void* src, uint64_t n_tokens,
+                     uint32_t flags, uint64_t* n_pushed) {
+  if (!net || (flags & ~(uint32_t)DF_IO_CONCURRENT)) return DF_EINVAL;
+  if (!(flags & DF_IO_CONCURRENT)) return df_push(net, src_actor, src, n_tokens, n_pushed);
+  if (!net->finalized) return DF_ESTATE;
+  cudaStream_t s;
+  uint64_t* pin;
+  const df_status st = io_channel(net, 0, &s, &pin);
+  if (st != DF_OK) return st;
+  return push_on(net, src_actor, src, n_tokens, n_pushed, s, pin);
 }
 
 df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_firings) {
@@ -956,7 +1073,8 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
     if (ev.second) DF_CUDA(cudaEventRecord(ev.second, net->stream));
   } else if (n_steps >= 0) {
     if (flags & DF_RUN_GRAPH) {
-      auto key = std::make_pair(n_steps, flags & DF_RUN_NO_BATCH);
+      // the graph of a step ends with the counter publication once concurrent I/O is in use
+      auto key = std::make_pair(n_steps, (flags & DF_RUN_NO_BATCH) | (net->io_used ? 0x100u : 0u));
       auto it = net->graphs.find(key);
       if (it == net->graphs.end()) {
         cudaGraph_t graph;
@@ -1019,25 +1137,20 @@ df_status df_sync(df_net* net, uint64_t* total_firings) {
 
 df_status df_pop(df_net* net, int32_t sink_actor, void* dst, uint64_t max_tokens,
                  uint64_t* n_popped) {
-  if (!net || (!dst && max_tokens)) return DF_EINVAL;
+  if (!net) return DF_EINVAL;
+  return pop_on(net, sink_actor, dst, max_tokens, n_popped, net->stream, net->h_pin);
+}
+
+df_status df_pop_ex(df_net* net, int32_t sink_actor, void* dst, uint64_t max_tokens, uint32_t flags,
+                    uint64_t* n_popped) {
+  if (!net || (flags & ~(uint32_t)DF_IO_CONCURRENT)) return DF_EINVAL;
+  if (!(flags & DF_IO_CONCURRENT)) return df_pop(net, sink_actor, dst, max_tokens, n_popped);
   if (!net->finalized) return DF_ESTATE;
-  if (sink_actor < 0 || sink_actor >= (int)net->actors.size()) return DF_EINVAL;
-  const ActorH& A = net->actors[sink_actor];
-  if (A.kind != DF_SINK) return DF_EINVAL;
-  DeviceGuard g(net->device);
-  const int32_t ch = A.in[0];
-  uint64_t w, r;
-  df_status st = read_counters(net, ch, &w, &r);
+  cudaStream_t s;
+  uint64_t* pin;
+  const df_status st = io_channel(net, 1, &s, &pin);
   if (st != DF_OK) return st;
-  const uint64_t n = std::min(max_tokens, w - r);
-  if (n) {
-    st = ring_copy(net, net->chans[ch].desc, r, dst, n, false);
-    if (st != DF_OK) return st;
-    DF_CUDA(launch_set_u64(net->d_ctr + 2 * ch + 1, r + n, net->stream));
-    DF_CUDA(cudaStreamSynchronize(net->stream));
-  }
-  if (n_popped) *n_popped = n;
-  return DF_OK;
+  return pop_on(net, sink_actor, dst, max_tokens, n_popped, s, pin);
 }
 
 df_status df_channel_counters(df_net* net, int32_t ch, uint64_t* produced, uint64_t* consumed,

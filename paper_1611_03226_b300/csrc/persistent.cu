@@ -39,7 +39,13 @@ __device__ bool grid_barrier(EngineDev* e, unsigned int expected, long long limi
     int ok = 1;
     if (arrived == expected) {
       e->barrier_count = 0;
-      if (snap) e->total_snap = *reinterpret_cast<volatile unsigned long long*>(&e->fired_total);
+      if (snap) {
+        e->total_snap = *reinterpret_cast<volatile unsigned long long*>(&e->fired_total);
+        // the step is over: publish its counters for concurrent host I/O
+        if (e->pub)
+          for (uint32_t i = 0; i < e->n_words; ++i)
+            e->pub[i] = reinterpret_cast<volatile uint64_t*>(e->ctr)[i];
+      }
       __threadfence();
       atomicAdd(&e->barrier_gen, 1u);
     } else {

@@ -119,7 +119,10 @@ class Net:
         L.check(L.lib.df_net_finalize(self.h), "df_net_finalize")
 
     # ---- execution ----
-    def push(self, src, buf, n_tokens=None):
+    def push(self, src, buf, n_tokens=None, concurrent=False):
+        """Copy whole tokens into every output channel of source `src` (all or
+        nothing).  concurrent=True runs the copy on the network's push stream, so
+        it may overlap a run() in another thread (df_push_ex, DF_IO_CONCURRENT)."""
         addr, nbytes = _ptr(buf)
         tok = self.chan_tok[self.actor_out[src][0]]
         if n_tokens is None:
@@ -129,7 +132,8 @@ class Net:
         elif n_tokens * tok > nbytes:
             raise ValueError("buffer too small")
         n = C.c_uint64()
-        L.check(L.lib.df_push(self.h, src, C.c_void_p(addr), n_tokens, C.byref(n)), "df_push")
+        L.check(L.lib.df_push_ex(self.h, src, C.c_void_p(addr), n_tokens,
+                                 L.DF_IO_CONCURRENT if concurrent else 0, C.byref(n)), "df_push")
         return n.value
 
     def run(self, n_steps=-1, flags=0):
@@ -145,18 +149,27 @@ class Net:
         L.check(L.lib.df_sync(self.h, C.byref(n)), "df_sync")
         return n.value
 
-    def pop(self, sink, max_tokens=None, out=None, dtype=np.uint8):
+    def pop(self, sink, max_tokens=None, out=None, dtype=np.uint8, concurrent=False):
+        """Copy up to max_tokens tokens out of sink `sink`.  concurrent=True runs
+        the copy on the network's pop stream (df_pop_ex, DF_IO_CONCURRENT); then
+        `out` or `max_tokens` must be given."""
         ch = self.actor_in[sink][0]
         tok = self.chan_tok[ch]
         if out is None:
-            produced, consumed, occ = self.counters(ch)
-            n_max = occ if max_tokens is None else min(max_tokens, occ)
+            if concurrent:
+                if max_tokens is None:
+                    raise ValueError("a concurrent pop needs out or max_tokens")
+                n_max = max_tokens
+            else:
+                produced, consumed, occ = self.counters(ch)
+                n_max = occ if max_tokens is None else min(max_tokens, occ)
             out = np.empty(n_max * tok, np.uint8)
         addr, nbytes = _ptr(out)
         cap = nbytes // tok
         n = C.c_uint64()
-        L.check(L.lib.df_pop(self.h, sink, C.c_void_p(addr),
-                             cap if max_tokens is None else min(cap, max_tokens), C.byref(n)),
+        L.check(L.lib.df_pop_ex(self.h, sink, C.c_void_p(addr),
+                                cap if max_tokens is None else min(cap, max_tokens),
+                                L.DF_IO_CONCURRENT if concurrent else 0, C.byref(n)),
                 "df_pop")
         if isinstance(out, np.ndarray):
             return out[: n.value * tok].view(dtype)
