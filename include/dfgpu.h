@@ -25,8 +25,8 @@
  * Memory.  A network owns every device buffer it allocates (channel rings,
  * counters, per-actor state); df_net_destroy frees them.  Channels are ring
  * buffers of `capacity` tokens of `token_bytes` bytes, token i of the stream
- * living in slot i mod capacity.  Push and pop copy (the caller keeps its
- * buffers).  All device work of a network is ordered on its stream.
+ * living in slot i mod capacity (or laid out as in Sec. 3.2, Eq. 1 and Fig. 2,
+ * see DF_CAPACITY_EQ1).  Push and pop copy (the caller keeps its buffers).  All device work of a network is ordered on its stream.
  *
  * Errors.  Every call returns a df_status; DF_OK (0) on success, a negative
  * code otherwise.  Out-parameters are written only on success.  No call aborts
@@ -150,7 +150,22 @@ df_status df_actor_add(df_net *net, int32_t kind, const void *params, size_t par
  * before any firing; their contents come from `initial_data` (host,
  * initial_tokens*token_bytes bytes) or are zero when it is NULL.  Control
  * channels need rate 1 and no initial tokens.  capacity must be >= initial +
- * rate.  Self-loops (src_actor == dst_actor) are rejected. */
+ * rate.  Self-loops (src_actor == dst_actor) are rejected.
+ *
+ * capacity_tokens == DF_CAPACITY_EQ1 selects the paper's own channel layout
+ * (Sec. 3.2): the buffer size is not chosen by the caller but set by Eq. 1,
+ * 2r slots (a double buffer) without a delay token and 3r+1 slots with one,
+ * and a channel with a delay token follows the access pattern of Fig. 2: the
+ * delay token sits in slot 0, write k fills slots 1+(kr mod 3r) .. +r-1, read
+ * k takes slots (kr mod 3r) .. +r-1, and the write that fills slot 3r is
+ * followed by a copy of slot 3r into slot 0.  Every window of r tokens is then
+ * one contiguous run of slots.  Such a channel holds at most 2r (no delay) or
+ * 3r (delay) unread tokens: one more window of r would overwrite a token
+ * not yet read.  Pushes into it write whole windows (n_tokens a multiple of
+ * r, else DF_EINVAL).  initial_tokens must be 0 or 1 (the paper gives the pattern
+ * for one delay token) and the writer must be a host source or an actor of a
+ * fixed token rate per firing (not the output of DF_MD); else DF_EINVAL. */
+#define DF_CAPACITY_EQ1 0u
 df_status df_channel_connect(df_net *net, int32_t src_actor, int32_t src_port,
                              int32_t dst_actor, int32_t dst_port, uint32_t token_bytes,
                              uint32_t rate, uint32_t capacity_tokens, uint32_t initial_tokens,
@@ -215,6 +230,30 @@ df_status df_pop_ex(df_net *net, int32_t sink_actor, void *dst, uint64_t max_tok
  * consumed, and currently held.  produced + initial == consumed + occupancy. */
 df_status df_channel_counters(df_net *net, int32_t ch, uint64_t *produced, uint64_t *consumed,
                               uint64_t *occupancy);
+
+/* Layout and size of channel `ch`: capacity = the most unread tokens it can
+ * hold; slots = buffer slots allocated (capacity, or capacity + 1 for a
+ * delay channel in the paper's layout); buffer_bytes = slots * token_bytes;
+ * layout = DF_LAYOUT_RING or DF_LAYOUT_EQ1.  Valid before and after
+ * finalize. */
+enum { DF_LAYOUT_RING = 0, DF_LAYOUT_EQ1 = 1 };
+typedef struct {
+    uint64_t capacity;
+    uint64_t slots;
+    uint64_t buffer_bytes;
+    uint32_t token_bytes;
+    uint32_t rate;
+    uint32_t initial_tokens;
+    int32_t layout;
+} df_channel_info_t;
+df_status df_channel_info(df_net *net, int32_t ch, df_channel_info_t *out);
+
+/* Copy n_slots raw buffer slots of channel `ch`, starting at slot first_slot,
+ * to `dst` (host), whatever tokens they hold: the physical layout (ring or
+ * Fig. 2) made visible for inspection.  Runs on the network's stream and
+ * blocks; DF_EINVAL when the range exceeds the slots of the channel. */
+df_status df_channel_peek_slots(df_net *net, int32_t ch, uint64_t first_slot, uint64_t n_slots,
+                                void *dst);
 
 /* Tile configuration of the predistorter kernel for one actor (0 = default):
  * samples per tile and threads per CTA.  The autotuner sets these. */

@@ -12,8 +12,9 @@ Model (Sec. 2.2, Sec. 3.1, Sec. 3.2):
 * Channels not attached to a control port may hold initial (delay) tokens.
   The paper allows 0 or 1 and notes the generalisation to more; this
   interpreter accepts any count below the capacity.
-* Capacity is chosen by the user (the paper fixes it by Eq. 1; see
-  :mod:`oracle.paper_layout`).
+* Capacity is chosen by the user, or, with capacity="eq1", fixed as the paper
+  does by Eq. 1: 2r unread tokens without a delay token, 3r with one (the
+  reading of Fig. 2 in :mod:`oracle.paper_layout`).
 
 Reading adopted for bounded steps (the paper runs one thread per actor and has
 no notion of a step): ``run(n)`` performs n sweeps; a sweep visits the actors
@@ -34,6 +35,8 @@ import threading
 from collections import deque
 
 import numpy as np
+
+from . import paper_layout
 
 
 class NetworkError(Exception):
@@ -143,6 +146,10 @@ class Network:
         if src_port in self.out_ch[src] or dst_port in self.in_ch[dst]:
             raise NetworkError("a port connects to exactly one channel (Sec. 3.2)")
         initial = list(initial)
+        if capacity == "eq1":
+            if len(initial) > 1:
+                raise NetworkError("Eq. 1 covers at most one delay token (Sec. 3.2)")
+            capacity = paper_layout.eq1_unread_capacity(rate, len(initial) == 1)
         if capacity < len(initial) + rate:
             raise NetworkError("capacity must hold the initial tokens plus one firing")
         dst_actor = self.actors[dst]

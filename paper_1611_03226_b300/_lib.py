@@ -17,6 +17,8 @@ DF_SOURCE, DF_SINK, DF_COPY, DF_DPD, DF_DPD_POLY, DF_DPD_FIR, DF_DPD_ADD, DF_MD 
 DF_GAUSS5, DF_THRES, DF_MED5 = 9, 10, 11
 DF_RUN_ASYNC, DF_RUN_GRAPH, DF_RUN_PERSISTENT, DF_RUN_NO_BATCH = 1, 2, 4, 8
 DF_IO_CONCURRENT = 1
+DF_CAPACITY_EQ1 = 0
+DF_LAYOUT_RING, DF_LAYOUT_EQ1 = 0, 1
 DF_MAX_BRANCHES, DF_MAX_TAPS = 16, 32
 DF_PROF_STEP, DF_PROF_DPD_BODY, DF_PROF_MD_MAIN, DF_PROF_COPY_BODY = 0, 1, 2, 3
 
@@ -33,6 +35,12 @@ class MdParams(C.Structure):
 
 class ImgParams(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("threshold", C.c_int32)]
+
+
+class ChannelInfo(C.Structure):
+    _fields_ = [("capacity", C.c_uint64), ("slots", C.c_uint64), ("buffer_bytes", C.c_uint64),
+                ("token_bytes", C.c_uint32), ("rate", C.c_uint32), ("initial_tokens", C.c_uint32),
+                ("layout", C.c_int32)]
 
 
 class DfError(RuntimeError):
@@ -58,6 +66,8 @@ _PROTOS = {
     "df_pop": (C.c_int32, [_P, C.c_int32, _P, C.c_uint64, C.POINTER(C.c_uint64)]),
     "df_push_ex": (C.c_int32, [_P, C.c_int32, _P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
     "df_pop_ex": (C.c_int32, [_P, C.c_int32, _P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
+    "df_channel_info": (C.c_int32, [_P, C.c_int32, C.POINTER(ChannelInfo)]),
+    "df_channel_peek_slots": (C.c_int32, [_P, C.c_int32, C.c_uint64, C.c_uint64, C.c_void_p]),
     "df_channel_counters": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint64),
                                         C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "df_dpd_set_tile": (C.c_int32, [_P, C.c_int32, C.c_uint32, C.c_uint32]),

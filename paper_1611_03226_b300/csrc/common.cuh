@@ -5,6 +5,14 @@
 // tokens included), rd = tokens ever read; token i sits in slot i mod cap.
 // Counters are 64-bit and only grow, so occupancy = wr - rd and
 // free = cap - (wr - rd) are exact at any time.
+//
+// A channel in the paper's layout with a delay token (Sec. 3.2, Fig. 2) has
+// one slot more: readers take token i from slot i mod cap (cap = 3r), writers
+// put it in slot 1 + (i - 1) mod cap, so a write window never wraps, and the
+// token that lands in slot cap is copied to slot 0 after its writer's body
+// (the spill).  Writers see the channel through a descriptor whose ring starts
+// at slot 1 and whose token index is shifted by wshift = 1; with that view
+// every writer's ring arithmetic stays (i - wshift) mod cap.
 #pragma once
 #include <cstdint>
 #include <cuda.h>
@@ -22,6 +30,8 @@ struct ChanDesc {          // immutable after finalize
   uint64_t tok;            // bytes per token
   uint32_t rate;
   uint32_t id;             // index into the counter array
+  uint32_t wshift;         // 1: writer view of a delay channel in the paper's layout
+  uint32_t pad_;
 };
 
 struct EngineDev {          // device-resident engine state
@@ -54,8 +64,22 @@ __host__ __device__ inline uint64_t* wr_ptr(uint64_t* ctr, uint32_t ch) { return
 __host__ __device__ inline uint64_t* rd_ptr(uint64_t* ctr, uint32_t ch) { return ctr + 2 * ch + 1; }
 
 __host__ __device__ inline uint8_t* slot_ptr(const ChanDesc& c, uint64_t token_index) {
-  return c.ring + (token_index % c.cap) * c.tok;
+  return c.ring + ((token_index - c.wshift) % c.cap) * c.tok;
 }
+
+// Copy of slot cap into slot 0 after a write window reached slot cap (Fig. 2).
+// The writer's plan keeps its counter from before the step (wr_before); the
+// step wrote tokens wr_before .. wr-1, and the one among them whose index is
+// a multiple of cap (at most one: a step writes at most cap tokens) sits in
+// slot cap.
+struct SpillArgs {
+  uint8_t* ring;            // slot 0 of the buffer (reader view)
+  uint64_t cap, tok;
+  const uint64_t* wr_before;
+  const uint64_t* ctr;
+  uint32_t id;
+  uint32_t unit;            // copy granularity in bytes: 16, 4 or 1
+};
 
 #ifdef __CUDACC__
 __device__ inline void set_status(EngineDev* e, int32_t code, int32_t where) {
@@ -195,12 +219,13 @@ struct MdArgs {
 
 // ------------------------------------------------ persistent step kernel ----
 constexpr int kPersistThreads = 256;
-enum : int { kPersistCopy = 1, kPersistDpd = 2, kPersistDyn = 3, kPersistMd = 4, kPersistImg = 5 };
+enum : int { kPersistCopy = 1, kPersistDpd = 2, kPersistDyn = 3, kPersistMd = 4, kPersistImg = 5,
+             kPersistSpill = 6 };
 
 struct PersistOp {            // one entry of the device-side step program
   int kind;
   int n;                      // predistorter group size
-  const void* args;           // CopyArgs / DpdArgs[n] / DynArgs / MdArgs in device memory
+  const void* args;           // CopyArgs / DpdArgs[n] / DynArgs / MdArgs / ImgArgs / SpillArgs[n]
 };
 
 // --------------------------------------- programmatic dependent launch ----
@@ -235,6 +260,7 @@ cudaError_t launch_set_u64(uint64_t* p, uint64_t v, cudaStream_t s);
 cudaError_t launch_add_u64(uint64_t* p, uint64_t v, cudaStream_t s);
 cudaError_t launch_step_begin(EngineDev* e, cudaStream_t s);
 cudaError_t launch_publish(EngineDev* e, cudaStream_t s);   // pub = ctr after a step
+cudaError_t launch_spill(const SpillArgs& a, cudaStream_t s);
 cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                         cudaEvent_t ev1 = nullptr);
 

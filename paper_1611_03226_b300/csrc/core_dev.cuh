@@ -45,7 +45,7 @@ __device__ inline void copy_units(const CopyArgs& a, const CopyPlan& pl, Grid g)
   for (int p = 0; p < a.n_out; ++p) {
     const ChanDesc& o = a.out[p];
     const uint64_t out_ring = o.cap * o.tok;
-    const uint64_t out_off = (pl.wr0[p] % o.cap) * o.tok;
+    const uint64_t out_off = ((pl.wr0[p] - o.wshift) % o.cap) * o.tok;
     for (uint64_t u = g.b * (uint64_t)blockDim.x + threadIdx.x; u < n_units; u += stride) {
       uint64_t b = u * unit;
       uint64_t si = in_off + b;
@@ -63,6 +63,26 @@ __device__ inline void copy_body_dev(const CopyArgs& a, Grid g) {
   if (a.unit == 16) copy_units<uint4>(a, pl, g);
   else if (a.unit == 4) copy_units<uint32_t>(a, pl, g);
   else copy_units<uint8_t>(a, pl, g);
+}
+
+// Spill of a delay channel in the paper's layout (Fig. 2): every CTA of the
+// grid copies its share of the token in slot cap to slot 0.
+__device__ inline void spill_dev(const SpillArgs& a, Grid g) {
+  // tokens w0 .. w1-1 were written (w0 >= 1: the delay token is token 0)
+  const uint64_t w1 = a.ctr[2 * a.id], w0 = *a.wr_before;
+  if ((w1 - 1) / a.cap == (w0 - 1) / a.cap) return;
+  const uint8_t* src = a.ring + a.cap * a.tok;
+  const uint64_t stride = (uint64_t)g.n * blockDim.x;
+  const uint64_t first = g.b * (uint64_t)blockDim.x + threadIdx.x;
+  if (a.unit == 16) {
+    for (uint64_t u = first; u < a.tok / 16; u += stride)
+      reinterpret_cast<uint4*>(a.ring)[u] = reinterpret_cast<const uint4*>(src)[u];
+  } else if (a.unit == 4) {
+    for (uint64_t u = first; u < a.tok / 4; u += stride)
+      reinterpret_cast<uint32_t*>(a.ring)[u] = reinterpret_cast<const uint32_t*>(src)[u];
+  } else {
+    for (uint64_t u = first; u < a.tok; u += stride) a.ring[u] = src[u];
+  }
 }
 
 }  // namespace dfg

@@ -275,7 +275,7 @@ __device__ inline void dpd_plan_dev(const DpdArgs& a) {
     a.plan->rd_data0 = s_rdd;
     a.plan->wr_out0 = s_wro;
     a.plan->slot_data0 = s_rdd % a.data.cap;
-    a.plan->slot_out0 = s_wro % a.out.cap;
+    a.plan->slot_out0 = (s_wro - a.out.wshift) % a.out.cap;
     a.plan->parity_in = s_par;
     if (n > 0) *a.parity = s_par ^ 1u;
     if (has_ctrl) *rd_ptr(ctr, a.ctrl.id) = s_rdc + n;

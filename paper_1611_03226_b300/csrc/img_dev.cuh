@@ -42,7 +42,7 @@ __device__ inline void img_plan_dev(const ImgArgs& a) {
   for (int p = 0; p < a.n_out; ++p) {
     const uint64_t w = *wr_ptr(ctr, a.out[p].id);
     a.plan->wr0[p] = w;
-    a.plan->slot_out[p] = w % a.out[p].cap;
+    a.plan->slot_out[p] = (w - a.out[p].wshift) % a.out[p].cap;
     *wr_ptr(ctr, a.out[p].id) = w + n * r;
   }
   atomicAdd(&a.eng->fired_step, (unsigned long long)n);

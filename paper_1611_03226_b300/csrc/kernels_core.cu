@@ -1,4 +1,6 @@
 // Counter maintenance and the launchers of the copy actor.
+#include <algorithm>
+
 #include "core_dev.cuh"
 
 namespace dfg {
@@ -29,6 +31,15 @@ __global__ void k_publish(const EngineDev* e) {
 
 cudaError_t launch_publish(EngineDev* e, cudaStream_t s) {
   k_publish<<<1, 256, 0, s>>>(e);
+  return cudaGetLastError();
+}
+
+__global__ void k_spill(SpillArgs a) { spill_dev(a, Grid{blockIdx.x, gridDim.x}); }
+
+cudaError_t launch_spill(const SpillArgs& a, cudaStream_t s) {
+  const uint64_t units = a.tok / a.unit;
+  const unsigned blocks = (unsigned)std::min<uint64_t>(64, (units + 255) / 256);
+  k_spill<<<blocks ? blocks : 1, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -38,8 +38,11 @@ struct ActorH {
 struct ChanH {
   int32_t src, sport, dst, dport;
   uint32_t tok, rate, cap, init;
+  bool eq1 = false;                   // the paper's layout (Eq. 1, Fig. 2)
   std::vector<uint8_t> init_data;
-  ChanDesc desc{};
+  ChanDesc desc{};                    // reader view
+  ChanDesc wdesc{};                   // writer view (differs for a delay channel in the paper's layout)
+  uint64_t slots() const { return (uint64_t)cap + (eq1 && init ? 1 : 0); }
 };
 
 enum OpKind { kOpCopy = 1, kOpDpd = 2, kOpMd = 3, kOpDyn = 4, kOpImg = 5 };
@@ -55,6 +58,7 @@ struct Op {
   int dpd_n = 0;                      // actors in the group
   int dpd_first_actor = -1;           // actor id of the first member
   int max_mt = 0;
+  std::vector<SpillArgs> spills;      // Fig. 2 copies after the op's bodies
 };
 
 struct Piece {                        // one carve of the device arena
@@ -260,7 +264,7 @@ df_status read_counters(df_net* net, int32_t ch, uint64_t* wr, uint64_t* rd,
 df_status ring_copy(df_net* net, const ChanDesc& c, uint64_t t, void* lin, uint64_t n_tok,
                     bool to_ring, cudaStream_t s = nullptr) {
   if (!s) s = net->stream;
-  const uint64_t slot = t % c.cap;
+  const uint64_t slot = (t - c.wshift) % c.cap;
   const uint64_t first = std::min<uint64_t>(n_tok, c.cap - slot);
   uint8_t* ring0 = c.ring + slot * c.tok;
   uint8_t* l = static_cast<uint8_t*>(lin);
@@ -363,6 +367,7 @@ df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
         break;
       }
     }
+    for (const SpillArgs& sp : op.spills) DF_CUDA(launch_spill(sp, s));
   }
   if (net->io_used) DF_CUDA(launch_publish(net->d_eng, s));
   if (step_ev.second) DF_CUDA(cudaEventRecord(step_ev.second, s));
@@ -384,12 +389,13 @@ df_status build_persistent(df_net* net) {
   std::vector<PersistOp> ops;
   size_t bytes = 0;
   for (const Op& op : net->program) {
+    if (!op.spills.empty()) bytes += align256(sizeof(SpillArgs) * op.spills.size());
     if (op.kind == kOpCopy) bytes += align256(sizeof(CopyArgs));
     if (op.kind == kOpDyn) bytes += align256(sizeof(DynArgs));
     if (op.kind == kOpMd) bytes += align256(sizeof(MdArgs));
     if (op.kind == kOpImg) bytes += align256(sizeof(ImgArgs));
   }
-  bytes += align256(sizeof(PersistOp) * std::max<size_t>(1, net->program.size()));
+  bytes += align256(sizeof(PersistOp) * std::max<size_t>(1, 2 * net->program.size()));
   if (cudaMalloc(&net->persist_mem, bytes) != cudaSuccess) {
     cudaGetLastError();
     net->persist_mem = nullptr;
@@ -430,6 +436,16 @@ df_status build_persistent(df_net* net) {
       mtmax = std::max(mtmax, op.max_mt);
     }
     ops.push_back(p);
+    if (!op.spills.empty()) {
+      DF_CUDA(cudaMemcpyAsync(base + off, op.spills.data(), sizeof(SpillArgs) * op.spills.size(),
+                              cudaMemcpyHostToDevice, net->stream));
+      PersistOp q{};
+      q.kind = kPersistSpill;
+      q.n = (int)op.spills.size();
+      q.args = base + off;
+      off += align256(sizeof(SpillArgs) * op.spills.size());
+      ops.push_back(q);
+    }
   }
   net->d_persist_ops = reinterpret_cast<PersistOp*>(base + off);
   if (!ops.empty())
@@ -577,9 +593,16 @@ df_status df_channel_connect(df_net* net, int32_t src_actor, int32_t src_port, i
   if (src_actor == dst_actor) return DF_EINVAL;
   if (src_port < 0 || dst_port < 0 || src_port >= 64 || dst_port >= 64) return DF_EINVAL;
   if (token_bytes == 0 || rate == 0) return DF_EINVAL;
-  if ((uint64_t)capacity_tokens < (uint64_t)initial_tokens + rate) return DF_EINVAL;
   ActorH& S = net->actors[src_actor];
   ActorH& D = net->actors[dst_actor];
+  const bool eq1 = capacity_tokens == DF_CAPACITY_EQ1;
+  if (eq1) {
+    // Eq. 1: a double buffer of 2r tokens, or 3r + 1 slots around one delay
+    // token of which 3r hold unread tokens (Fig. 2)
+    if (initial_tokens > 1 || S.kind == DF_MD || (uint64_t)rate * 3 > 0xffffffffull) return DF_EINVAL;
+    capacity_tokens = initial_tokens ? 3 * rate : 2 * rate;
+  }
+  if ((uint64_t)capacity_tokens < (uint64_t)initial_tokens + rate) return DF_EINVAL;
   if (S.kind == DF_SINK || D.kind == DF_SOURCE) return DF_EINVAL;
   if ((int)S.out.size() > src_port && S.out[src_port] >= 0) return DF_EINVAL;
   if ((int)D.in.size() > dst_port && D.in[dst_port] >= 0) return DF_EINVAL;
@@ -588,6 +611,7 @@ df_status df_channel_connect(df_net* net, int32_t src_actor, int32_t src_port, i
   ChanH c{};
   c.src = src_actor; c.sport = src_port; c.dst = dst_actor; c.dport = dst_port;
   c.tok = token_bytes; c.rate = rate; c.cap = capacity_tokens; c.init = initial_tokens;
+  c.eq1 = eq1;
   if (initial_tokens && initial_data) {
     const uint8_t* p = static_cast<const uint8_t*>(initial_data);
     c.init_data.assign(p, p + (size_t)initial_tokens * token_bytes);
@@ -621,7 +645,7 @@ df_status df_net_finalize(df_net* net) {
   };
   std::vector<Piece> ring(net->chans.size());
   for (size_t c = 0; c < net->chans.size(); ++c)
-    ring[c] = take((size_t)net->chans[c].cap * net->chans[c].tok);
+    ring[c] = take((size_t)net->chans[c].slots() * net->chans[c].tok);
   const Piece p_ctr = take(2 * sizeof(uint64_t) * std::max<size_t>(1, net->chans.size()));
   const Piece p_pub = take(2 * sizeof(uint64_t) * std::max<size_t>(1, net->chans.size()));
   const Piece p_eng = take(sizeof(EngineDev));
@@ -707,6 +731,12 @@ df_status df_net_finalize(df_net* net) {
     C.desc.tok = C.tok;
     C.desc.rate = C.rate;
     C.desc.id = (uint32_t)c;
+    C.desc.wshift = 0;
+    C.wdesc = C.desc;
+    if (C.slots() > C.cap) {            // writers start at slot 1 (Fig. 2)
+      C.wdesc.ring += C.tok;
+      C.wdesc.wshift = 1;
+    }
     if (C.init && !C.init_data.empty())
       DF_CUDA(cudaMemcpyAsync(C.desc.ring, C.init_data.data(), C.init_data.size(),
                               cudaMemcpyHostToDevice, s));
@@ -743,7 +773,7 @@ df_status df_net_finalize(df_net* net) {
         d.ctrl = net->chans[A.in[0]].desc;
         d.data = net->chans[A.in[1]].desc;
       }
-      d.out = net->chans[A.out[0]].desc;
+      d.out = net->chans[A.out[0]].wdesc;
       d.ctr = net->d_ctr;
       d.eng = net->d_eng;
       d.K = fir ? 1 : A.dpd.K;
@@ -778,11 +808,26 @@ df_status df_net_finalize(df_net* net) {
     DF_CUDA(cudaMemcpyAsync(net->d_dpd, net->dpd_host.data(), sizeof(DpdArgs) * net->dpd_host.size(),
                             cudaMemcpyHostToDevice, s));
   net->program.clear();
+  // Fig. 2 copy after the writer of a delay channel in the paper's layout
+  auto add_spill = [&](Op& op, int32_t ch, const uint64_t* wr_before) {
+    const ChanH& C = net->chans[ch];
+    if (!C.wdesc.wshift) return;
+    SpillArgs sp{};
+    sp.ring = C.desc.ring;
+    sp.cap = C.cap;
+    sp.tok = C.tok;
+    sp.wr_before = wr_before;
+    sp.ctr = net->d_ctr;
+    sp.id = (uint32_t)ch;
+    sp.unit = C.tok % 16 == 0 ? 16 : (C.tok % 4 == 0 ? 4 : 1);
+    op.spills.push_back(sp);
+  };
   std::vector<int> group;                 // current predistorter group (actor ids)
   auto flush_group = [&]() {
     if (group.empty()) return;
     Op op{};
     op.kind = kOpDpd;
+    for (int a : group) add_spill(op, net->actors[a].out[0], &net->dpd_host[net->dpd_index[a]].plan->wr_out0);
     op.dpd_dev = net->d_dpd + net->dpd_index[group[0]];
     op.dpd_n = (int)group.size();
     op.dpd_first_actor = group[0];
@@ -817,7 +862,7 @@ df_status df_net_finalize(df_net* net) {
         y.bit[p] = always ? -1 : (poly ? p - 1 : p);
         y.is_out[p] = poly ? (p > 0) : (p == A.dpd.K);
         const int32_t c = poly ? (p == 0 ? A.in[1] : A.out[p - 1]) : (p < A.dpd.K ? A.in[p + 1] : A.out[0]);
-        y.port[p] = net->chans[c].desc;
+        y.port[p] = y.is_out[p] ? net->chans[c].wdesc : net->chans[c].desc;
       }
       y.n_max = net->chans[A.in[0]].cap;
       y.ctr = net->d_ctr;
@@ -825,6 +870,8 @@ df_status df_net_finalize(df_net* net) {
       y.plan = reinterpret_cast<DynPlanHdr*>(base + q.plan.off);
       y.masks = reinterpret_cast<uint32_t*>(base + q.masks.off);
       y.rank = reinterpret_cast<uint32_t*>(base + q.rank.off);
+      for (int p = 0; p < y.np; ++p)
+        if (y.is_out[p]) add_spill(op, poly ? A.out[p - 1] : A.out[0], &y.plan->base[p]);
       net->program.push_back(op);
     } else if (is_dpd_like(A.kind)) {
       bool ok = (int)group.size() < 1024;
@@ -843,13 +890,14 @@ df_status df_net_finalize(df_net* net) {
       };
       fit(c.in.tok);
       for (int p = 0; p < c.n_out; ++p) {
-        c.out[p] = net->chans[A.out[p]].desc;
+        c.out[p] = net->chans[A.out[p]].wdesc;
         fit(c.out[p].tok);
       }
       c.unit = unit;
       c.ctr = net->d_ctr;
       c.eng = net->d_eng;
       c.plan = reinterpret_cast<CopyPlan*>(base + cp[copy_index[a]].off);
+      for (int p = 0; p < c.n_out; ++p) add_spill(op, A.out[p], &c.plan->wr0[p]);
       net->program.push_back(op);
     } else if (A.kind == DF_GAUSS5 || A.kind == DF_THRES || A.kind == DF_MED5) {
       Op op{};
@@ -859,13 +907,14 @@ df_status df_net_finalize(df_net* net) {
       m.n_in = (int)A.in.size();
       for (int i = 0; i < m.n_in; ++i) m.in[i] = net->chans[A.in[i]].desc;
       m.n_out = (int)A.out.size();
-      for (int p = 0; p < m.n_out; ++p) m.out[p] = net->chans[A.out[p]].desc;
+      for (int p = 0; p < m.n_out; ++p) m.out[p] = net->chans[A.out[p]].wdesc;
       m.W = A.img.width;
       m.H = A.img.height;
       m.thr = A.img.threshold;
       m.ctr = net->d_ctr;
       m.eng = net->d_eng;
       m.plan = reinterpret_cast<ImgPlan*>(base + ip[img_index[a]].off);
+      for (int p = 0; p < m.n_out; ++p) add_spill(op, A.out[p], &m.plan->wr0[p]);
       net->program.push_back(op);
     } else if (A.kind == DF_MD) {
       Op op{};
@@ -975,17 +1024,20 @@ df_status push_on(df_net* net, int32_t src_actor, const void* src, uint64_t n_to
     const df_status st = concurrent ? read_io_counters(net, A.out[p], true, &w, &r, s, pin)
                                     : read_counters(net, A.out[p], &w, &r, s, pin);
     if (st != DF_OK) return st;
+    if (net->chans[A.out[p]].eq1 && n_tokens % net->chans[A.out[p]].rate) return DF_EINVAL;
     if (net->chans[A.out[p]].cap - (w - r) < n_tokens) return DF_EFULL;
     wr[p] = w;
   }
   if (n_tokens) {
     for (size_t p = 0; p < A.out.size(); ++p) {
-      const ChanDesc& c = net->chans[A.out[p]].desc;
+      const ChanH& C = net->chans[A.out[p]];
+      const ChanDesc& c = C.wdesc;
       if (p > 0 && c.tok == net->chans[A.out[0]].desc.tok) {
-        // further broadcast copies come from the first channel (device to device)
+        // further broadcast copies come from the first channel (device to device;
+        // its reader view, whose Fig. 2 copy is already done)
         const ChanDesc& c0 = net->chans[A.out[0]].desc;
         for (uint64_t done = 0; done < n_tokens;) {
-          const uint64_t s0 = (wr[0] + done) % c0.cap, s1 = (wr[p] + done) % c.cap;
+          const uint64_t s0 = (wr[0] + done) % c0.cap, s1 = (wr[p] + done - c.wshift) % c.cap;
           const uint64_t run = std::min({n_tokens - done, c0.cap - s0, c.cap - s1});
           DF_CUDA(cudaMemcpyAsync(c.ring + s1 * c.tok, c0.ring + s0 * c0.tok, run * c.tok,
                                   cudaMemcpyDeviceToDevice, s));
@@ -995,6 +1047,10 @@ df_status push_on(df_net* net, int32_t src_actor, const void* src, uint64_t n_to
         const df_status st = ring_copy(net, c, wr[p], const_cast<void*>(src), n_tokens, true, s);
         if (st != DF_OK) return st;
       }
+      // Fig. 2: the token that landed in slot cap is copied to slot 0
+      if (c.wshift && (wr[p] - 1) / C.cap != (wr[p] + n_tokens - 1) / C.cap)
+        DF_CUDA(cudaMemcpyAsync(C.desc.ring, C.desc.ring + (uint64_t)C.cap * C.tok, C.tok,
+                                cudaMemcpyDeviceToDevice, s));
       DF_CUDA(launch_set_u64(net->d_ctr + 2 * A.out[p], wr[p] + n_tokens, s));
     }
     DF_CUDA(cudaStreamSynchronize(s));
@@ -1167,6 +1223,35 @@ df_status df_channel_counters(df_net* net, int32_t ch, uint64_t* produced, uint6
   return DF_OK;
 }
 
+df_status df_channel_info(df_net* net, int32_t ch, df_channel_info_t* out) {
+  if (!net || !out || ch < 0 || ch >= (int)net->chans.size()) return DF_EINVAL;
+  const ChanH& C = net->chans[ch];
+  df_channel_info_t i{};
+  i.capacity = C.cap;
+  i.slots = C.slots();
+  i.buffer_bytes = C.slots() * C.tok;
+  i.token_bytes = C.tok;
+  i.rate = C.rate;
+  i.initial_tokens = C.init;
+  i.layout = C.eq1 ? DF_LAYOUT_EQ1 : DF_LAYOUT_RING;
+  *out = i;
+  return DF_OK;
+}
+
+df_status df_channel_peek_slots(df_net* net, int32_t ch, uint64_t first_slot, uint64_t n_slots,
+                                void* dst) {
+  if (!net || ch < 0 || ch >= (int)net->chans.size() || (!dst && n_slots)) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  const ChanH& C = net->chans[ch];
+  if (first_slot > C.slots() || n_slots > C.slots() - first_slot) return DF_EINVAL;
+  if (!n_slots) return DF_OK;
+  DeviceGuard g(net->device);
+  DF_CUDA(cudaMemcpyAsync(dst, C.desc.ring + first_slot * C.tok, n_slots * C.tok, cudaMemcpyDeviceToHost,
+                          net->stream));
+  DF_CUDA(cudaStreamSynchronize(net->stream));
+  return DF_OK;
+}
+
 df_status df_set_wait_limit(df_net* net, int64_t limit_ns) {
   if (!net || limit_ns <= 0) return DF_EINVAL;
   net->wait_limit_ns = limit_ns;
@@ -1285,6 +1370,7 @@ df_status df_autotune(df_net* net, uint64_t* n_firings) {
         st = DF_ENOTSUP;
       }
     }
+    for (const SpillArgs& sp : op.spills) DF_CUDA(launch_spill(sp, s));
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

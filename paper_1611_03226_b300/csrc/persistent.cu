@@ -109,6 +109,10 @@ __global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp*
         if (lead && threadIdx.x == 0) img_plan_dev(a);
         if (!grid_barrier(eng, nb, limit_ns)) return;
         img_body_dev(a, g, reinterpret_cast<uint8_t*>(smem));
+      } else if (op.kind == kPersistSpill) {
+        // the writer op before this one ended with a barrier: its tokens are in place
+        const SpillArgs* sp = static_cast<const SpillArgs*>(op.args);
+        for (int i = 0; i < op.n; ++i) spill_dev(sp[i], g);
       } else if (op.kind == kPersistMd) {
         const MdArgs& a = *static_cast<const MdArgs*>(op.args);
         if (lead) md_plan_dev(a);

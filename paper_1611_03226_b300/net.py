@@ -100,6 +100,10 @@ class Net:
 
     def connect(self, src, src_port, dst, dst_port, token_bytes, rate, capacity, initial=0,
                 initial_data=None):
+        """capacity="eq1" (DF_CAPACITY_EQ1) gives the paper's layout: Eq. 1 sizes the
+        buffer and a delay channel follows the access pattern of Fig. 2."""
+        if capacity == "eq1":
+            capacity = L.DF_CAPACITY_EQ1
         ch = C.c_int32()
         ptr = None
         if initial_data is not None:
@@ -174,6 +178,25 @@ class Net:
         if isinstance(out, np.ndarray):
             return out[: n.value * tok].view(dtype)
         return out, n.value
+
+    def channel_info(self, ch):
+        """Layout and size of a channel: dict of capacity (most unread tokens), slots,
+        buffer_bytes, token_bytes, rate, initial_tokens and layout ("ring" or "eq1")."""
+        i = L.ChannelInfo()
+        L.check(L.lib.df_channel_info(self.h, ch, C.byref(i)), "df_channel_info")
+        d = {k: getattr(i, k) for k, _ in L.ChannelInfo._fields_}
+        d["layout"] = "eq1" if i.layout == L.DF_LAYOUT_EQ1 else "ring"
+        return d
+
+    def peek_slots(self, ch, first=0, n=None):
+        """Raw buffer slots of a channel (uint8 array of n slots x token bytes)."""
+        info = self.channel_info(ch)
+        if n is None:
+            n = info["slots"] - first
+        out = np.empty(n * info["token_bytes"], np.uint8)
+        L.check(L.lib.df_channel_peek_slots(self.h, ch, first, n, C.c_void_p(out.ctypes.data)),
+                "df_channel_peek_slots")
+        return out.reshape(n, info["token_bytes"])
 
     def counters(self, ch):
         p, c, o = C.c_uint64(), C.c_uint64(), C.c_uint64()

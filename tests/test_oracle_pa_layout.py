@@ -1,6 +1,9 @@
 """Pins for the power-amplifier model and for Eq. 1 / Fig. 2."""
+import copy
 import json
 import os
+
+import pytest
 
 import numpy as np
 
@@ -53,3 +56,36 @@ def test_triple_buffer_is_a_fifo():
             nxt += r
             got += tb.read()
         assert got == ["D"] + list(range(9 * r - 1))
+
+
+def _orders_deliver_fifo(make, r, bound, depth):
+    """Depth-first over every order of window writes and reads in which a write
+    is allowed iff unread + r <= bound and a read iff r tokens are unread; True
+    iff every read returns the next r tokens of the stream."""
+    def dfs(buf, nxt_w, nxt_r, d):
+        if d == 0:
+            return True
+        ok = True
+        if buf.unread() + r <= bound:
+            b = copy.deepcopy(buf)
+            b.write(list(range(nxt_w, nxt_w + r)))
+            ok = ok and dfs(b, nxt_w + r, nxt_r, d - 1)
+        if ok and buf.unread() >= r:
+            b = copy.deepcopy(buf)
+            got = b.read()
+            ok = got == list(range(nxt_r, nxt_r + r)) and dfs(b, nxt_w, nxt_r + r, d - 1)
+        return ok
+    buf = make()
+    first_read = -1 if isinstance(buf, PL.TripleBuffer) else 0   # the delay token is token -1
+    return dfs(buf, 0, first_read, depth)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_eq1_unread_capacity_is_the_exact_bound(r):
+    """The reading of Fig. 2: a delay buffer of 3r + 1 slots holds at most 3r
+    unread tokens, a double buffer 2r; one more window breaks FIFO order."""
+    for make, delay in ((lambda: PL.TripleBuffer(r, -1), True), (lambda: PL.DoubleBuffer(r), False)):
+        cap = PL.eq1_unread_capacity(r, delay)
+        assert cap + (1 if delay else 0) == PL.eq1_capacity_tokens(r, delay)
+        assert _orders_deliver_fifo(make, r, cap, 12)
+        assert not _orders_deliver_fifo(make, r, cap + r, 12)
