@@ -527,6 +527,30 @@ def bench_md_paper(args, P, torch, pk):
         if i >= args.warmup:
             st_s.append(dt)
     net.close()
+    # the paper's own buffers (Sec. 3.2): Eq. 1 sizes every channel (8-frame
+    # double buffers, a 13-slot delay buffer with the Fig. 2 access pattern),
+    # so the host threads push one window of 4 frames at a time
+    T1 = min(T, 1024)
+    net = P.Net(stream=torch.cuda.current_stream().cuda_stream)
+    src, g, t, m, snk = (net.add_source(), net.add_gauss5(W, H), net.add_thres(W, H, thr),
+                         net.add_med5(W, H), net.add_sink())
+    chans = [net.connect(src, 0, g, 0, fb, rate, "eq1"), net.connect(g, 0, t, 0, fb, rate, "eq1"),
+             net.connect(g, 1, t, 1, fb, rate, "eq1", 1), net.connect(t, 0, m, 0, fb, rate, "eq1"),
+             net.connect(m, 0, snk, 0, fb, rate, "eq1")]
+    net.finalize()
+    eq1_bytes = sum(net.channel_info(c)["buffer_bytes"] for c in chans)
+    pop8 = torch.empty((2 * rate, H, W), dtype=torch.uint8).pin_memory()
+    st_q = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got, n_steps_eq1 = stream(net, {src: [host[j:j + rate] for j in range(0, T1, rate)]},
+                                  {snk: (2 * rate, pop8)}, flags=L.DF_RUN_GRAPH)
+        dt = time.perf_counter() - t0
+        assert got[snk] == T1
+        if i >= args.warmup:
+            st_q.append(dt)
+    net.close()
     # oracle on a bounded sample (64 frames)
     from oracle import motion_paper as MP
     ns = 64 if not args.quick else 16
@@ -544,6 +568,11 @@ def bench_md_paper(args, P, torch, pk):
             "e2e_streamed": {"value": frames_done / statistics.mean(st_s), "unit": "frames/s",
                              "note": "producer and consumer host threads beside the running steps "
                                      "(DF_IO_CONCURRENT), 256-frame channels, 64-frame chunks"},
+            "e2e_streamed_eq1": {"value": T1 / statistics.mean(st_q), "unit": "frames/s", "frames": T1,
+                                 "steps": n_steps_eq1, "buffer_bytes": eq1_bytes,
+                                 "paper_table1_MB": 3.46,
+                                 "note": "as e2e_streamed, but every channel sized by Eq. 1 (the paper's "
+                                         "layout, Fig. 2 delay buffer): 4-frame pushes, 8-frame pops"},
             "cpu_baseline": {"value": ns / cpu_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
                              "sample": f"first {ns} frames, numpy single thread"},
             "paper_table3_context": {"i7_gpu_fps": 6063, "carrizo_gpu_fps": 4614,
