@@ -516,12 +516,21 @@ def bench_md_paper(args, P, torch, pk):
     net.connect(m, 0, snk, 0, fb, rate, cap_s)
     net.finalize()
     pop_buf = torch.empty((chunk, H, W), dtype=torch.uint8).pin_memory()
-    st_s = []
+    st_py, st_s = [], []
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         got, _ = stream(net, {src: [host[j:j + chunk] for j in range(0, T, chunk)]},
                         {snk: (chunk, pop_buf)}, flags=L.DF_RUN_GRAPH)
+        dt = time.perf_counter() - t0
+        assert got[snk] == frames_done
+        if i >= args.warmup:
+            st_py.append(dt)
+    # the same with the native runner (C++ threads, df_stream)
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got, _ = net.stream({src: (host, chunk)}, {snk: (out_h, chunk)}, L.DF_RUN_GRAPH)
         dt = time.perf_counter() - t0
         assert got[snk] == frames_done
         if i >= args.warmup:
@@ -539,13 +548,11 @@ def bench_md_paper(args, P, torch, pk):
              net.connect(m, 0, snk, 0, fb, rate, "eq1")]
     net.finalize()
     eq1_bytes = sum(net.channel_info(c)["buffer_bytes"] for c in chans)
-    pop8 = torch.empty((2 * rate, H, W), dtype=torch.uint8).pin_memory()
     st_q = []
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        got, n_steps_eq1 = stream(net, {src: [host[j:j + rate] for j in range(0, T1, rate)]},
-                                  {snk: (2 * rate, pop8)}, flags=L.DF_RUN_GRAPH)
+        got, n_steps_eq1 = net.stream({src: (host[:T1], rate)}, {snk: (out_h[:T1], 2 * rate)}, L.DF_RUN_GRAPH)
         dt = time.perf_counter() - t0
         assert got[snk] == T1
         if i >= args.warmup:
@@ -566,13 +573,16 @@ def bench_md_paper(args, P, torch, pk):
             "e2e": {"value": frames_done / statistics.mean(e2e), "unit": "frames/s",
                     "h2d_bytes_per_step": T * fb, "d2h_bytes_per_step": frames_done * fb},
             "e2e_streamed": {"value": frames_done / statistics.mean(st_s), "unit": "frames/s",
-                             "note": "producer and consumer host threads beside the running steps "
-                                     "(DF_IO_CONCURRENT), 256-frame channels, 64-frame chunks"},
+                             "python_threads_value": frames_done / statistics.mean(st_py),
+                             "note": "native producer and consumer threads (df_stream) beside the running "
+                                     "steps (DF_IO_CONCURRENT), 256-frame channels, 64-frame chunks; "
+                                     "python_threads_value: the same with Python threads"},
             "e2e_streamed_eq1": {"value": T1 / statistics.mean(st_q), "unit": "frames/s", "frames": T1,
                                  "steps": n_steps_eq1, "buffer_bytes": eq1_bytes,
                                  "paper_table1_MB": 3.46,
-                                 "note": "as e2e_streamed, but every channel sized by Eq. 1 (the paper's "
-                                         "layout, Fig. 2 delay buffer): 4-frame pushes, 8-frame pops"},
+                                 "note": "native runner as e2e_streamed, but every channel sized by Eq. 1 "
+                                         "(the paper's layout, Fig. 2 delay buffer): 4-frame pushes, "
+                                         "8-frame pops"},
             "cpu_baseline": {"value": ns / cpu_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
                              "sample": f"first {ns} frames, numpy single thread"},
             "paper_table3_context": {"i7_gpu_fps": 6063, "carrizo_gpu_fps": 4614,

@@ -226,6 +226,36 @@ df_status df_push_ex(df_net *net, int32_t src_actor, const void *src, uint64_t n
 df_status df_pop_ex(df_net *net, int32_t sink_actor, void *dst, uint64_t max_tokens,
                     uint32_t flags, uint64_t *n_popped);
 
+/* Native runner of the paper's host actors (Sec. 3.3: every actor an OS
+ * thread, a read that lacks tokens blocks until they arrive).  One host
+ * thread per feed pushes its tokens in batches of `batch` (a batch that does
+ * not fit is retried once a step or a pop has freed space), one thread per
+ * drain pops up to `batch` tokens at a time into consecutive places of
+ * `data`, and the calling thread runs the GPU actors one step at a time
+ * (df_run_ex with run_flags, which must not contain DF_RUN_ASYNC).  All I/O
+ * uses DF_IO_CONCURRENT, so its copies overlap the steps.  The run ends when
+ * every feed is pushed, a step fires nothing, every drained sink's channel is
+ * empty and one more step fires nothing; drains[i].n_popped then holds the
+ * tokens popped (a drain also stops when max_tokens are in).  When nothing
+ * moves (no firing, push or pop) for idle_limit_ns (<= 0: 2 s) the run stops
+ * with DF_EDEADLOCK, e.g. when an undrained sink is full.  Feed data may be
+ * host (pinned for full speed) or device memory, as for df_push. */
+typedef struct {
+    int32_t source;          /* DF_SOURCE actor */
+    const void *data;        /* n_tokens tokens */
+    uint64_t n_tokens;
+    uint64_t batch;          /* tokens per push (a multiple of r for Eq. 1 channels) */
+} df_feed;
+typedef struct {
+    int32_t sink;            /* DF_SINK actor */
+    void *data;              /* room for max_tokens tokens */
+    uint64_t max_tokens;
+    uint64_t batch;          /* tokens per pop, at most */
+    uint64_t n_popped;       /* out */
+} df_drain;
+df_status df_stream(df_net *net, const df_feed *feeds, int32_t n_feeds, df_drain *drains,
+                    int32_t n_drains, uint32_t run_flags, int64_t idle_limit_ns, uint64_t *n_steps);
+
 /* Counters of channel `ch`: tokens produced (excluding initial tokens),
  * consumed, and currently held.  produced + initial == consumed + occupancy. */
 df_status df_channel_counters(df_net *net, int32_t ch, uint64_t *produced, uint64_t *consumed,

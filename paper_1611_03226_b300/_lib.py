@@ -43,6 +43,16 @@ class ChannelInfo(C.Structure):
                 ("layout", C.c_int32)]
 
 
+class Feed(C.Structure):
+    _fields_ = [("source", C.c_int32), ("data", C.c_void_p), ("n_tokens", C.c_uint64),
+                ("batch", C.c_uint64)]
+
+
+class Drain(C.Structure):
+    _fields_ = [("sink", C.c_int32), ("data", C.c_void_p), ("max_tokens", C.c_uint64),
+                ("batch", C.c_uint64), ("n_popped", C.c_uint64)]
+
+
 class DfError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -67,6 +77,8 @@ _PROTOS = {
     "df_push_ex": (C.c_int32, [_P, C.c_int32, _P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
     "df_pop_ex": (C.c_int32, [_P, C.c_int32, _P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
     "df_channel_info": (C.c_int32, [_P, C.c_int32, C.POINTER(ChannelInfo)]),
+    "df_stream": (C.c_int32, [_P, C.POINTER(Feed), C.c_int32, C.POINTER(Drain), C.c_int32, C.c_uint32,
+                              C.c_int64, C.POINTER(C.c_uint64)]),
     "df_channel_peek_slots": (C.c_int32, [_P, C.c_int32, C.c_uint64, C.c_uint64, C.c_void_p]),
     "df_channel_counters": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint64),
                                         C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),

@@ -47,7 +47,7 @@ struct EngineDev {          // device-resident engine state
   // step's counters before its bodies move the data, so a push or pop that
   // runs beside the steps takes the other side's counter from here.
   uint64_t* ctr;
-  uint64_t* pub;            // null until concurrent I/O is used
+  uint64_t* pub;            // mapped host memory: the host reads it without a copy
   uint32_t n_words;         // 2 per channel
 };
 

@@ -11,12 +11,16 @@
 // gathers and scatters are all device kernels reading the device counters.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -78,7 +82,11 @@ struct df_net {
   uint8_t* arena = nullptr;
   size_t arena_bytes = 0;
   uint64_t* d_ctr = nullptr;
-  uint64_t* d_pub = nullptr;          // counters published after each step (concurrent I/O)
+  uint64_t* d_pub = nullptr;          // counters published after each step (concurrent I/O),
+  uint64_t* h_pub = nullptr;          // in mapped pinned host memory: d_pub is its device address
+  // the counters only the host moves (wr of a source's channels, rd of a
+  // sink's), kept by the pushing / popping thread after each of its calls
+  std::vector<uint64_t> host_ctr;
   std::atomic<bool> io_used{false};   // a concurrent push or pop happened: publish every step
   EngineDev* d_eng = nullptr;
   std::vector<DpdArgs> dpd_host;      // one per predistorter actor (by dpd index)
@@ -86,6 +94,8 @@ struct df_net {
   DpdArgs* d_dpd = nullptr;           // device copy of dpd_host
   std::vector<Op> program;
   uint64_t* h_pin = nullptr;          // pinned staging (counters, status)
+  uint64_t fired_seen = 0;            // fired_total as last read after all queued work
+  bool fired_known = false;           // false after asynchronous runs and the autotuner
   // concurrent host I/O (DF_IO_CONCURRENT): [0] pushes, [1] pops, each on a
   // stream of its own, created on first use (counters are staged in pinned
   // memory of the calling thread, so several sources or sinks can be served
@@ -241,12 +251,25 @@ df_status validate_actor(const df_net* net, int a) {
   }
 }
 
-df_status fail_if_device_error(df_net* net) {
+// The engine word after all queued work, with one copy into the pinned
+// staging and one wait: the firing total and the device status.
+static_assert(offsetof(EngineDev, fired_total) == 0 && offsetof(EngineDev, status) == 16,
+              "engine word layout");
+df_status read_engine(df_net* net, uint64_t* total, int32_t* status) {
+  DF_CUDA(cudaMemcpyAsync(net->h_pin, net->d_eng, 24, cudaMemcpyDeviceToHost, net->stream));
   DF_CUDA(cudaStreamSynchronize(net->stream));
-  DF_CUDA(cudaMemcpy(net->h_pin, &net->d_eng->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  *total = net->h_pin[0];
+  std::memcpy(status, reinterpret_cast<const uint8_t*>(net->h_pin) + 16, sizeof(int32_t));
+  net->fired_seen = *total;
+  net->fired_known = true;
+  return DF_OK;
+}
+
+df_status fail_if_device_error(df_net* net) {
+  uint64_t total;
   int32_t st;
-  std::memcpy(&st, net->h_pin, sizeof(st));
-  return st;
+  const df_status e = read_engine(net, &total, &st);
+  return e != DF_OK ? e : st;
 }
 
 df_status read_counters(df_net* net, int32_t ch, uint64_t* wr, uint64_t* rd,
@@ -518,6 +541,7 @@ void df_net_destroy(df_net* net) {
   if (net->persist_mem) cudaFree(net->persist_mem);
   if (net->arena) cudaFree(net->arena);
   if (net->h_pin) cudaFreeHost(net->h_pin);
+  if (net->h_pub) cudaFreeHost(net->h_pub);
   for (int i = 0; i < 2; ++i) {
     if (net->io_stream[i]) {
       cudaStreamSynchronize(net->io_stream[i]);
@@ -647,7 +671,6 @@ df_status df_net_finalize(df_net* net) {
   for (size_t c = 0; c < net->chans.size(); ++c)
     ring[c] = take((size_t)net->chans[c].slots() * net->chans[c].tok);
   const Piece p_ctr = take(2 * sizeof(uint64_t) * std::max<size_t>(1, net->chans.size()));
-  const Piece p_pub = take(2 * sizeof(uint64_t) * std::max<size_t>(1, net->chans.size()));
   const Piece p_eng = take(sizeof(EngineDev));
   struct DpdPieces { Piece plan, masks, rank, act, cnt, hist, parity, h; };
   struct MdPieces { Piece plan, counts, tot, off; };
@@ -744,9 +767,14 @@ df_status df_net_finalize(df_net* net) {
   }
   if (!ctr0.empty()) {
     DF_CUDA(cudaMemcpyAsync(net->d_ctr, ctr0.data(), ctr0.size() * 8, cudaMemcpyHostToDevice, s));
-    DF_CUDA(cudaMemcpyAsync(base + p_pub.off, ctr0.data(), ctr0.size() * 8, cudaMemcpyHostToDevice, s));
   }
-  net->d_pub = reinterpret_cast<uint64_t*>(base + p_pub.off);
+  // published counters in mapped host memory: a concurrent push or pop reads
+  // them with a plain load, no copy and no wait
+  DF_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&net->h_pub),
+                        2 * sizeof(uint64_t) * std::max<size_t>(1, net->chans.size()), cudaHostAllocMapped));
+  if (!ctr0.empty()) std::memcpy(net->h_pub, ctr0.data(), ctr0.size() * 8);
+  DF_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&net->d_pub), net->h_pub, 0));
+  net->host_ctr = ctr0;
   {
     // engine word: where the counters and their published copy are
     uint64_t* ptrs[2] = {net->d_ctr, net->d_pub};
@@ -972,15 +1000,13 @@ df_status df_net_finalize(df_net* net) {
 namespace {
 
 // Counters of a channel for a push (writer) or pop (reader) beside running
-// steps: the caller's own counter from the live array, the other side's from
-// the copy published after the last finished step.
-df_status read_io_counters(df_net* net, int32_t ch, bool writer, uint64_t* wr, uint64_t* rd,
-                           cudaStream_t s, uint64_t* pin) {
-  DF_CUDA(cudaMemcpyAsync(pin, net->d_ctr + 2 * ch, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaMemcpyAsync(pin + 2, net->d_pub + 2 * ch, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaStreamSynchronize(s));
-  *wr = writer ? pin[0] : pin[2];
-  *rd = writer ? pin[3] : pin[1];
+// steps: the caller's own counter from the host's record (only the host moves
+// it), the other side's from the copy published after the last finished step
+// (mapped host memory, read with a plain load).
+df_status read_io_counters(df_net* net, int32_t ch, bool writer, uint64_t* wr, uint64_t* rd) {
+  const volatile uint64_t* pub = net->h_pub;
+  *wr = writer ? net->host_ctr[2 * ch] : pub[2 * ch];
+  *rd = writer ? pub[2 * ch + 1] : net->host_ctr[2 * ch + 1];
   return DF_OK;
 }
 
@@ -1021,7 +1047,7 @@ df_status push_on(df_net* net, int32_t src_actor, const void* src, uint64_t n_to
   std::vector<uint64_t> wr(A.out.size());
   for (size_t p = 0; p < A.out.size(); ++p) {
     uint64_t w, r;
-    const df_status st = concurrent ? read_io_counters(net, A.out[p], true, &w, &r, s, pin)
+    const df_status st = concurrent ? read_io_counters(net, A.out[p], true, &w, &r)
                                     : read_counters(net, A.out[p], &w, &r, s, pin);
     if (st != DF_OK) return st;
     if (net->chans[A.out[p]].eq1 && n_tokens % net->chans[A.out[p]].rate) return DF_EINVAL;
@@ -1054,6 +1080,7 @@ df_status push_on(df_net* net, int32_t src_actor, const void* src, uint64_t n_to
       DF_CUDA(launch_set_u64(net->d_ctr + 2 * A.out[p], wr[p] + n_tokens, s));
     }
     DF_CUDA(cudaStreamSynchronize(s));
+    for (size_t p = 0; p < A.out.size(); ++p) net->host_ctr[2 * A.out[p]] = wr[p] + n_tokens;
   }
   if (n_pushed) *n_pushed = n_tokens;
   return DF_OK;
@@ -1071,7 +1098,7 @@ df_status pop_on(df_net* net, int32_t sink_actor, void* dst, uint64_t max_tokens
   DeviceGuard g(net->device);
   const int32_t ch = A.in[0];
   uint64_t w, r;
-  df_status st = s != net->stream ? read_io_counters(net, ch, false, &w, &r, s, pin)
+  df_status st = s != net->stream ? read_io_counters(net, ch, false, &w, &r)
                                   : read_counters(net, ch, &w, &r, s, pin);
   if (st != DF_OK) return st;
   const uint64_t n = std::min(max_tokens, w - r);
@@ -1080,6 +1107,7 @@ df_status pop_on(df_net* net, int32_t sink_actor, void* dst, uint64_t max_tokens
     if (st != DF_OK) return st;
     DF_CUDA(launch_set_u64(net->d_ctr + 2 * ch + 1, r + n, s));
     DF_CUDA(cudaStreamSynchronize(s));
+    net->host_ctr[2 * ch + 1] = r + n;
   }
   if (n_popped) *n_popped = n;
   return DF_OK;
@@ -1113,10 +1141,17 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
   const bool no_batch = flags & DF_RUN_NO_BATCH;
   uint64_t before = 0;
   if (!(flags & DF_RUN_ASYNC)) {
-    DF_CUDA(cudaStreamSynchronize(net->stream));
-    DF_CUDA(cudaMemcpy(&before, &net->d_eng->fired_total, 8, cudaMemcpyDeviceToHost));
+    if (!net->fired_known) {
+      int32_t dst;
+      const df_status e = read_engine(net, &before, &dst);
+      if (e != DF_OK) return e;
+    }
+    before = net->fired_seen;
+    net->fired_known = false;         // until the run's own read at its end
   } else if (n_steps < 0) {
     return DF_EINVAL;
+  } else {
+    net->fired_known = false;
   }
   if (flags & DF_RUN_PERSISTENT) {
     df_status st = build_persistent(net);
@@ -1166,13 +1201,12 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
     if (i == kMaxSteps) return DF_EDEADLOCK;
   }
   if (flags & DF_RUN_ASYNC) return DF_OK;
-  const df_status st = fail_if_device_error(net);
-  if (st != DF_OK) return st;
-  if (n_firings) {
-    uint64_t after = 0;
-    DF_CUDA(cudaMemcpy(&after, &net->d_eng->fired_total, 8, cudaMemcpyDeviceToHost));
-    *n_firings = after - before;
-  }
+  uint64_t after = 0;
+  int32_t dst = DF_OK;
+  const df_status e = read_engine(net, &after, &dst);
+  if (e != DF_OK) return e;
+  if (dst != DF_OK) return dst;
+  if (n_firings) *n_firings = after - before;
   return DF_OK;
 }
 
@@ -1184,10 +1218,12 @@ df_status df_sync(df_net* net, uint64_t* total_firings) {
   if (!net) return DF_EINVAL;
   if (!net->finalized) return DF_ESTATE;
   DeviceGuard g(net->device);
-  const df_status st = fail_if_device_error(net);
-  if (st != DF_OK) return st;
-  if (total_firings) DF_CUDA(cudaMemcpy(total_firings, &net->d_eng->fired_total, 8,
-                                        cudaMemcpyDeviceToHost));
+  uint64_t total = 0;
+  int32_t dst = DF_OK;
+  const df_status e = read_engine(net, &total, &dst);
+  if (e != DF_OK) return e;
+  if (dst != DF_OK) return dst;
+  if (total_firings) *total_firings = total;
   return DF_OK;
 }
 
@@ -1207,6 +1243,184 @@ df_status df_pop_ex(df_net* net, int32_t sink_actor, void* dst, uint64_t max_tok
   const df_status st = io_channel(net, 1, &s, &pin);
   if (st != DF_OK) return st;
   return pop_on(net, sink_actor, dst, max_tokens, n_popped, s, pin);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Events of a streamed run: every push, pop and firing step bumps the
+// generation, and a thread with nothing to do sleeps until it moves (or a
+// short timeout passes, as a copy on another stream may have freed space).
+struct StreamHub {
+  std::mutex mu;
+  std::condition_variable cv;
+  uint64_t gen = 0;
+  std::atomic<int32_t> err{DF_OK};
+  std::atomic<bool> finished{false};
+  std::atomic<int> producers_left{0};
+  void bump() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      ++gen;
+    }
+    cv.notify_all();
+  }
+  uint64_t now() {
+    std::lock_guard<std::mutex> lk(mu);
+    return gen;
+  }
+  void wait(uint64_t seen) {
+    std::unique_lock<std::mutex> lk(mu);
+    cv.wait_for(lk, std::chrono::microseconds(200),
+                [&] { return gen != seen || err.load() != DF_OK || finished.load(); });
+  }
+  void fail(int32_t st) {
+    int32_t ok = DF_OK;
+    err.compare_exchange_strong(ok, st);
+    bump();
+  }
+};
+
+uint64_t endpoint_token_bytes(const df_net* net, int32_t actor, int kind) {
+  if (actor < 0 || actor >= (int)net->actors.size()) return 0;
+  const ActorH& A = net->actors[actor];
+  if (A.kind != kind) return 0;
+  const std::vector<int32_t>& ports = kind == DF_SOURCE ? A.out : A.in;
+  return ports.empty() ? 0 : net->chans[ports[0]].tok;
+}
+
+void stream_produce(df_net* net, const df_feed& f, uint64_t tok, StreamHub& hub) {
+  const uint8_t* src = static_cast<const uint8_t*>(f.data);
+  for (uint64_t done = 0; done < f.n_tokens && hub.err.load() == DF_OK;) {
+    const uint64_t n = std::min(f.batch, f.n_tokens - done);
+    const uint64_t seen = hub.now();
+    const df_status st = df_push_ex(net, f.source, src + done * tok, n, DF_IO_CONCURRENT, nullptr);
+    if (st == DF_OK) {
+      done += n;
+      hub.bump();
+    } else if (st == DF_EFULL) {
+      hub.wait(seen);
+    } else {
+      hub.fail(st);
+    }
+  }
+  hub.producers_left.fetch_sub(1);
+  hub.bump();
+}
+
+void stream_consume(df_net* net, df_drain& d, uint64_t tok, StreamHub& hub) {
+  uint8_t* dst = static_cast<uint8_t*>(d.data);
+  uint64_t got = 0;
+  while (hub.err.load() == DF_OK && got < d.max_tokens) {
+    const uint64_t seen = hub.now();
+    const bool last = hub.finished.load();     // read before the pop: nothing arrives after it
+    uint64_t n = 0;
+    const df_status st = df_pop_ex(net, d.sink, dst + got * tok, std::min(d.batch, d.max_tokens - got),
+                                   DF_IO_CONCURRENT, &n);
+    if (st != DF_OK) {
+      hub.fail(st);
+      break;
+    }
+    if (n) {
+      got += n;
+      hub.bump();
+    } else if (last) {
+      break;
+    } else {
+      hub.wait(seen);
+    }
+  }
+  d.n_popped = got;
+}
+
+}  // namespace
+
+extern "C" {
+
+df_status df_stream(df_net* net, const df_feed* feeds, int32_t n_feeds, df_drain* drains, int32_t n_drains,
+                    uint32_t run_flags, int64_t idle_limit_ns, uint64_t* n_steps) {
+  if (!net || n_feeds < 0 || n_drains < 0 || (n_feeds && !feeds) || (n_drains && !drains)) return DF_EINVAL;
+  if (!net->finalized) return DF_ESTATE;
+  if (run_flags & DF_RUN_ASYNC) return DF_EINVAL;
+  std::vector<uint64_t> ftok(n_feeds), dtok(n_drains);
+  for (int i = 0; i < n_feeds; ++i) {
+    ftok[i] = endpoint_token_bytes(net, feeds[i].source, DF_SOURCE);
+    if (!ftok[i] || !feeds[i].batch || (!feeds[i].data && feeds[i].n_tokens)) return DF_EINVAL;
+  }
+  for (int i = 0; i < n_drains; ++i) {
+    dtok[i] = endpoint_token_bytes(net, drains[i].sink, DF_SINK);
+    if (!dtok[i] || !drains[i].batch || (!drains[i].data && drains[i].max_tokens)) return DF_EINVAL;
+  }
+  if (idle_limit_ns <= 0) idle_limit_ns = 2000000000LL;
+  net->io_used = true;                       // every step publishes its counters
+  StreamHub hub;
+  hub.producers_left = n_feeds;
+  std::vector<std::thread> threads;
+  for (int i = 0; i < n_feeds; ++i)
+    threads.emplace_back(stream_produce, net, std::cref(feeds[i]), ftok[i], std::ref(hub));
+  for (int i = 0; i < n_drains; ++i)
+    threads.emplace_back(stream_consume, net, std::ref(drains[i]), dtok[i], std::ref(hub));
+  // this thread runs the GPU actors: one step at a time, sleeping while
+  // nothing can fire; the run is over when the sources are exhausted, a step
+  // fired nothing, every drained sink is empty and one more step (after the
+  // pops that emptied them) fires nothing either
+  uint64_t steps = 0;
+  auto idle_since = std::chrono::steady_clock::now();
+  while (hub.err.load() == DF_OK) {
+    const uint64_t seen = hub.now();
+    uint64_t fired = 0;
+    const df_status st = df_run_ex(net, 1, run_flags, &fired);
+    ++steps;
+    if (st != DF_OK) {
+      hub.fail(st);
+      break;
+    }
+    if (fired) {
+      hub.bump();
+      idle_since = std::chrono::steady_clock::now();
+      continue;
+    }
+    if (hub.producers_left.load() == 0) {
+      bool empty = true;
+      for (int i = 0; i < n_drains && empty; ++i) {
+        uint64_t occ = 0;
+        const df_status cs = df_channel_counters(net, net->actors[drains[i].sink].in[0], nullptr, nullptr, &occ);
+        if (cs != DF_OK) {
+          hub.fail(cs);
+          break;
+        }
+        empty = occ == 0;
+      }
+      if (hub.err.load() != DF_OK) break;
+      if (empty) {
+        const df_status st2 = df_run_ex(net, 1, run_flags, &fired);
+        ++steps;
+        if (st2 != DF_OK) {
+          hub.fail(st2);
+          break;
+        }
+        if (!fired) break;
+        hub.bump();
+        continue;
+      }
+    }
+    if (hub.now() == seen) {
+      if (std::chrono::steady_clock::now() - idle_since > std::chrono::nanoseconds(idle_limit_ns)) {
+        hub.fail(DF_EDEADLOCK);              // nothing moved: a full undrained sink or a cycle
+        break;
+      }
+      hub.wait(seen);
+    } else {
+      idle_since = std::chrono::steady_clock::now();
+    }
+  }
+  hub.finished = true;
+  hub.bump();
+  for (std::thread& t : threads) t.join();
+  if (hub.err.load() != DF_OK) return hub.err.load();
+  if (n_steps) *n_steps = steps;
+  return DF_OK;
 }
 
 df_status df_channel_counters(df_net* net, int32_t ch, uint64_t* produced, uint64_t* consumed,

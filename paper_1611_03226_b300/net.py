@@ -179,6 +179,31 @@ class Net:
             return out[: n.value * tok].view(dtype)
         return out, n.value
 
+    def stream(self, feeds, drains, flags=0, idle_limit_s=0.0):
+        """Run to completion with the paper's host actors as native threads
+        (df_stream): feeds {source: (buffer of tokens, tokens per push)}, drains
+        {sink: (output buffer, tokens per pop)}.  Returns ({sink: tokens popped},
+        steps run)."""
+        fs = (L.Feed * max(1, len(feeds)))()
+        keep = []
+        for i, (src, (buf, batch)) in enumerate(feeds.items()):
+            addr, nbytes = _ptr(buf)
+            tok = self.chan_tok[self.actor_out[src][0]]
+            if nbytes % tok:
+                raise ValueError("feed is not a whole number of tokens")
+            fs[i] = L.Feed(src, addr, nbytes // tok, batch)
+            keep.append(buf)
+        ds = (L.Drain * max(1, len(drains)))()
+        for i, (snk, (buf, batch)) in enumerate(drains.items()):
+            addr, nbytes = _ptr(buf)
+            tok = self.chan_tok[self.actor_in[snk][0]]
+            ds[i] = L.Drain(snk, addr, nbytes // tok, batch, 0)
+            keep.append(buf)
+        steps = C.c_uint64()
+        L.check(L.lib.df_stream(self.h, fs, len(feeds), ds, len(drains), flags, int(idle_limit_s * 1e9),
+                                C.byref(steps)), "df_stream")
+        return {snk: ds[i].n_popped for i, snk in enumerate(drains)}, steps.value
+
     def channel_info(self, ch):
         """Layout and size of a channel: dict of capacity (most unread tokens), slots,
         buffer_bytes, token_bytes, rate, initial_tokens and layout ("ring" or "eq1")."""
