@@ -125,9 +125,10 @@ constexpr int kImgThreads = 256;
 constexpr int kImgMaxWidth = 2048;
 // shared memory of an image body CTA: two staging buffers of input rows
 // (band + 2-row halo each side) and, for the Gaussian, the vertical sums as
-// u16 with 2 clamped columns each side
+// u16 rows of W + 16 (8 leading elements hold the 2 clamped left columns, so
+// pixel 0 starts 16-byte aligned; the 2 clamped right columns follow pixel W-1)
 __host__ __device__ constexpr size_t img_smem_bytes(int W) {
-  return 2 * (size_t)(kImgBand + 4) * W + (size_t)kImgBand * (W + 4) * 2 + 16;
+  return 2 * (size_t)(kImgBand + 4) * W + (size_t)kImgBand * (W + 16) * 2 + 16;
 }
 
 // --------------------------------------------------- fused predistorter ----

@@ -155,19 +155,19 @@ __device__ __forceinline__ void stage_rows(const uint8_t* frame, uint8_t* s, int
 __device__ __forceinline__ void img_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void img_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Calls f(y, x) for every row y in [ya, yb) and 4-pixel group x = 0, 4, ..
-// of a W-pixel row, spread over the CTA's threads (flat index tid + k *
-// blockDim.x, advanced without a division per step).
+// Calls f(y, x) for every row y in [ya, yb) and 16-pixel unit x = 0, 16, ..
+// of a W-pixel row (W % 16 == 0), spread over the CTA's threads (flat index
+// tid + k * blockDim.x, advanced without a division per step).
 template <typename F>
-__device__ __forceinline__ void for_groups(int ya, int yb, int W, F&& f) {
-  const int q = W / 4;
+__device__ __forceinline__ void for_units(int ya, int yb, int W, F&& f) {
+  const int q = W / 16;
   const int n = (yb - ya) * q;
   if (n <= 0) return;
   int e = threadIdx.x;
   int y = ya + e / q, c = e % q;
   const int dy = (int)blockDim.x / q, dc = (int)blockDim.x % q;
   for (; e < n; e += blockDim.x) {
-    f(y, 4 * c);
+    f(y, 16 * c);
     y += dy;
     c += dc;
     if (c >= q) {
@@ -218,84 +218,130 @@ __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& 
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Gauss over bands of kImgBand rows.  Vertical sums of the 5 rows (weights
-// 1, 4, 6, 4, 1) go to shared memory as u16 (<= 16 * 255) with the edge
-// columns repeated twice on each side; the horizontal pass then weights 5
+// Weighted vertical sum (1, 4, 6, 4, 1) of five rows' 4-pixel words: pixels
+// 0 and 2 in the 16-bit lanes of lo, pixels 1 and 3 in those of hi (<= 16 * 255).
+__device__ __forceinline__ void vsum5(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e,
+                                      uint32_t& lo, uint32_t& hi) {
+  lo = __byte_perm(a, 0, 0x4240) + __byte_perm(e, 0, 0x4240) +
+       4u * (__byte_perm(b, 0, 0x4240) + __byte_perm(d, 0, 0x4240)) + 6u * __byte_perm(c, 0, 0x4240);
+  hi = __byte_perm(a, 0, 0x4341) + __byte_perm(e, 0, 0x4341) +
+       4u * (__byte_perm(b, 0, 0x4341) + __byte_perm(d, 0, 0x4341)) + 6u * __byte_perm(c, 0, 0x4341);
+}
+
+// Horizontal pass of 4 pixels from the vertical sums v[x-2] .. v[x+5] as four
+// u16 pairs: pairs (v_i, v_{i+2}) for the even pixels x, x+2 and the odd
+// pixels x+1, x+3; each 16-bit lane of the weighted sum stays below 65536.
+__device__ __forceinline__ uint32_t hsum5(uint32_t w01, uint32_t w23, uint32_t w45, uint32_t w67) {
+  const uint32_t s02 = __byte_perm(w01, w23, 0x5410), s13 = __byte_perm(w01, w23, 0x7632);
+  const uint32_t s24 = __byte_perm(w23, w45, 0x5410), s35 = __byte_perm(w23, w45, 0x7632);
+  const uint32_t s46 = __byte_perm(w45, w67, 0x5410), s57 = __byte_perm(w45, w67, 0x7632);
+  const uint32_t he = s02 + 4 * s13 + 6 * s24 + 4 * s35 + s46 + 0x00800080u;
+  const uint32_t ho = s13 + 4 * s24 + 6 * s35 + 4 * s46 + s57 + 0x00800080u;
+  return ((he >> 8) & 0x00ff00ffu) | (((ho >> 8) & 0x00ff00ffu) << 8);
+}
+
+// Vertical sums: u16 rows of kImgVPitch(W) elements, pixel x at index x + 8
+// (16-byte aligned for x % 16 == 0), clamped columns -2, -1 at 6, 7 and W, W+1
+// at W + 8, W + 9.
+__host__ __device__ constexpr int kImgVPitch(int W) { return W + 16; }
+
+// Gauss over bands of kImgBand rows, 16 pixels per thread and pass.  Vertical
+// sums of the 5 rows go to shared memory; the horizontal pass then weights 5
 // neighbouring sums, adds 128 and shifts right by 8.
 __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
-  // after the two staging buffers: vertical sums, u16, 2 clamped columns each side
   uint16_t* v = reinterpret_cast<uint16_t*>(smem + 2 * (size_t)(kImgBand + 4) * W);
-  const int vw = W + 4;                                             // u16 per vertical-sum row
+  const int vw = kImgVPitch(W);
   for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
     // vertical pass over the band's filtered rows (2 <= y < H-2)
     const int fa = max(y0, 2), fb = min(y1, H - 2);
-    for_groups(fa, fb, W, [&](int yr, int x) {
-      uint32_t lo = 0, hi = 0;                                      // pixels x, x+2 / x+1, x+3 in 16-bit lanes
-      const uint8_t* col = s + (size_t)(yr - y0) * W + x;           // row yr-2
-#pragma unroll
-      for (int dy = 0; dy < 5; ++dy) {
-        const uint32_t w = *reinterpret_cast<const uint32_t*>(col + dy * W);
-        const uint32_t k = dy == 2 ? 6u : (dy == 1 || dy == 3) ? 4u : 1u;
-        lo += k * (w & 0x00ff00ffu);
-        hi += k * ((w >> 8) & 0x00ff00ffu);
-      }
-      uint16_t* vr = v + (size_t)(yr - y0) * vw + 2;
-      const uint32_t p01 = __byte_perm(lo, hi, 0x5410), p23 = __byte_perm(lo, hi, 0x7632);
-      *reinterpret_cast<uint32_t*>(vr + x) = p01;                   // 4-byte aligned: vw, x even
-      *reinterpret_cast<uint32_t*>(vr + x + 2) = p23;
-      if (x == 0) vr[-1] = vr[-2] = (uint16_t)p01;                  // clamped columns -1, -2
-      if (x + 4 == W) vr[W] = vr[W + 1] = (uint16_t)(p23 >> 16);    // clamped columns W, W+1
+    for_units(fa, fb, W, [&](int yr, int x) {
+      const uint8_t* col = s + (yr - y0) * W + x;                   // row yr-2
+      const uint4 r0 = *reinterpret_cast<const uint4*>(col);
+      const uint4 r1 = *reinterpret_cast<const uint4*>(col + W);
+      const uint4 r2 = *reinterpret_cast<const uint4*>(col + 2 * W);
+      const uint4 r3 = *reinterpret_cast<const uint4*>(col + 3 * W);
+      const uint4 r4 = *reinterpret_cast<const uint4*>(col + 4 * W);
+      uint32_t lo[4], hi[4];
+      vsum5(r0.x, r1.x, r2.x, r3.x, r4.x, lo[0], hi[0]);
+      vsum5(r0.y, r1.y, r2.y, r3.y, r4.y, lo[1], hi[1]);
+      vsum5(r0.z, r1.z, r2.z, r3.z, r4.z, lo[2], hi[2]);
+      vsum5(r0.w, r1.w, r2.w, r3.w, r4.w, lo[3], hi[3]);
+      uint16_t* vr = v + (yr - y0) * vw + 8;
+      const uint4 p0 = make_uint4(__byte_perm(lo[0], hi[0], 0x5410), __byte_perm(lo[0], hi[0], 0x7632),
+                                  __byte_perm(lo[1], hi[1], 0x5410), __byte_perm(lo[1], hi[1], 0x7632));
+      const uint4 p1 = make_uint4(__byte_perm(lo[2], hi[2], 0x5410), __byte_perm(lo[2], hi[2], 0x7632),
+                                  __byte_perm(lo[3], hi[3], 0x5410), __byte_perm(lo[3], hi[3], 0x7632));
+      *reinterpret_cast<uint4*>(vr + x) = p0;
+      *reinterpret_cast<uint4*>(vr + x + 8) = p1;
+      if (x == 0) vr[-1] = vr[-2] = (uint16_t)p0.x;                 // clamped columns -1, -2
+      if (x + 16 == W) vr[W] = vr[W + 1] = (uint16_t)(p1.w >> 16);  // clamped columns W, W+1
     });
     __syncthreads();
-    // horizontal pass and the unfiltered rows; 4 pixels per thread
-    for_groups(y0, y1, W, [&](int y, int x) {
-      uint32_t out;
+    // horizontal pass and the unfiltered rows
+    for_units(y0, y1, W, [&](int y, int x) {
+      uint4 out;
       if (y < 2 || y >= H - 2) {
-        out = *reinterpret_cast<const uint32_t*>(s + (size_t)(y - y0 + 2) * W + x);
+        out = *reinterpret_cast<const uint4*>(s + (y - y0 + 2) * W + x);
       } else {
-        // v[x-2] .. v[x+5] as four u16 pairs (8-byte aligned: vw = W + 4, x % 4 == 0)
-        const uint16_t* vr = v + (size_t)(y - y0) * vw + x;
-        const uint2 q0 = *reinterpret_cast<const uint2*>(vr), q1 = *reinterpret_cast<const uint2*>(vr + 4);
-        const uint32_t w01 = q0.x, w23 = q0.y, w45 = q1.x, w67 = q1.y;
-        // pairs (v_i, v_{i+2}) for the even pixels x, x+2 and the odd pixels x+1, x+3;
-        // each 16-bit lane of the weighted sum stays below 65536 (16 * 16 * 255)
-        const uint32_t s02 = __byte_perm(w01, w23, 0x5410), s13 = __byte_perm(w01, w23, 0x7632);
-        const uint32_t s24 = __byte_perm(w23, w45, 0x5410), s35 = __byte_perm(w23, w45, 0x7632);
-        const uint32_t s46 = __byte_perm(w45, w67, 0x5410), s57 = __byte_perm(w45, w67, 0x7632);
-        const uint32_t he = s02 + 4 * s13 + 6 * s24 + 4 * s35 + s46 + 0x00800080u;
-        const uint32_t ho = s13 + 4 * s24 + 6 * s35 + 4 * s46 + s57 + 0x00800080u;
-        out = ((he >> 8) & 0x00ff00ffu) | (((ho >> 8) & 0x00ff00ffu) << 8);
+        // v[x-2] .. v[x+17] as ten u16 pairs
+        const uint16_t* vr = v + (y - y0) * vw + 8 + x;
+        const uint32_t w1 = *reinterpret_cast<const uint32_t*>(vr - 2);
+        const uint4 qa = *reinterpret_cast<const uint4*>(vr);
+        const uint4 qb = *reinterpret_cast<const uint4*>(vr + 8);
+        const uint32_t w10 = *reinterpret_cast<const uint32_t*>(vr + 16);
+        out.x = hsum5(w1, qa.x, qa.y, qa.z);
+        out.y = hsum5(qa.y, qa.z, qa.w, qb.x);
+        out.z = hsum5(qa.w, qb.x, qb.y, qb.z);
+        out.w = hsum5(qb.y, qb.z, qb.w, w10);
       }
-      for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint32_t*>(of[p] + (size_t)y * W + x) = out;
+      const size_t o = (size_t)y * W + x;
+      for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint4*>(of[p] + o) = out;
     });
   });
 }
 
-// Med over bands of kImgBand rows; 4 pixels per thread with bytewise min/max.
+// Any byte of w neither 0x00 nor 0xff: a nonzero word.
+__device__ __forceinline__ uint32_t nonbinary_bits(uint32_t w) { return (w ^ (w << 1)) & 0xfefefefeu; }
+
+// Med over bands of kImgBand rows, 16 pixels per thread.  Where a whole warp's
+// inputs hold only 0 and 255 (every motion map) the median is a bitwise
+// majority; otherwise the bytewise min/max network runs.
 __device__ inline void med_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
   for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
-    for_groups(y0, y1, W, [&](int y, int x) {
-      const uint8_t* row = s + (size_t)(y - y0 + 2) * W;
-      const uint32_t c = *reinterpret_cast<const uint32_t*>(row + x);
-      uint32_t out = c;
+    for_units(y0, y1, W, [&](int y, int x) {
+      const uint8_t* row = s + (y - y0 + 2) * W;
+      const uint4 c = *reinterpret_cast<const uint4*>(row + x);
+      uint4 out = c;
       if (y >= 1 && y < H - 1) {
-        const uint32_t up = *reinterpret_cast<const uint32_t*>(row - W + x);
-        const uint32_t dn = *reinterpret_cast<const uint32_t*>(row + W + x);
-        const uint32_t pw = x >= 4 ? *reinterpret_cast<const uint32_t*>(row + x - 4) : 0u;
-        const uint32_t nw = x + 4 < W ? *reinterpret_cast<const uint32_t*>(row + x + 4) : 0u;
-        const uint32_t lf = __funnelshift_l(pw, c, 8);              // pixels x-1 .. x+2
-        const uint32_t rt = __funnelshift_r(c, nw, 8);              // pixels x+1 .. x+4
-        // motion maps hold only 0 and 255: there the median is a bitwise majority
-        out = bytes_binary(up) && bytes_binary(dn) && bytes_binary(lf) && bytes_binary(rt) &&
-                      bytes_binary(c)
-                  ? maj5(up, dn, lf, rt, c)
-                  : med5_bytes(up, dn, lf, rt, c);
-        if (x == 0) out = (out & 0xffffff00u) | (c & 0xffu);        // column 0 copied
-        if (x + 4 == W) out = (out & 0x00ffffffu) | (c & 0xff000000u);   // column W-1 copied
+        const uint4 up = *reinterpret_cast<const uint4*>(row - W + x);
+        const uint4 dn = *reinterpret_cast<const uint4*>(row + W + x);
+        const uint32_t pw = x > 0 ? *reinterpret_cast<const uint32_t*>(row + x - 4) : 0u;
+        const uint32_t nw = x + 16 < W ? *reinterpret_cast<const uint32_t*>(row + x + 16) : 0u;
+        const uint32_t cw[6] = {pw, c.x, c.y, c.z, c.w, nw};
+        const uint32_t uw[4] = {up.x, up.y, up.z, up.w}, dw[4] = {dn.x, dn.y, dn.z, dn.w};
+        uint32_t nb = nonbinary_bits(pw) | nonbinary_bits(nw);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) nb |= nonbinary_bits(uw[j]) | nonbinary_bits(dw[j]) | nonbinary_bits(cw[j + 1]);
+        uint32_t m[4];
+        if (__all_sync(__activemask(), nb == 0)) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            m[j] = maj5(uw[j], dw[j], __funnelshift_l(cw[j], cw[j + 1], 8), __funnelshift_r(cw[j + 1], cw[j + 2], 8),
+                        cw[j + 1]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            m[j] = med5_bytes(uw[j], dw[j], __funnelshift_l(cw[j], cw[j + 1], 8),
+                              __funnelshift_r(cw[j + 1], cw[j + 2], 8), cw[j + 1]);
+        }
+        out = make_uint4(m[0], m[1], m[2], m[3]);
+        if (x == 0) out.x = (out.x & 0xffffff00u) | (c.x & 0xffu);                 // column 0 copied
+        if (x + 16 == W) out.w = (out.w & 0x00ffffffu) | (c.w & 0xff000000u);      // column W-1 copied
       }
-      for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint32_t*>(of[p] + (size_t)y * W + x) = out;
+      const size_t o = (size_t)y * W + x;
+      for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint4*>(of[p] + o) = out;
     });
   });
 }
