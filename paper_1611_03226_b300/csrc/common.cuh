@@ -120,7 +120,9 @@ struct ImgArgs {
   ImgPlan* plan;
 };
 
-constexpr int kImgBand = 16;        // output rows per work item
+// output rows per work item: 32, or 16 for frames wider than 1024 pixels (the
+// shared memory of a CTA then stays under 227 KB up to the widest frame)
+__host__ __device__ constexpr int img_band(int W) { return W <= 1024 ? 32 : 16; }
 constexpr int kImgThreads = 256;
 constexpr int kImgMaxWidth = 2048;
 // shared memory of an image body CTA: two staging buffers of input rows
@@ -128,7 +130,7 @@ constexpr int kImgMaxWidth = 2048;
 // u16 rows of W + 16 (8 leading elements hold the 2 clamped left columns, so
 // pixel 0 starts 16-byte aligned; the 2 clamped right columns follow pixel W-1)
 __host__ __device__ constexpr size_t img_smem_bytes(int W) {
-  return 2 * (size_t)(kImgBand + 4) * W + (size_t)kImgBand * (W + 16) * 2 + 16;
+  return 2 * (size_t)(img_band(W) + 4) * W + (size_t)img_band(W) * (W + 16) * 2 + 16;
 }
 
 // --------------------------------------------------- fused predistorter ----

@@ -138,11 +138,11 @@ __device__ inline void thres_body(const ImgArgs& a, const ImgPlan& pl, Grid g) {
   }
 }
 
-// Start copying input rows y0-2 .. y0+kImgBand+1 (those inside the frame) of
+// Start copying input rows y0-2 .. y0+band+1 (those inside the frame) of
 // one frame into s (row y at s + (y - y0 + 2) * W) with 16-byte asynchronous
 // copies; the caller commits and waits.
-__device__ __forceinline__ void stage_rows(const uint8_t* frame, uint8_t* s, int W, int H, int y0) {
-  const int ya = max(y0 - 2, 0), yb = min(y0 + kImgBand + 2, H);
+__device__ __forceinline__ void stage_rows(const uint8_t* frame, uint8_t* s, int W, int H, int y0, int band) {
+  const int ya = max(y0 - 2, 0), yb = min(y0 + band + 2, H);
   const int vpr = W / 16;
   const int nv = (yb - ya) * vpr;
   const uint8_t* src = frame + (size_t)ya * W;
@@ -155,55 +155,69 @@ __device__ __forceinline__ void stage_rows(const uint8_t* frame, uint8_t* s, int
 __device__ __forceinline__ void img_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void img_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Calls f(y, x) for every row y in [ya, yb) and 16-pixel unit x = 0, 16, ..
-// of a W-pixel row (W % 16 == 0), spread over the CTA's threads (flat index
-// tid + k * blockDim.x, advanced without a division per step).
-template <typename F>
-__device__ __forceinline__ void for_units(int ya, int yb, int W, F&& f) {
+// A thread's walk over the 16-pixel units of W-pixel rows: unit e = tid +
+// k * blockDim.x of a row range is (row e / q, column e % q), q = W / 16.
+// The start and the stride are fixed per thread, so they are computed once.
+struct UnitMap {
+  int row0, col0, drow, dcol, q;
+};
+__device__ __forceinline__ UnitMap unit_map(int W) {
   const int q = W / 16;
-  const int n = (yb - ya) * q;
-  if (n <= 0) return;
-  int e = threadIdx.x;
-  int y = ya + e / q, c = e % q;
-  const int dy = (int)blockDim.x / q, dc = (int)blockDim.x % q;
-  for (; e < n; e += blockDim.x) {
+  return UnitMap{(int)threadIdx.x / q, (int)threadIdx.x % q, (int)blockDim.x / q, (int)blockDim.x % q, q};
+}
+
+// Calls f(y, x) for every row y in [ya, yb) and 16-pixel unit x = 0, 16, ..
+// of the row, spread over the CTA's threads as the map says.
+template <typename F>
+__device__ __forceinline__ void for_units(const UnitMap& m, int ya, int yb, F&& f) {
+  int y = ya + m.row0, c = m.col0;
+  while (y < yb) {
     f(y, 16 * c);
-    y += dy;
-    c += dc;
-    if (c >= q) {
-      c -= q;
+    y += m.drow;
+    c += m.dcol;
+    if (c >= m.q) {
+      c -= m.q;
       ++y;
     }
   }
 }
 
-// Band items (frame, band of kImgBand rows) of this CTA with the input rows of
-// the next item staged while the current one is computed (two buffers).
+// Band items (frame, band of img_band(W) rows) of this CTA with the input
+// rows of the next item staged while the current one is computed (two
+// buffers).  Items g.b, g.b + g.n, ..: (frame, band) advances by a fixed
+// step, so it is carried along instead of divided out per item.
 template <typename F>
 __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem,
                                                F&& compute) {
-  const int W = a.W, H = a.H;
+  const int W = a.W, H = a.H, band = img_band(W);
   const uint64_t frames = pl.n * a.in[0].rate;
-  const int bands = (H + kImgBand - 1) / kImgBand;
-  const uint64_t items = frames * bands;
-  const size_t sb = (size_t)(kImgBand + 4) * W;                    // one staging buffer
-  auto stage = [&](uint64_t it, int buf) {
-    uint64_t f;
-    uint32_t b;
-    div_item(it, (uint32_t)bands, f, b);
-    stage_rows(img_frame(a.in[0], pl.slot_in[0], f), smem + buf * sb, W, H, (int)b * kImgBand);
+  const uint32_t bands = (uint32_t)((H + band - 1) / band);
+  const size_t sb = (size_t)(band + 4) * W;                        // one staging buffer
+  uint64_t f;
+  uint32_t b;
+  div_item(g.b, bands, f, b);
+  uint64_t fq;
+  uint32_t fr;
+  div_item(g.n, bands, fq, fr);
+  auto next = [&](uint64_t& nf, uint32_t& nb) {
+    nb += fr;
+    nf += fq;
+    if (nb >= bands) {
+      nb -= bands;
+      ++nf;
+    }
   };
   __shared__ uint8_t* out_frames[kMaxPorts];
   int buf = 0;
-  if ((uint64_t)g.b < items) stage(g.b, 0);
+  if (f < frames) stage_rows(img_frame(a.in[0], pl.slot_in[0], f), smem, W, H, (int)b * band, band);
   img_commit();
-  for (uint64_t it = g.b; it < items; it += g.n) {
-    if (it + g.n < items) stage(it + g.n, buf ^ 1);
+  while (f < frames) {
+    uint64_t f1 = f;
+    uint32_t b1 = b;
+    next(f1, b1);
+    if (f1 < frames) stage_rows(img_frame(a.in[0], pl.slot_in[0], f1), smem + (buf ^ 1) * sb, W, H, (int)b1 * band, band);
     img_commit();
-    uint64_t f;
-    uint32_t b;
-    div_item(it, (uint32_t)bands, f, b);
-    const int y0 = (int)b * kImgBand;
+    const int y0 = (int)b * band;
     // this item's output frames, one per port
     if (threadIdx.x < a.n_out) {
       const int p = threadIdx.x;
@@ -211,9 +225,11 @@ __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& 
     }
     img_wait_prev();
     __syncthreads();
-    compute(y0, min(y0 + kImgBand, H), smem + buf * sb, out_frames);
+    compute(y0, min(y0 + band, H), smem + buf * sb, out_frames);
     __syncthreads();
     buf ^= 1;
+    f = f1;
+    b = b1;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -245,17 +261,18 @@ __device__ __forceinline__ uint32_t hsum5(uint32_t w01, uint32_t w23, uint32_t w
 // at W + 8, W + 9.
 __host__ __device__ constexpr int kImgVPitch(int W) { return W + 16; }
 
-// Gauss over bands of kImgBand rows, 16 pixels per thread and pass.  Vertical
+// Gauss over bands of img_band(W) rows, 16 pixels per thread and pass.  Vertical
 // sums of the 5 rows go to shared memory; the horizontal pass then weights 5
 // neighbouring sums, adds 128 and shifts right by 8.
 __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
-  uint16_t* v = reinterpret_cast<uint16_t*>(smem + 2 * (size_t)(kImgBand + 4) * W);
+  uint16_t* v = reinterpret_cast<uint16_t*>(smem + 2 * (size_t)(img_band(W) + 4) * W);
   const int vw = kImgVPitch(W);
+  const UnitMap um = unit_map(W);
   for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
     // vertical pass over the band's filtered rows (2 <= y < H-2)
     const int fa = max(y0, 2), fb = min(y1, H - 2);
-    for_units(fa, fb, W, [&](int yr, int x) {
+    for_units(um, fa, fb, [&](int yr, int x) {
       const uint8_t* col = s + (yr - y0) * W + x;                   // row yr-2
       const uint4 r0 = *reinterpret_cast<const uint4*>(col);
       const uint4 r1 = *reinterpret_cast<const uint4*>(col + W);
@@ -279,7 +296,7 @@ __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, u
     });
     __syncthreads();
     // horizontal pass and the unfiltered rows
-    for_units(y0, y1, W, [&](int y, int x) {
+    for_units(um, y0, y1, [&](int y, int x) {
       uint4 out;
       if (y < 2 || y >= H - 2) {
         out = *reinterpret_cast<const uint4*>(s + (y - y0 + 2) * W + x);
@@ -304,13 +321,14 @@ __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, u
 // Any byte of w neither 0x00 nor 0xff: a nonzero word.
 __device__ __forceinline__ uint32_t nonbinary_bits(uint32_t w) { return (w ^ (w << 1)) & 0xfefefefeu; }
 
-// Med over bands of kImgBand rows, 16 pixels per thread.  Where a whole warp's
+// Med over bands of img_band(W) rows, 16 pixels per thread.  Where a whole warp's
 // inputs hold only 0 and 255 (every motion map) the median is a bitwise
 // majority; otherwise the bytewise min/max network runs.
 __device__ inline void med_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
+  const UnitMap um = unit_map(W);
   for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
-    for_units(y0, y1, W, [&](int y, int x) {
+    for_units(um, y0, y1, [&](int y, int x) {
       const uint8_t* row = s + (y - y0 + 2) * W;
       const uint4 c = *reinterpret_cast<const uint4*>(row + x);
       uint4 out = c;
