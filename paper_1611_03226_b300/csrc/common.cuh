@@ -115,6 +115,7 @@ struct ImgArgs {
   ChanDesc out[kMaxPorts];
   int n_out;
   int W, H, thr;
+  int dedup;                // Thres: in[1] is in[0]'s stream delayed by one token (same broadcast writer)
   uint64_t* ctr;
   EngineDev* eng;
   ImgPlan* plan;

@@ -97,8 +97,61 @@ __device__ __forceinline__ uint32_t med5_bytes(uint32_t a, uint32_t b, uint32_t 
   return lo | (hi << 8);
 }
 
+__device__ __forceinline__ uint4 thres4(uint4 x, uint4 y, uint32_t thr4) {
+  return make_uint4(__vcmpgtu4(__vabsdiffu4(x.x, y.x), thr4), __vcmpgtu4(__vabsdiffu4(x.y, y.y), thr4),
+                    __vcmpgtu4(__vabsdiffu4(x.z, y.z), thr4), __vcmpgtu4(__vabsdiffu4(x.w, y.w), thr4));
+}
+
+constexpr int kThresChunk = 4;     // frames per item when the previous frames are shared
+
+// Thres when in[1] carries in[0]'s stream one token later: an item walks
+// kThresChunk consecutive frames of one vector block, reading each current
+// frame once and keeping it as the next frame's previous one; only the
+// first frame of the chunk takes its previous frame from the other input
+// (frame 0 of the window: the delay channel's own token).
+__device__ inline void thres_dedup(const ImgArgs& a, const ImgPlan& pl, Grid g) {
+  const uint64_t frames = pl.n * a.in[0].rate;
+  const uint32_t vpf = (uint32_t)((uint64_t)a.W * a.H / 16);
+  const uint32_t per_item = 4 * blockDim.x;
+  const uint32_t ipf = (vpf + per_item - 1) / per_item;
+  const uint64_t items = (frames + kThresChunk - 1) / kThresChunk * ipf;
+  const uint32_t thr4 = 0x01010101u * (uint32_t)a.thr;
+  for (uint64_t it = g.b; it < items; it += g.n) {
+    uint64_t ch;
+    uint32_t ci;
+    div_item(it, ipf, ch, ci);
+    const uint64_t j0 = ch * kThresChunk;
+    const int nj = (int)min((uint64_t)kThresChunk, frames - j0);
+    const uint32_t v0 = ci * per_item + threadIdx.x;
+    const uint4* p = reinterpret_cast<const uint4*>(
+        j0 == 0 ? img_frame(a.in[1], pl.slot_in[1], 0) : img_frame(a.in[0], pl.slot_in[0], j0 - 1));
+    uint4 y[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (v0 + k * blockDim.x < vpf) y[k] = p[v0 + k * blockDim.x];
+    for (int j = 0; j < nj; ++j) {
+      const uint4* c = reinterpret_cast<const uint4*>(img_frame(a.in[0], pl.slot_in[0], j0 + j));
+      uint4* o = reinterpret_cast<uint4*>(img_frame(a.out[0], pl.slot_out[0], j0 + j));
+      uint4 x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (v0 + k * blockDim.x < vpf) x[k] = c[v0 + k * blockDim.x];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (v0 + k * blockDim.x < vpf) {
+          o[v0 + k * blockDim.x] = thres4(x[k], y[k], thr4);
+          y[k] = x[k];
+        }
+    }
+  }
+}
+
 // Thres over whole frames: 255 where |cur - prev| > thr.
 __device__ inline void thres_body(const ImgArgs& a, const ImgPlan& pl, Grid g) {
+  if (a.dedup) {
+    thres_dedup(a, pl, g);
+    return;
+  }
   const uint64_t frames = pl.n * a.in[0].rate;
   const uint32_t vpf = (uint32_t)((uint64_t)a.W * a.H / 16);        // 16-byte vectors per frame
   const uint32_t per_item = 4 * kImgThreads;

@@ -939,6 +939,16 @@ df_status df_net_finalize(df_net* net) {
       m.W = A.img.width;
       m.H = A.img.height;
       m.thr = A.img.threshold;
+      if (A.kind == DF_THRES) {
+        // Both inputs come from one writer that puts the same tokens on all its
+        // outputs, the second with one delay token: then within a step the
+        // previous frame of window frame j >= 1 is frame j - 1 of the first input.
+        const ChanH &cur = net->chans[A.in[0]], &prev = net->chans[A.in[1]];
+        const int wk = net->actors[cur.src].kind;
+        const bool broadcast = wk == DF_SOURCE || wk == DF_COPY || wk == DF_GAUSS5 || wk == DF_THRES ||
+                               wk == DF_MED5;
+        m.dedup = (cur.src == prev.src && broadcast && cur.init == 0 && prev.init == 1) ? 1 : 0;
+      }
       m.ctr = net->d_ctr;
       m.eng = net->d_eng;
       m.plan = reinterpret_cast<ImgPlan*>(base + ip[img_index[a]].off);

@@ -114,3 +114,39 @@ def test_single_actor_on_gray_frames(Net, kind, H, W):
     for s in (s0, s1):
         np.testing.assert_array_equal(net.pop(s, dtype=np.uint8).reshape(T, H, W), want)
     net.close()
+
+
+@pytest.mark.parametrize("wiring", ["two_sources", "delay_on_first_input", "one_source"])
+def test_thres_input_wirings(Net, wiring):
+    """Thres reads its previous frames from the current input only when the second input
+    is the first one's stream one token later (one broadcast writer, delay on input 1);
+    the other wirings take every frame from its own channel."""
+    T, H, W, rate, t = 12, 24, 48, 2, 20
+    a = synth.uniform_frames(T, H, W, seed=21)
+    b = synth.uniform_frames(T, H, W, seed=22)
+    init = synth.uniform_frames(1, H, W, seed=23)[0]
+    fb = H * W
+    net = Net()
+    s0 = net.add_source()
+    s1 = net.add_source() if wiring == "two_sources" else s0
+    th, snk = net.add_thres(W, H, t), net.add_sink()
+    d0, d1 = (1, 0) if wiring == "delay_on_first_input" else (0, 1 if wiring == "one_source" else 0)
+    net.connect(s0, 0, th, 0, fb, rate, T + 1, d0, init if d0 else None)
+    net.connect(s1, 1 if s1 == s0 else 0, th, 1, fb, rate, T + 1, d1, init if d1 else None)
+    net.connect(th, 0, snk, 0, fb, rate, T + 1)
+    net.finalize()
+    net.push(s0, a)
+    if wiring == "two_sources":
+        net.push(s1, b)
+    net.run(-1)
+    got = net.pop(snk, dtype=np.uint8).reshape(-1, H, W)
+    net.close()
+    if wiring == "two_sources":
+        first, second = a, b
+    elif wiring == "delay_on_first_input":
+        first, second = np.concatenate([init[None], a]), a
+    else:
+        first, second = a, np.concatenate([init[None], a])
+    n = min(len(first), len(second)) // rate * rate
+    assert len(got) == n
+    np.testing.assert_array_equal(got, np.stack([MP.thres(first[i], second[i], t) for i in range(n)]))
