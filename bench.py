@@ -699,6 +699,7 @@ def bench_dpd_fit(args, P, torch, pk):
     n = x.numel()
     stream = torch.cuda.current_stream()
     F.ila_fit(x, steps=3)                                   # warm-up
+    F.ila_fit(x, steps=3, graph=False)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -706,6 +707,12 @@ def bench_dpd_fit(args, P, torch, pk):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_fit = e0.elapsed_time(e1)
+    # the same fit with the training step issued eagerly (no graph)
+    e0.record(stream)
+    F.ila_fit(x, steps=w.steps, lr=w.lr, graph=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fit_eager = e0.elapsed_time(e1)
     gain = F.small_signal_gain()
     nmse_off = F.nmse_db(F.saleh_pa(x) / gain, x)
     nmse_on = F.nmse_db(F.saleh_pa(G.dpd_forward(x, h, w.orders)) / gain, x)
@@ -777,6 +784,8 @@ def bench_dpd_fit(args, P, torch, pk):
     return {
         "workload": f"dpd_fit_{n}_K4_M10_{w.steps}steps", "value": ms_fit / w.steps,
         "unit": "ms/Adam step", "higher_is_better": False, "dtype": "f32",
+        "launch_mode": "one CUDA graph per training step (forward, loss, adjoint, Adam update)",
+        "eager_ms_per_step": ms_fit_eager / w.steps,
         "fwd_bwd_msamples_s": n / ((fwd_ms + bwd_ms) / 1e3) / 1e6,
         "kernel_ms": {"forward": fwd_ms, "backward": bwd_ms},
         "loss_first_last": [float(losses[0]), float(losses[-1])],

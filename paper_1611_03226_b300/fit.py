@@ -45,34 +45,72 @@ def nmse_db(a: torch.Tensor, ref: torch.Tensor) -> float:
     return float(10 * torch.log10(num / den))
 
 
-def adam_fit(u: torch.Tensor, target: torch.Tensor, h0: torch.Tensor, orders, steps=200, lr=1e-3):
+def adam_fit(u: torch.Tensor, target: torch.Tensor, h0: torch.Tensor, orders, steps=200, lr=1e-3,
+             graph=True):
     """Adam on the predistorter taps so that P(u) ~ target (loss mean |P(u) - target|^2);
-    P's forward and gradient run in the engine's kernels.  Returns (h, losses)."""
+    P's forward and gradient run in the engine's kernels.  Returns (h, losses).
+
+    graph=True records one whole training step (forward, loss, adjoint, Adam update)
+    as a CUDA graph and replays it `steps` times, so the host issues one launch
+    per step instead of a few dozen; graph=False runs the same step eagerly."""
     h = h0.detach().clone().requires_grad_(True)
-    opt = torch.optim.Adam([h], lr=lr)
-    losses = []
-    for _ in range(steps):
-        opt.zero_grad(set_to_none=True)
+    if not graph:
+        opt = torch.optim.Adam([h], lr=lr)
+        losses = []
+        for _ in range(steps):
+            opt.zero_grad(set_to_none=True)
+            out = dpd(u, h, orders)
+            loss = (out - target).abs().pow(2).mean()
+            loss.backward()
+            opt.step()
+            losses.append(loss.detach())
+        return h.detach(), torch.stack(losses).cpu().numpy()
+    opt = torch.optim.Adam([h], lr=lr, capturable=True)
+
+    def train_step():
         out = dpd(u, h, orders)
         loss = (out - target).abs().pow(2).mean()
         loss.backward()
         opt.step()
-        losses.append(loss.detach())
-    return h.detach(), torch.stack(losses).cpu().numpy()
+        return loss.detach()
+
+    # two eager steps on a side stream create the optimizer state, the gradient
+    # and the adjoint's scratch before capture; then taps and state are reset
+    side = torch.cuda.Stream(device=u.device)
+    side.wait_stream(torch.cuda.current_stream(u.device))
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            opt.zero_grad(set_to_none=True)
+            train_step()
+        with torch.no_grad():
+            h.copy_(h0)
+            for st in opt.state[h].values():
+                st.zero_()
+    torch.cuda.current_stream(u.device).wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    opt.zero_grad(set_to_none=True)
+    with torch.cuda.graph(g):
+        static_loss = train_step()
+    losses = torch.empty(steps, dtype=static_loss.dtype, device=u.device)
+    for i in range(steps):
+        g.replay()
+        losses[i].copy_(static_loss)
+    return h.detach().clone(), losses.cpu().numpy()
 
 
 def ila_fit(x: torch.Tensor, K=4, M=10, orders=(1, 3, 5, 7), steps=200, lr=1e-3,
-            saleh=(2.1587, 1.1517, 4.0033, 9.1040), memory=(1.0, 0.1, -0.05)):
+            saleh=(2.1587, 1.1517, 4.0033, 9.1040), memory=(1.0, 0.1, -0.05), graph=True):
     """Returns (h, losses) for complex64 CUDA input x."""
     G = small_signal_gain(saleh, memory)
     u = (saleh_pa(x, saleh, memory) / G).to(torch.complex64).contiguous()
     h = torch.zeros((K, M), dtype=torch.complex64, device=x.device)
     h[0, 0] = 1
-    return adam_fit(u, x, h, orders, steps, lr)
+    return adam_fit(u, x, h, orders, steps, lr, graph)
 
 
 def ila_fit_iterative(x: torch.Tensor, iterations=3, K=4, M=10, orders=(1, 3, 5, 7), steps=200,
-                      lr=1e-3, saleh=(2.1587, 1.1517, 4.0033, 9.1040), memory=(1.0, 0.1, -0.05)):
+                      lr=1e-3, saleh=(2.1587, 1.1517, 4.0033, 9.1040), memory=(1.0, 0.1, -0.05),
+                      graph=True):
     """Iterative indirect learning: in iteration i the current predistorter P_i
     drives the amplifier with z = P_i(x) (forward kernel); a postdistorter started
     from P_i's taps is trained so that P(PA(z)/G) ~ z and becomes P_{i+1}; P_0 is
@@ -86,7 +124,7 @@ def ila_fit_iterative(x: torch.Tensor, iterations=3, K=4, M=10, orders=(1, 3, 5,
         with torch.no_grad():
             z = dpd(x, h, orders).contiguous()
             u = (saleh_pa(z, saleh, memory) / G).to(torch.complex64).contiguous()
-        h, losses = adam_fit(u, z, h, orders, steps, lr)
+        h, losses = adam_fit(u, z, h, orders, steps, lr, graph)
         curves.append(losses)
         with torch.no_grad():
             nmse.append(nmse_db(saleh_pa(dpd(x, h, orders), saleh, memory) / G, x))

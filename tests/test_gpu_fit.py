@@ -34,18 +34,35 @@ def test_pa_model_matches_oracle():
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-5
 
 
-def test_ila_fit_tracks_float64_oracle():
-    """40 Adam steps on 2^14 samples: the engine's loss curve follows the
-    float64 oracle's within 1e-3 relative, and the fit improves the PA."""
+@pytest.mark.parametrize("graph", [True, False])
+def test_ila_fit_tracks_float64_oracle(graph):
+    """40 Adam steps on 2^14 samples, as one CUDA graph per step or eagerly: the
+    engine's loss curve follows the float64 oracle's within 1e-3 relative, and
+    the fit improves the PA."""
     import torch
     from paper_1611_03226_b300 import fit as F
     w = synth.dpd_fit(n=1 << 14)
     steps = 40
-    h, losses = F.ila_fit(torch.from_numpy(w.x).cuda(), steps=steps, lr=1e-3)
+    h, losses = F.ila_fit(torch.from_numpy(w.x).cuda(), steps=steps, lr=1e-3, graph=graph)
     h64, losses64 = OF.ila_fit(w.x, steps=steps, lr=1e-3)
+    assert losses.shape == (steps,)
     assert np.max(np.abs(losses - losses64) / losses64) < 1e-3
     assert losses[-1] < 0.9 * losses[0]
     assert np.linalg.norm(h.cpu().numpy() - h64) / np.linalg.norm(h64) < 1e-3
+
+
+def test_graphed_and_eager_fits_agree():
+    """The captured training step replays the eager one: same loss curve and taps
+    up to float32 rounding of the update (the capturable Adam keeps its step
+    count on the device)."""
+    import torch
+    from paper_1611_03226_b300 import fit as F
+    w = synth.dpd_fit(n=1 << 15)
+    x = torch.from_numpy(w.x).cuda()
+    hg, lg = F.ila_fit(x, steps=30, graph=True)
+    he, le = F.ila_fit(x, steps=30, graph=False)
+    assert np.max(np.abs(lg - le) / le) < 1e-5
+    assert torch.linalg.norm(hg - he) / torch.linalg.norm(he) < 1e-5
 
 
 def test_iterative_ila_tracks_float64_oracle():
