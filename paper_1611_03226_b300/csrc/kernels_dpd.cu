@@ -269,18 +269,38 @@ __global__ void __launch_bounds__(kStatelessP) k_dpd_bwd(StatelessArgs a) {
   }
 }
 
-// grad_h[k][m] = sum over tiles (ascending) of partial[tile][k][m]; fixed order.
-__global__ void k_gh_final(const float2* partial, uint64_t n_tiles, int K, int M, int MT, float2* gh) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= K * M) return;
+// grad_h[k][m] = sum over tiles of partial[tile][k][m], in a fixed order.
+// One CTA per tap (k, m): thread j sums the tile partials j, j + 256, .. in
+// ascending order, then the 256 sums are combined by a tree of fixed shape
+// (warp shuffles, then the 8 warp sums in order), so the result is the same
+// on every run.
+constexpr int kGhThreads = 256;
+__global__ void __launch_bounds__(kGhThreads) k_gh_final(const float2* partial, uint64_t n_tiles, int K, int M,
+                                                         int MT, float2* gh) {
+  const int e = blockIdx.x;
   const int k = e / M, m = e % M;
   float2 s = make_float2(0.f, 0.f);
-  for (uint64_t t = 0; t < n_tiles; ++t) {
+  for (uint64_t t = threadIdx.x; t < n_tiles; t += kGhThreads) {
     const float2 v = partial[(t * K + k) * MT + m];
     s.x += v.x;
     s.y += v.y;
   }
-  gh[e] = s;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+  }
+  __shared__ float2 ws[kGhThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float2 t = ws[0];
+    for (int w = 1; w < kGhThreads / 32; ++w) {
+      t.x += ws[w].x;
+      t.y += ws[w].y;
+    }
+    gh[e] = t;
+  }
 }
 
 static uint64_t stateless_tiles(uint64_t n) {
@@ -347,7 +367,7 @@ cudaError_t dpd_backward_stateless(const float2* x, uint64_t n, const float2* h,
     const unsigned grid = (unsigned)std::min<uint64_t>(nt, 148ull * 16);
     k_dpd_bwd<kStatelessR><<<grid, kStatelessP, smem, s>>>(a);
   }
-  k_gh_final<<<(K * M + 127) / 128, 128, 0, s>>>(a.partial, nt, K, M, a.MT, gh);
+  k_gh_final<<<K * M, kGhThreads, 0, s>>>(a.partial, nt, K, M, a.MT, gh);
   return cudaGetLastError();
 }
 
