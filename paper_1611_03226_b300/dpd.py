@@ -77,3 +77,32 @@ class DPDFunction(torch.autograd.Function):
 
 def dpd(x, h, orders):
     return DPDFunction.apply(x, h, tuple(orders))
+
+
+class DPDMSEFunction(torch.autograd.Function):
+    """loss = mean |P_h(u) - target|^2 with the residual kept for the backward:
+    dL/dy = 2 (y - target) / n (PyTorch's complex convention) goes straight into
+    the adjoint, so the loss adds one subtraction, one dot product and one
+    scale to the forward and one scale to the backward."""
+
+    @staticmethod
+    def forward(ctx, u, h, target, orders):
+        y = dpd_forward(u, h, orders)
+        d = (y - target).contiguous()
+        dr = torch.view_as_real(d).reshape(-1)
+        loss = torch.dot(dr, dr) / d.numel()
+        ctx.save_for_backward(u, h, d)
+        ctx.orders = tuple(orders)
+        return loss
+
+    @staticmethod
+    def backward(ctx, g):
+        u, h, d = ctx.saved_tensors
+        grad_y = d * (g * (2.0 / d.numel()))
+        _, gh = dpd_backward(u, h, ctx.orders, grad_y, need_x=False)
+        return None, gh, None, None
+
+
+def dpd_mse(u, h, target, orders):
+    """mean |P_h(u) - target|^2, differentiable in h (u and target are data)."""
+    return DPDMSEFunction.apply(u, h, target, tuple(orders))

@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import torch
 
-from .dpd import dpd
+from .dpd import dpd, dpd_mse
 
 
 def saleh_pa(x: torch.Tensor, saleh=(2.1587, 1.1517, 4.0033, 9.1040),
@@ -59,8 +59,7 @@ def adam_fit(u: torch.Tensor, target: torch.Tensor, h0: torch.Tensor, orders, st
         losses = []
         for _ in range(steps):
             opt.zero_grad(set_to_none=True)
-            out = dpd(u, h, orders)
-            loss = (out - target).abs().pow(2).mean()
+            loss = dpd_mse(u, h, target, orders)
             loss.backward()
             opt.step()
             losses.append(loss.detach())
@@ -68,8 +67,7 @@ def adam_fit(u: torch.Tensor, target: torch.Tensor, h0: torch.Tensor, orders, st
     opt = torch.optim.Adam([h], lr=lr, capturable=True)
 
     def train_step():
-        out = dpd(u, h, orders)
-        loss = (out - target).abs().pow(2).mean()
+        loss = dpd_mse(u, h, target, orders)
         loss.backward()
         opt.step()
         return loss.detach()

@@ -78,3 +78,24 @@ def test_iterative_ila_tracks_float64_oracle():
         assert np.max(np.abs(c - c64) / c64) < 1e-3
     assert np.max(np.abs(np.array(nmse) - nmse64)) < 1e-3
     assert np.linalg.norm(h.cpu().numpy() - h64) / np.linalg.norm(h64) < 1e-3
+
+
+def test_fused_mse_matches_plain_torch_loss():
+    """dpd_mse's value and tap gradient equal those of the plain composition
+    mean |dpd(u, h) - t|^2 through autograd."""
+    import torch
+    from paper_1611_03226_b300.dpd import dpd, dpd_mse
+    rng = np.random.default_rng(9)
+    n, K, M = 5000, 4, 10
+    u = torch.tensor((rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n)).astype(np.complex64), device="cuda")
+    t = torch.tensor((rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n)).astype(np.complex64), device="cuda")
+    h0 = torch.tensor((rng.normal(0, .1, (K, M)) + 1j * rng.normal(0, .1, (K, M))).astype(np.complex64),
+                      device="cuda")
+    h1 = h0.clone().requires_grad_(True)
+    l1 = dpd_mse(u, h1, t, (1, 3, 5, 7))
+    l1.backward()
+    h2 = h0.clone().requires_grad_(True)
+    l2 = (dpd(u, h2, (1, 3, 5, 7)) - t).abs().pow(2).mean()
+    l2.backward()
+    assert abs(l1.item() - l2.item()) <= 1e-5 * l2.item()
+    assert torch.linalg.norm(h1.grad - h2.grad) <= 1e-4 * torch.linalg.norm(h2.grad)
