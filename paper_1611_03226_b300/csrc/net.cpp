@@ -1542,8 +1542,8 @@ df_status df_autotune(df_net* net, uint64_t* n_firings) {
   if (!net->finalized) return DF_ESTATE;
   DeviceGuard g(net->device);
   cudaStream_t s = net->stream;
-  static const uint32_t kCand[][2] = {{512, 64},   {1024, 128}, {2048, 256}, {1024, 64},
-                                      {2048, 128}, {4096, 256}};
+  static const uint32_t kCand[][2] = {{256, 32},   {512, 32},   {512, 64},  {1024, 128}, {2048, 256},
+                                      {1024, 64},  {2048, 128}, {4096, 256}};
   uint64_t before = 0;
   DF_CUDA(cudaStreamSynchronize(s));
   DF_CUDA(cudaMemcpy(&before, &net->d_eng->fired_total, 8, cudaMemcpyDeviceToHost));
