@@ -41,3 +41,35 @@ def test_param_struct_layout_matches_header():
     # int32 K, M, orders[16], uint32 block_len, int32 branch, then an 8-byte aligned pointer
     assert ctypes.sizeof(L.DpdParams) == 4 * (2 + 16 + 2) + 8
     assert ctypes.sizeof(L.MdParams) == 16
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every parameter struct of the header has the same size and field offsets
+    under gcc (plain C99) as in the ctypes binding."""
+    import shutil
+    import subprocess
+    import pytest
+    from paper_1611_03226_b300 import _lib as L
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {"df_dpd_params": L.DpdParams, "df_md_params": L.MdParams, "df_img_params": L.ImgParams,
+               "df_channel_info_t": L.ChannelInfo, "df_feed": L.Feed, "df_drain": L.Drain}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "dfgpu.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
