@@ -310,3 +310,34 @@ def test_streamed_paper_pipeline_in_eq1_layout(P):
     got = np.concatenate(out[ids["sink"]]).reshape(-1, H, W)
     net.close()
     np.testing.assert_array_equal(got, MP.pipeline(f))
+
+
+def test_layout_and_runner_error_paths(P):
+    from paper_1611_03226_b300 import _lib as L
+    net, ids = EN.motion_paper(P.Net, 24, 32, "eq1", 2)
+    f = synth.uniform_frames(6, 24, 32)
+    with pytest.raises(L.DfError) as e:
+        net.push(ids["src"], f[:3])                            # not a whole window of 2 frames
+    assert e.value.status == L.DF_EINVAL
+    assert net.counters(ids["ch_in"]) == (0, 0, 0)              # nothing written
+    with pytest.raises(L.DfError) as e:
+        net.peek_slots(ids["ch_prev"], 6, 2)                    # the delay buffer has 7 slots
+    assert e.value.status == L.DF_EINVAL
+    with pytest.raises(L.DfError) as e:
+        net.channel_info(99)
+    assert e.value.status == L.DF_EINVAL
+    out = np.zeros_like(f)
+    with pytest.raises(L.DfError) as e:
+        net.stream({ids["src"]: (f, 0)}, {ids["sink"]: (out, 2)})          # batch 0
+    assert e.value.status == L.DF_EINVAL
+    with pytest.raises(L.DfError) as e:
+        net.stream({ids["src"]: (f, 2)}, {ids["sink"]: (out, 2)}, L.DF_RUN_ASYNC)
+    assert e.value.status == L.DF_EINVAL
+    fs = (L.Feed * 1)()
+    fs[0] = L.Feed(ids["sink"], f.ctypes.data, 6, 2)                     # a sink is no source
+    assert L.lib.df_stream(net.h, fs, 1, None, 0, 0, 0, None) == L.DF_EINVAL
+    # the network is still usable: the paper's layout streamed by the persistent kernel
+    popped, _ = net.stream({ids["src"]: (f, 2)}, {ids["sink"]: (out, 2)}, L.DF_RUN_PERSISTENT)
+    assert popped[ids["sink"]] == 6
+    np.testing.assert_array_equal(out, MP.pipeline(f))
+    net.close()
