@@ -1265,25 +1265,27 @@ namespace {
 struct StreamHub {
   std::mutex mu;
   std::condition_variable cv;
-  uint64_t gen = 0;
+  std::atomic<uint64_t> gen{0};
   std::atomic<int32_t> err{DF_OK};
   std::atomic<bool> finished{false};
   std::atomic<int> producers_left{0};
   void bump() {
     {
       std::lock_guard<std::mutex> lk(mu);
-      ++gen;
+      gen.fetch_add(1);
     }
     cv.notify_all();
   }
-  uint64_t now() {
-    std::lock_guard<std::mutex> lk(mu);
-    return gen;
-  }
+  uint64_t now() { return gen.load(); }
+  bool moved(uint64_t seen) { return gen.load() != seen || err.load() != DF_OK || finished.load(); }
+  // A handoff is usually a few microseconds away: spin that long first, then
+  // sleep on the condition variable.
   void wait(uint64_t seen) {
+    const auto t0 = std::chrono::steady_clock::now();
+    while (std::chrono::steady_clock::now() - t0 < std::chrono::microseconds(30))
+      if (moved(seen)) return;
     std::unique_lock<std::mutex> lk(mu);
-    cv.wait_for(lk, std::chrono::microseconds(200),
-                [&] { return gen != seen || err.load() != DF_OK || finished.load(); });
+    cv.wait_for(lk, std::chrono::microseconds(200), [&] { return moved(seen); });
   }
   void fail(int32_t st) {
     int32_t ok = DF_OK;
