@@ -286,7 +286,8 @@ df_status df_channel_peek_slots(df_net *net, int32_t ch, uint64_t first_slot, ui
                                 void *dst);
 
 /* Tile configuration of the predistorter kernel for one actor (0 = default):
- * samples per tile and threads per CTA.  The autotuner sets these. */
+ * samples per tile and threads per CTA (32, 64, 128 or 256; 8 or 16 samples
+ * per thread, else DF_EINVAL).  The autotuner sets these. */
 df_status df_dpd_set_tile(df_net *net, int32_t actor, uint32_t tile, uint32_t threads);
 
 /* Time every supported tile configuration on the network's current pending

@@ -1505,7 +1505,7 @@ df_status df_dpd_set_tile(df_net* net, int32_t actor, uint32_t tile, uint32_t th
   if (!net || actor < 0 || actor >= (int)net->actors.size()) return DF_EINVAL;
   if (net->actors[actor].kind != DF_DPD && net->actors[actor].kind != DF_DPD_FIR) return DF_EINVAL;
   if (tile || threads) {
-    if (threads != 64 && threads != 128 && threads != 256) return DF_EINVAL;
+    if (threads != 32 && threads != 64 && threads != 128 && threads != 256) return DF_EINVAL;
     const uint32_t R = tile / threads;
     if (tile != R * threads || (R != 8 && R != 16)) return DF_EINVAL;
   }

@@ -92,6 +92,7 @@ def test_tiny_workload_full_size(Net):
     (2047, 32, 1, 5, 4, (2048, 256)),  # two 16-tap chunks
     (777, 13, 3, 16, 9, (1024, 64)),  # 16 branches, odd tap count
     (4096, 9, 1, 6, 5, (2048, 128)),  # R = 16 variant
+    (3000, 11, 2, 4, 6, (256, 32)),   # one-warp CTAs, the autotuner's smallest tile
 ])
 def test_random_masks_parity(Net, L, M, d, K, cap, tile):
     rng = np.random.default_rng(L + 7 * M + K)
