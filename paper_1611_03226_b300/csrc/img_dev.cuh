@@ -374,13 +374,20 @@ __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, u
 // Any byte of w neither 0x00 nor 0xff: a nonzero word.
 __device__ __forceinline__ uint32_t nonbinary_bits(uint32_t w) { return (w ^ (w << 1)) & 0xfefefefeu; }
 
-// Med over bands of img_band(W) rows, 16 pixels per thread.  Where a whole warp's
-// inputs hold only 0 and 255 (every motion map) the median is a bitwise
-// majority; otherwise the bytewise min/max network runs.
+// Med over bands of img_band(W) rows, 16 pixels per thread.  One vote per
+// band: when every input byte of the band and its halo rows is 0 or 255 (every
+// motion map) the median is a bitwise majority; otherwise the bytewise
+// min/max network runs.
 __device__ inline void med_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
   const UnitMap um = unit_map(W);
   for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
+    uint32_t nb = 0;
+    for_units(um, max(y0 - 1, 0), min(y1 + 1, H), [&](int y, int x) {
+      const uint4 c = *reinterpret_cast<const uint4*>(s + (y - y0 + 2) * W + x);
+      nb |= nonbinary_bits(c.x) | nonbinary_bits(c.y) | nonbinary_bits(c.z) | nonbinary_bits(c.w);
+    });
+    const bool binary = __syncthreads_or(nb != 0) == 0;
     for_units(um, y0, y1, [&](int y, int x) {
       const uint8_t* row = s + (y - y0 + 2) * W;
       const uint4 c = *reinterpret_cast<const uint4*>(row + x);
@@ -392,11 +399,8 @@ __device__ inline void med_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uin
         const uint32_t nw = x + 16 < W ? *reinterpret_cast<const uint32_t*>(row + x + 16) : 0u;
         const uint32_t cw[6] = {pw, c.x, c.y, c.z, c.w, nw};
         const uint32_t uw[4] = {up.x, up.y, up.z, up.w}, dw[4] = {dn.x, dn.y, dn.z, dn.w};
-        uint32_t nb = nonbinary_bits(pw) | nonbinary_bits(nw);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) nb |= nonbinary_bits(uw[j]) | nonbinary_bits(dw[j]) | nonbinary_bits(cw[j + 1]);
         uint32_t m[4];
-        if (__all_sync(__activemask(), nb == 0)) {
+        if (binary) {
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             m[j] = maj5(uw[j], dw[j], __funnelshift_l(cw[j], cw[j + 1], 8), __funnelshift_r(cw[j + 1], cw[j + 2], 8),
