@@ -256,8 +256,8 @@ def bench_motion(args, P, torch, pk, ws):
         "dtype": "u8", "frames": T,
         "records_per_step": recs / args.steps,
         "kernel_ms": {"md_main_avg": main_avg, "eager_step_avg": step_ms / max(args.steps, 1)},
-        "gpu_launches_per_step": 4,
-        "launch_mode": "CUDA graph replay of one engine step",
+        "gpu_launches_per_step": 3,
+        "launch_mode": "CUDA graph replay of one engine step (plan, main and emit kernels)",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
                      "traffic": profiled_traffic("k_md_main_tma__motion_300x1920x1080.md") if T == 300 else None,
@@ -377,7 +377,7 @@ def bench_dpd_large(args, P, torch, pk, ws):
                              "frac": hbm_gbs / pk["hbm_gbs"], "bytes_per_sample": 16}},
         "e2e": {"value": ws * samples / e2e_s / 1e6, "unit": "Msamples/s",
                 "h2d_bytes_per_step": samples * 8 + nb * 4, "d2h_bytes_per_step": samples * 8},
-        "gpu_launches_per_step": 3,
+        "gpu_launches_per_step": 2,
         "_oracle": w,
     }
 
@@ -583,7 +583,7 @@ def bench_md_paper(args, P, torch, pk):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"], "traffic": None,
                          "algorithmic_bytes_per_frame": bytes_per_frame,
-                         "note": "whole step (6 kernels + step begin) against its channel traffic"},
+                         "note": "whole step (3 plan and 3 body kernels) against its channel traffic"},
             "e2e": {"value": frames_done / statistics.mean(e2e), "unit": "frames/s",
                     "h2d_bytes_per_step": T * fb, "d2h_bytes_per_step": frames_done * fb},
             "e2e_streamed": {"value": frames_done / statistics.mean(st_s), "unit": "frames/s",
@@ -693,7 +693,7 @@ def bench_dpd_batch(args, P, torch, pk):
                             "per_channel_eager": t_per, "per_channel_graph": t_per_graph},
         "batched_vs_per_channel": t_per / t_graph,
         "autotuned_tile": {"samples": tuned[0], "threads": tuned[1]},
-        "gpu_launches_per_step": {"batched": 3, "per_channel": 1 + 2 * C},
+        "gpu_launches_per_step": {"batched": 2, "per_channel": 2 * C},
         "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": ach / peak_tf, "traffic": None, "kernel": "k_dpd_body",
                      "algorithmic_flops_per_launch": flops},

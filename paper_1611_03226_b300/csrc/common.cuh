@@ -36,7 +36,6 @@ struct ChanDesc {          // immutable after finalize
 
 struct EngineDev {          // device-resident engine state
   unsigned long long fired_total;
-  unsigned long long fired_step;
   int32_t status;           // DF_OK or the first device-side error
   int32_t status_where;     // which kernel / wait reported it
   unsigned int barrier_count;   // persistent-kernel grid barrier
@@ -262,7 +261,6 @@ cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_
 // ----------------------------------------------------------- launchers ----
 cudaError_t launch_set_u64(uint64_t* p, uint64_t v, cudaStream_t s);
 cudaError_t launch_add_u64(uint64_t* p, uint64_t v, cudaStream_t s);
-cudaError_t launch_step_begin(EngineDev* e, cudaStream_t s);
 cudaError_t launch_publish(EngineDev* e, cudaStream_t s);   // pub = ctr after a step
 cudaError_t launch_spill(const SpillArgs& a, cudaStream_t s);
 cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s, cudaEvent_t ev0 = nullptr,

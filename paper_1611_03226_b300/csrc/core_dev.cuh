@@ -30,7 +30,6 @@ __device__ inline void copy_plan_dev(const CopyArgs& a) {
     a.plan->wr0[p] = w;
     *wr_ptr(ctr, a.out[p].id) = w + n * a.out[p].rate;
   }
-  atomicAdd(&a.eng->fired_step, (unsigned long long)n);
   atomicAdd(&a.eng->fired_total, (unsigned long long)n);
 }
 

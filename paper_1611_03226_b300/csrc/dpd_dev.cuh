@@ -281,7 +281,6 @@ __device__ inline void dpd_plan_dev(const DpdArgs& a) {
     if (has_ctrl) *rd_ptr(ctr, a.ctrl.id) = s_rdc + n;
     *rd_ptr(ctr, a.data.id) = s_rdd + n;
     *wr_ptr(ctr, a.out.id) = s_wro + n;
-    atomicAdd(&a.eng->fired_step, (unsigned long long)n);
     atomicAdd(&a.eng->fired_total, (unsigned long long)n);
   }
 }

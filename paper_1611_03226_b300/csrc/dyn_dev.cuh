@@ -91,7 +91,6 @@ __device__ inline void dyn_plan_dev(const DynArgs& a) {
     const uint32_t n = (uint32_t)s_n;
     a.plan->n = n;
     *rd_ptr(ctr, a.ctrl.id) = s_rdc + n;
-    atomicAdd(&a.eng->fired_step, (unsigned long long)n);
     atomicAdd(&a.eng->fired_total, (unsigned long long)n);
   }
   __syncthreads();

@@ -45,7 +45,6 @@ __device__ inline void img_plan_dev(const ImgArgs& a) {
     a.plan->slot_out[p] = (w - a.out[p].wshift) % a.out[p].cap;
     *wr_ptr(ctr, a.out[p].id) = w + n * r;
   }
-  atomicAdd(&a.eng->fired_step, (unsigned long long)n);
   atomicAdd(&a.eng->fired_total, (unsigned long long)n);
 }
 

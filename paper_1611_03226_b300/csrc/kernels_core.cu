@@ -7,7 +7,6 @@ namespace dfg {
 
 __global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
 __global__ void k_add_u64(uint64_t* p, uint64_t v) { *p += v; }
-__global__ void k_step_begin(EngineDev* e) { e->fired_step = 0; }
 
 cudaError_t launch_set_u64(uint64_t* p, uint64_t v, cudaStream_t s) {
   k_set_u64<<<1, 1, 0, s>>>(p, v);
@@ -15,10 +14,6 @@ cudaError_t launch_set_u64(uint64_t* p, uint64_t v, cudaStream_t s) {
 }
 cudaError_t launch_add_u64(uint64_t* p, uint64_t v, cudaStream_t s) {
   k_add_u64<<<1, 1, 0, s>>>(p, v);
-  return cudaGetLastError();
-}
-cudaError_t launch_step_begin(EngineDev* e, cudaStream_t s) {
-  k_step_begin<<<1, 1, 0, s>>>(e);
   return cudaGetLastError();
 }
 

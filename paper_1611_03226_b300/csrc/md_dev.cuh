@@ -384,7 +384,6 @@ __device__ inline void md_emit_frame(const MdArgs& a, uint64_t j, bool lead) {
     *rd_ptr(ctr, a.prev.id) = pl.rd_prev0 + n;
     *wr_ptr(ctr, a.cnt.id) = pl.wr_cnt0 + n;
     *wr_ptr(ctr, a.rec.id) = pl.wr_rec0 + s_used;
-    atomicAdd(&a.eng->fired_step, (unsigned long long)n);
     atomicAdd(&a.eng->fired_total, (unsigned long long)n);
   }
   if (j >= n) return;

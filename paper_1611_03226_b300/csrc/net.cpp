@@ -253,13 +253,13 @@ df_status validate_actor(const df_net* net, int a) {
 
 // The engine word after all queued work, with one copy into the pinned
 // staging and one wait: the firing total and the device status.
-static_assert(offsetof(EngineDev, fired_total) == 0 && offsetof(EngineDev, status) == 16,
+static_assert(offsetof(EngineDev, fired_total) == 0 && offsetof(EngineDev, status) == 8,
               "engine word layout");
 df_status read_engine(df_net* net, uint64_t* total, int32_t* status) {
-  DF_CUDA(cudaMemcpyAsync(net->h_pin, net->d_eng, 24, cudaMemcpyDeviceToHost, net->stream));
+  DF_CUDA(cudaMemcpyAsync(net->h_pin, net->d_eng, 16, cudaMemcpyDeviceToHost, net->stream));
   DF_CUDA(cudaStreamSynchronize(net->stream));
   *total = net->h_pin[0];
-  std::memcpy(status, reinterpret_cast<const uint8_t*>(net->h_pin) + 16, sizeof(int32_t));
+  std::memcpy(status, reinterpret_cast<const uint8_t*>(net->h_pin) + 8, sizeof(int32_t));
   net->fired_seen = *total;
   net->fired_known = true;
   return DF_OK;
@@ -349,7 +349,6 @@ df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
   cudaStream_t s = net->stream;
   const auto step_ev = prof_pair(net, DF_PROF_STEP, capturing);
   if (step_ev.first) DF_CUDA(cudaEventRecord(step_ev.first, s));
-  DF_CUDA(launch_step_begin(net->d_eng, s));
   for (const Op& op : net->program) {
     switch (op.kind) {
       case kOpCopy: {
@@ -1198,15 +1197,18 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
       }
     }
   } else {
+    // a step fired nothing when the (monotonic) firing total did not move
     const int64_t kMaxSteps = 1 << 20;
     int64_t i = 0;
+    uint64_t total = before;
     for (; i < kMaxSteps; ++i) {
       const df_status st = enqueue_step(net, no_batch);
       if (st != DF_OK) return st;
-      DF_CUDA(cudaMemcpyAsync(net->h_pin, &net->d_eng->fired_step, 8, cudaMemcpyDeviceToHost,
+      DF_CUDA(cudaMemcpyAsync(net->h_pin, &net->d_eng->fired_total, 8, cudaMemcpyDeviceToHost,
                               net->stream));
       DF_CUDA(cudaStreamSynchronize(net->stream));
-      if (net->h_pin[0] == 0) break;
+      if (net->h_pin[0] == total) break;
+      total = net->h_pin[0];
     }
     if (i == kMaxSteps) return DF_EDEADLOCK;
   }
@@ -1553,7 +1555,6 @@ df_status df_autotune(df_net* net, uint64_t* n_firings) {
   DF_CUDA(cudaEventCreate(&e0));
   DF_CUDA(cudaEventCreate(&e1));
   df_status st = DF_OK;
-  DF_CUDA(launch_step_begin(net->d_eng, s));
   for (const Op& op : net->program) {
     if (op.kind == kOpCopy) {
       DF_CUDA(launch_copy(op.copy, net->n_sm, s));

@@ -77,9 +77,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp*
   const int64_t max_steps = n_steps < 0 ? (int64_t)1 << 20 : n_steps;
   volatile unsigned long long* snap = &eng->total_snap;
   if (n_ops == 0) return;
-  // fired_step counts the firings of the whole launch here (the host reads
-  // fired_total); the first barrier records the total before any commit
-  if (lead && threadIdx.x == 0) eng->fired_step = 0;
+  // the first barrier records the firing total before any commit
   if (!grid_barrier(eng, nb, limit_ns, true)) return;
   unsigned long long fired0 = *snap;
   for (int64_t step = 0; step < max_steps; ++step) {
