@@ -341,3 +341,35 @@ def test_layout_and_runner_error_paths(P):
     assert popped[ids["sink"]] == 6
     np.testing.assert_array_equal(out, MP.pipeline(f))
     net.close()
+
+
+@pytest.mark.parametrize("rate", [1, 3])
+def test_broadcast_push_into_eq1_delay_buffer(P, rate):
+    """A source broadcasting into two Eq. 1 channels of Thres, the second with one
+    delay token: the push fills the delay buffer by a device copy from the first
+    channel and makes the slot 3r -> 0 copy itself; Thres takes its previous frames
+    from its current input.  Raw slots follow Fig. 2 after every push and step."""
+    H, W, T = 16, 32, 6 * rate
+    f = synth.uniform_frames(T, H, W, seed=31)
+    init = synth.uniform_frames(1, H, W, seed=32)[0]
+    net = P.Net()
+    src, th, snk = net.add_source(), net.add_thres(W, H, 20), net.add_sink()
+    c0 = net.connect(src, 0, th, 0, H * W, rate, "eq1")
+    c1 = net.connect(src, 1, th, 1, H * W, rate, "eq1", 1, init)
+    net.connect(th, 0, snk, 0, H * W, rate, "eq1")
+    net.finalize()
+    models = [(SlotModel(rate), c0), (SlotModel(rate, init), c1)]
+    got = []
+    for i in range(0, T, rate):
+        net.push(src, f[i:i + rate])
+        for m, c in models:
+            m.check(net, c, f)
+        net.run(1)
+        for m, c in models:
+            m.check(net, c, f)
+        got.append(net.pop(snk, dtype=np.uint8))
+    net.close()
+    got = np.concatenate(got).reshape(-1, H, W)
+    prev = np.concatenate([init[None], f[:-1]])
+    np.testing.assert_array_equal(got, np.stack([MP.thres(f[i], prev[i], 20) for i in range(T)]))
+    assert models[1][0].buf.nw >= 3                 # the delay buffer filled slot 3r at least once
