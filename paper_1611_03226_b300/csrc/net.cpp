@@ -1371,10 +1371,19 @@ df_status df_stream(df_net* net, const df_feed* feeds, int32_t n_feeds, df_drain
   StreamHub hub;
   hub.producers_left = n_feeds;
   std::vector<std::thread> threads;
-  for (int i = 0; i < n_feeds; ++i)
-    threads.emplace_back(stream_produce, net, std::cref(feeds[i]), ftok[i], std::ref(hub));
-  for (int i = 0; i < n_drains; ++i)
-    threads.emplace_back(stream_consume, net, std::ref(drains[i]), dtok[i], std::ref(hub));
+  try {
+    threads.reserve((size_t)n_feeds + (size_t)n_drains);
+    for (int i = 0; i < n_feeds; ++i)
+      threads.emplace_back(stream_produce, net, std::cref(feeds[i]), ftok[i], std::ref(hub));
+    for (int i = 0; i < n_drains; ++i)
+      threads.emplace_back(stream_consume, net, std::ref(drains[i]), dtok[i], std::ref(hub));
+  } catch (...) {                            // no thread: stop the ones started, report it
+    hub.fail(DF_ENOMEM);
+    hub.finished = true;
+    hub.bump();
+    for (std::thread& t : threads) t.join();
+    return DF_ENOMEM;
+  }
   // this thread runs the GPU actors: one step at a time, sleeping while
   // nothing can fire; the run is over when the sources are exhausted, a step
   // fired nothing, every drained sink is empty and one more step (after the
