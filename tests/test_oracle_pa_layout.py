@@ -89,3 +89,29 @@ def test_eq1_unread_capacity_is_the_exact_bound(r):
         assert cap + (1 if delay else 0) == PL.eq1_capacity_tokens(r, delay)
         assert _orders_deliver_fifo(make, r, cap, 12)
         assert not _orders_deliver_fifo(make, r, cap + r, 12)
+
+
+def test_oracle_network_eq1_capacities_and_pipeline():
+    """capacity="eq1" gives 2r unread tokens to a plain channel and 3r to a delay
+    channel; the paper's pipeline built that way still computes the motion maps,
+    and more than one delay token is refused."""
+    import synth
+    from oracle import motion_paper as MP
+    from oracle import nets as ON
+    from oracle.network import Network, NetworkError, Sink, Source
+    from oracle import actors as A
+    for rate in (1, 4):
+        net, ids = ON.motion_paper(16, 32, "eq1", rate)
+        caps = [net.channels[ids[k]].capacity for k in ("ch_in", "ch_cur", "ch_prev", "ch_map", "ch_out")]
+        assert caps == [2 * rate, 2 * rate, 3 * rate, 2 * rate, 2 * rate]
+        f = synth.uniform_frames(4 * rate, 16, 32)
+        got = []
+        for i in range(0, len(f), rate):
+            net.push(ids["src"], list(f[i:i + rate]))
+            net.run(-1)
+            got += net.pop(ids["sink"])
+        assert np.array_equal(np.array(got), MP.pipeline(f))
+    net = Network()
+    a, c = net.add_actor(Source()), net.add_actor(A.Copy())
+    with pytest.raises(NetworkError):
+        net.connect(a, 0, c, 0, 2, "eq1", [b"xx", b"yy"], 2)
