@@ -515,14 +515,14 @@ def bench_md_paper(args, P, torch, pk):
         if i >= args.warmup:
             e2e.append(time.perf_counter() - t0)
     net.close()
-    # the paper's concurrent host actors: a producer thread pushes 64-frame
+    # the paper's concurrent host actors: a producer thread pushes 256-frame
     # chunks from pinned memory and a consumer thread pops motion maps into
-    # pinned memory, through channels of 256 frames, while steps run
+    # pinned memory, through channels of 1024 frames, while steps run
     from paper_1611_03226_b300.stream import stream
     net = P.Net(stream=torch.cuda.current_stream().cuda_stream)
     src, g, t, m, snk = (net.add_source(), net.add_gauss5(W, H), net.add_thres(W, H, thr),
                          net.add_med5(W, H), net.add_sink())
-    cap_s, chunk = 256, 64
+    cap_s, chunk = 1024, 256
     net.connect(src, 0, g, 0, fb, rate, cap_s)
     net.connect(g, 0, t, 0, fb, rate, cap_s)
     net.connect(g, 1, t, 1, fb, rate, cap_s, 1)
@@ -589,7 +589,7 @@ def bench_md_paper(args, P, torch, pk):
             "e2e_streamed": {"value": frames_done / statistics.mean(st_s), "unit": "frames/s",
                              "python_threads_value": frames_done / statistics.mean(st_py),
                              "note": "native producer and consumer threads (df_stream) beside the running "
-                                     "steps (DF_IO_CONCURRENT), 256-frame channels, 64-frame chunks; "
+                                     "steps (DF_IO_CONCURRENT), 1024-frame channels, 256-frame chunks; "
                                      "python_threads_value: the same with Python threads"},
             "e2e_streamed_eq1": {"value": T1 / statistics.mean(st_q), "unit": "frames/s", "frames": T1,
                                  "steps": n_steps_eq1, "buffer_bytes": eq1_bytes,
