@@ -5,8 +5,13 @@ P(y/G) ~ x (y = PA(x), G = small-signal gain), loss mean |P(y/G) - x|^2,
 Adam from the identity.  Gradients come from the float64 adjoint
 (dpd.dpd_stream_backward); Adam acts on the real and imaginary parts as
 separate real parameters (bias-corrected first and second moments).
-Parity unpinned: there is no paper value for the fit outcome; the tests
-compare the engine's loss curve with this one.
+
+Pins: the update rule of :func:`adam_fit` against a hand-expanded recurrence on
+a one-tap problem and against torch.optim.Adam in float64 (gradients from
+torch autograd); the amplifier against the identities of the Saleh model; the
+gradient against finite differences.  The paper prints no fit outcome, so the
+final NMSE itself has no value to be compared with; the tests compare the
+engine's loss curve with this one.
 """
 from __future__ import annotations
 

@@ -8,6 +8,12 @@ Memoryless Saleh model followed by a short memory FIR:
     y[n]   = sum_i c_i v[n - i]                  (zeros before the first sample)
 
 The fit normalises by the small-signal gain G = alpha_a * sum_i c_i.
+
+Pins (tests): A(r) = A(1/(beta_a r)) and Phi(r) + Phi(1/(beta_p r)) =
+alpha_p / beta_p at large and small amplitudes, the small-signal limits, the
+AM/AM peak at r = 1/sqrt(beta_a), the sign of the phase shift, and the
+memory taps acting after the nonlinearity (numpy.convolve of the memoryless
+output).
 """
 from __future__ import annotations
 
