@@ -52,6 +52,13 @@ def peaks():
     return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0, "source": "fallback"}
 
 
+def fp32_peak(pk, torch):
+    """FP32 FMA peak of GPU 0 in TFLOP/s: SMs (from the device) x 128 lanes x 2 flop
+    x the maximum SM clock."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    return n_sm * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12, n_sm
+
+
 def profiled_traffic(summary):
     """DRAM bytes per launch from a profiles/ summary, or None when the kernel
     sources have changed since the counters were taken."""
@@ -346,7 +353,7 @@ def bench_dpd_large(args, P, torch, pk, ws):
     samples = nb * Lb
     body_avg = body_ms / max(body_n, 1)
     flops = dpd_flops(w.masks, w.n_taps, Lb)
-    peak_tf = 148 * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    peak_tf, n_sm = fp32_peak(pk, torch)
     achieved_tf = flops / (body_avg / 1e3) / 1e12
     hbm_gbs = 16.0 * samples / (body_avg / 1e3) / 1e9
     # e2e through the C ABI from pinned host memory (blocks in, blocks out)
@@ -372,7 +379,7 @@ def bench_dpd_large(args, P, torch, pk, ws):
                      "traffic": profiled_traffic("k_dpd_body__dpd_large_512x1048576.md") if nb == 512 else None,
                      "kernel": "k_dpd_body",
                      "algorithmic_flops_per_launch": flops,
-                     "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
+                     "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
                      "hbm": {"achieved": hbm_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                              "frac": hbm_gbs / pk["hbm_gbs"], "bytes_per_sample": 16}},
         "e2e": {"value": ws * samples / e2e_s / 1e6, "unit": "Msamples/s",
@@ -673,7 +680,7 @@ def bench_dpd_batch(args, P, torch, pk):
     samples = int(w.lengths.sum()) * nb
     flops = float(sum(8 * int(w.taps[c]) * int(w.lengths[c]) * nb * bin(int(w.masks[c])).count("1")
                       for c in range(C)))
-    peak_tf = 148 * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    peak_tf, _ = fp32_peak(pk, torch)
     ach = flops / (body_ms / 1e3) / 1e12
     # oracle on the first four channels
     from oracle import nets as ON

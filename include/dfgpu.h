@@ -112,7 +112,8 @@ typedef struct {
  * outside the frame count as set) then a 3x3 dilation (outside counts as
  * clear); for every 16x16 tile (raster order, partial last tile row allowed)
  * with count > 0 one 8-byte record {u16 x, u16 y, u32 count} is emitted, x/y
- * being the tile's top-left pixel.  width must be a multiple of 32. */
+ * being the tile's top-left pixel.  width must be a multiple of 32 and tile
+ * 16: other valid sizes return DF_ENOTSUP from df_actor_add. */
 typedef struct {
     int32_t width;
     int32_t height;
@@ -121,7 +122,8 @@ typedef struct {
 } df_md_params;
 
 /* Image-actor parameters (DF_GAUSS5, DF_THRES, DF_MED5).  width must be a
- * multiple of 16 and at most 2048; threshold (DF_THRES) in 0..255. */
+ * multiple of 16 and at most 2048 (other widths return DF_ENOTSUP from
+ * df_actor_add); threshold (DF_THRES) in 0..255. */
 typedef struct {
     int32_t width;
     int32_t height;
@@ -132,15 +134,24 @@ typedef struct df_net df_net;
 
 /* Create an empty network on `device`.  `cuda_stream` is a cudaStream_t the
  * network will use for all its work (NULL: the network creates and owns a
- * non-blocking stream).  *out receives the handle. */
+ * non-blocking stream).  *out receives the handle.
+ * Defined by: Sec. 2.2 (a network is a set of actors and a set of FIFO
+ * channels) and Sec. 3.4 (the application declares its network through the
+ * framework's C library). */
 df_status df_net_create(df_net **out, int device, void *cuda_stream);
 
-/* Free every resource of the network (NULL-safe).  Waits for its stream. */
+/* Free every resource of the network (NULL-safe).  Waits for its stream.
+ * Defined by: Sec. 3.3 (the framework's threads and buffers live from the
+ * start of the application to its end). */
 void df_net_destroy(df_net *net);
 
 /* Add an actor of `kind` with kind-specific `params` (copied).  Returns its
  * id in *out_id; ids are dense and give the step order (Sec. 3.3 leaves the
- * schedule to the OS; this engine fixes it to insertion order). */
+ * schedule to the OS; this engine fixes it to insertion order).
+ * Defined by: Sec. 2.2 (static actors, dynamic actors with a control port)
+ * and Sec. 3.1 (an actor's init, fire and control functions: init is this
+ * call, fire and control run on the device); the actor kinds are those of
+ * Sec. 4.1 and Sec. 4.2. */
 df_status df_actor_add(df_net *net, int32_t kind, const void *params, size_t params_bytes,
                        int32_t *out_id);
 
@@ -164,7 +175,9 @@ df_status df_actor_add(df_net *net, int32_t kind, const void *params, size_t par
  * not yet read.  Pushes into it write whole windows (n_tokens a multiple of
  * r, else DF_EINVAL).  initial_tokens must be 0 or 1 (the paper gives the pattern
  * for one delay token) and the writer must be a host source or an actor of a
- * fixed token rate per firing (not the output of DF_MD); else DF_EINVAL. */
+ * fixed token rate per firing (not the output of DF_MD); else DF_EINVAL.
+ * Defined by: Sec. 2.2 (order-preserving FIFO between one output and one input
+ * port, token rate, initial tokens), Sec. 3.2 (capacity, Eq. 1, Fig. 2). */
 #define DF_CAPACITY_EQ1 0u
 df_status df_channel_connect(df_net *net, int32_t src_actor, int32_t src_port,
                              int32_t dst_actor, int32_t dst_port, uint32_t token_bytes,
@@ -173,18 +186,28 @@ df_status df_channel_connect(df_net *net, int32_t src_actor, int32_t src_port,
 
 /* Validate (ports connected exactly once and numbered densely, rates and token
  * sizes consistent with each actor kind), plan and allocate device memory.
- * The network is frozen afterwards. */
+ * The network is frozen afterwards.
+ * Defined by: Sec. 2.2 (control channels have rate 1 and no initial tokens;
+ * one channel per port) and Sec. 3.2 (every buffer is allocated before the
+ * actors start, at its fixed size). */
 df_status df_net_finalize(df_net *net);
 
 /* Copy n_tokens tokens (n_tokens*token_bytes bytes at `src`, host or device
  * memory) into every output channel of source actor `src_actor`.
- * All-or-nothing: DF_EFULL when any channel lacks space (nothing written). */
+ * All-or-nothing: DF_EFULL when any channel lacks space (nothing written).
+ * Defined by: Sec. 3.3 and Sec. 4 (host-side source actors feed the network:
+ * video frames read by the CPU, predistorter input blocks); a write that lacks
+ * space is refused here instead of blocking as in Sec. 3.3. */
 df_status df_push(df_net *net, int32_t src_actor, const void *src, uint64_t n_tokens,
                   uint64_t *n_pushed);
 
 /* Run n_steps steps (n_steps < 0: until a step fires nothing, at most 2^20
  * steps, else DF_EDEADLOCK).  Blocks until the device work is done, then
- * reports the device status word and, if non-NULL, the number of firings. */
+ * reports the device status word and, if non-NULL, the number of firings.
+ * Defined by: Sec. 2.2 (the firing rule of a dynamic actor: read one control
+ * token, fix the port rates, consume, compute, produce), with Sec. 3.3's free-
+ * running actor threads read as steps: each step fires every actor, in
+ * insertion order, while it is enabled. */
 df_status df_run(df_net *net, int64_t n_steps, uint64_t *n_firings);
 
 /* Run flags for df_run_ex. */
@@ -196,14 +219,20 @@ enum {
                                 barrier bounded by the wait limit (df_set_wait_limit) */
     DF_RUN_NO_BATCH = 8      /* one launch per predistorter actor instead of one per group */
 };
+/* df_run with flags.  Defined by: Sec. 2.2 as df_run; the flags choose how the
+ * steps are launched (Sec. 3.3's contrast: no host round trip per firing). */
 df_status df_run_ex(df_net *net, int64_t n_steps, uint32_t flags, uint64_t *n_firings);
 
 /* Wait for the network's stream and return the device status word (DF_OK or
- * the first device-side error) and the total number of firings so far. */
+ * the first device-side error) and the total number of firings so far.
+ * Defined by: Sec. 3.3 (the host learns of the GPU actors' progress); the
+ * firing count is the Sec. 2.2 firing counted on the device. */
 df_status df_sync(df_net *net, uint64_t *total_firings);
 
 /* Copy up to max_tokens tokens from the input channel of sink `sink_actor`
- * into `dst` (host or device memory).  Blocks until the copy is done. */
+ * into `dst` (host or device memory).  Blocks until the copy is done.
+ * Defined by: Sec. 3.3 and Sec. 4 (host-side sink actors consume the
+ * network's output). */
 df_status df_pop(df_net *net, int32_t sink_actor, void *dst, uint64_t max_tokens,
                  uint64_t *n_popped);
 
@@ -219,7 +248,9 @@ df_status df_pop(df_net *net, int32_t sink_actor, void *dst, uint64_t max_tokens
  * with the flag may run concurrently with df_run, df_sync and each other
  * (different sources and sinks from different threads).  df_push/df_pop and
  * df_channel_counters stay on the network's stream and belong to the thread
- * that runs it. */
+ * that runs it.
+ * Defined by: Sec. 3.3 (every actor a thread of its own, host and GPU actors
+ * running concurrently) and Sec. 1 (concurrent CPU and GPU actors). */
 enum { DF_IO_CONCURRENT = 1 };
 df_status df_push_ex(df_net *net, int32_t src_actor, const void *src, uint64_t n_tokens,
                      uint32_t flags, uint64_t *n_pushed);
@@ -239,7 +270,9 @@ df_status df_pop_ex(df_net *net, int32_t sink_actor, void *dst, uint64_t max_tok
  * tokens popped (a drain also stops when max_tokens are in).  When nothing
  * moves (no firing, push or pop) for idle_limit_ns (<= 0: 2 s) the run stops
  * with DF_EDEADLOCK, e.g. when an undrained sink is full.  Feed data may be
- * host (pinned for full speed) or device memory, as for df_push. */
+ * host (pinned for full speed) or device memory, as for df_push.
+ * Defined by: Sec. 3.3 (one OS thread per actor, blocking FIFO reads and
+ * writes) for the host actors; the GPU actors run as df_run. */
 typedef struct {
     int32_t source;          /* DF_SOURCE actor */
     const void *data;        /* n_tokens tokens */
@@ -257,7 +290,9 @@ df_status df_stream(df_net *net, const df_feed *feeds, int32_t n_feeds, df_drain
                     int32_t n_drains, uint32_t run_flags, int64_t idle_limit_ns, uint64_t *n_steps);
 
 /* Counters of channel `ch`: tokens produced (excluding initial tokens),
- * consumed, and currently held.  produced + initial == consumed + occupancy. */
+ * consumed, and currently held.  produced + initial == consumed + occupancy.
+ * Defined by: Sec. 2.2 (a FIFO channel delivers the tokens written to it, in
+ * order, plus its initial tokens). */
 df_status df_channel_counters(df_net *net, int32_t ch, uint64_t *produced, uint64_t *consumed,
                               uint64_t *occupancy);
 
@@ -265,7 +300,7 @@ df_status df_channel_counters(df_net *net, int32_t ch, uint64_t *produced, uint6
  * hold; slots = buffer slots allocated (capacity, or capacity + 1 for a
  * delay channel in the paper's layout); buffer_bytes = slots * token_bytes;
  * layout = DF_LAYOUT_RING or DF_LAYOUT_EQ1.  Valid before and after
- * finalize. */
+ * finalize.  Defined by: Sec. 3.2 (Eq. 1) and Table 1 (buffer memory). */
 enum { DF_LAYOUT_RING = 0, DF_LAYOUT_EQ1 = 1 };
 typedef struct {
     uint64_t capacity;
@@ -281,28 +316,33 @@ df_status df_channel_info(df_net *net, int32_t ch, df_channel_info_t *out);
 /* Copy n_slots raw buffer slots of channel `ch`, starting at slot first_slot,
  * to `dst` (host), whatever tokens they hold: the physical layout (ring or
  * Fig. 2) made visible for inspection.  Runs on the network's stream and
- * blocks; DF_EINVAL when the range exceeds the slots of the channel. */
+ * blocks; DF_EINVAL when the range exceeds the slots of the channel.
+ * Defined by: Sec. 3.2 and Fig. 2 (the slots of the double and triple buffer). */
 df_status df_channel_peek_slots(df_net *net, int32_t ch, uint64_t first_slot, uint64_t n_slots,
                                 void *dst);
 
 /* Tile configuration of the predistorter kernel for one actor (0 = default):
  * samples per tile and threads per CTA (32, 64, 128 or 256; 8 or 16 samples
- * per thread, else DF_EINVAL).  The autotuner sets these. */
+ * per thread, else DF_EINVAL).  The autotuner sets these.
+ * The paper has no counterpart: a launch parameter of this engine's kernel
+ * for the Sec. 4.2 predistorter. */
 df_status df_dpd_set_tile(df_net *net, int32_t actor, uint32_t tile, uint32_t threads);
 
 /* Time every supported tile configuration on the network's current pending
  * predistorter work (the firings a step would take now) and keep the fastest
- * for every DF_DPD actor / group.  Runs one step; returns its firings. */
+ * for every DF_DPD actor / group.  Runs one step; returns its firings.
+ * The paper has no counterpart (the tile autotuner of this engine). */
 df_status df_autotune(df_net *net, uint64_t *n_firings);
 
 /* The tile configuration an actor (the first actor of a batched group) uses;
- * 0/0 = the default. */
+ * 0/0 = the default.  The paper has no counterpart. */
 df_status df_dpd_get_tile(df_net *net, int32_t actor, uint32_t *tile, uint32_t *threads);
 
 /* Kernel timing.  While enabled, every non-graph step records CUDA events on
  * the network's stream around the kernels named below; df_profile_get waits
  * for the stream and returns their summed device time (ms) and launch count
- * since the last enable.  Graph replays (DF_RUN_GRAPH) are not timed. */
+ * since the last enable.  Graph replays (DF_RUN_GRAPH) are not timed.
+ * The paper has no counterpart (measurement of this engine's kernels). */
 enum {
     DF_PROF_STEP = 0,        /* one whole step (every launch of the step) */
     DF_PROF_DPD_BODY = 1,    /* predistorter body launches */
@@ -314,20 +354,22 @@ df_status df_profile_get(df_net *net, int32_t what, double *total_ms, uint64_t *
 
 /* Upper bound, in nanoseconds, of every device-side wait of the network (the
  * persistent kernel's grid barrier); default one second.  A wait that runs out
- * records DF_ETIMEOUT in the status word and the kernel returns. */
+ * records DF_ETIMEOUT in the status word and the kernel returns.
+ * The paper has no counterpart (its actors block on mutexes, Sec. 3.3). */
 df_status df_set_wait_limit(df_net *net, int64_t limit_ns);
 
 /* Self-test of the bounded waits: runs a grid barrier that waits for one more
  * CTA than it has, so it can only end by its limit.  Returns the status word
  * that run left (DF_ETIMEOUT when the bound works), then clears it so the
- * network stays usable. */
+ * network stays usable.  The paper has no counterpart. */
 df_status df_selftest_wait_timeout(df_net *net, int64_t limit_ns);
 
-/* Text for a status code (static storage). */
+/* Text for a status code (static storage).  The paper has no counterpart. */
 const char *df_status_str(df_status s);
 
 /* The failing CUDA call and its error string behind the calling thread's most
- * recent DF_ECUDA (empty if none); valid until the thread's next failure. */
+ * recent DF_ECUDA (empty if none); valid until the thread's next failure.
+ * The paper has no counterpart. */
 const char *df_last_error(void);
 
 /* ---------------------------------------------------------------------------
@@ -336,6 +378,11 @@ const char *df_last_error(void);
  *   y[t] = sum_k sum_{m<M} h[k,m] z_k[t-m],  z_k = |x|^(orders[k]-1) x,  z_k[<0] = 0.
  * x, y: n complex64; h: K*M complex64 (device); orders: host array of K ints.
  * ------------------------------------------------------------------------- */
+/* Defined by: Sec. 4.2 (the predistorter: a Poly actor feeding parallel
+ * FIR filters whose outputs an Adder sums), with every branch active on one
+ * signal.  The paper does not print the branch function; it is read as the
+ * memory-polynomial branch z_k above, with odd orders.  This is the form the
+ * differentiable fit drives (indirect learning of the taps). */
 df_status df_dpd_forward(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
                          const int32_t *orders, void *y, void *cuda_stream);
 
@@ -346,11 +393,42 @@ df_status df_dpd_forward(const void *x, uint64_t n, const void *h, int32_t K, in
  *   grad_x[j]   = sum_k (q_k+1) u^q_k gz_k[j] + q_k u^(q_k-1) x^2 conj(gz_k[j]),
  *                 u = |x[j]|^2, q_k = (orders[k]-1)/2.
  * grad_x may be NULL.  The z_k are recomputed from x, not stored.  grad_h is
- * reduced deterministically (fixed-order two-level sum).  Uses a scratch
- * buffer the library allocates once per device and grows on demand. */
+ * reduced deterministically (fixed-order two-level sum).
+ * Scratch: the tap-gradient partial sums live in a buffer the library
+ * allocates per (device, stream) and grows on demand; a buffer is never freed
+ * while the process runs (a grown one is retired, not released), so CUDA
+ * graphs that captured an earlier call stay valid.  Calls on the same stream
+ * are ordered by that stream; calls on different streams use different
+ * buffers.  A call that would have to grow the buffer while its stream is
+ * being captured returns DF_ESTATE (make one call of that size or larger
+ * before capturing).  A graph captured from a call uses the buffer of the
+ * stream it was captured on: replay it on that stream, or make sure no call
+ * on that stream overlaps the replay.
+ * Defined by: the adjoint of the Sec. 4.2 predistorter (df_dpd_forward); the
+ * paper has no gradient, it is what fits the taps. */
 df_status df_dpd_backward(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
                           const int32_t *orders, const void *grad_y, void *grad_x, void *grad_h,
                           void *cuda_stream);
+
+/* Scratch of the adjoint for callers that provide it: the number of complex64
+ * elements df_dpd_backward_scratch needs for n samples, K branches and M taps
+ * (ceil(n/1024) * K * MT, at least 1; MT = M rounded up to 4, 8, M for 9..16,
+ * or 32); 0 for K or M out of range.
+ * Defined by: the adjoint of the Sec. 4.2 predistorter, as df_dpd_backward;
+ * the scratch itself has no counterpart in the paper. */
+uint64_t df_dpd_backward_scratch_elems(uint64_t n, int32_t K, int32_t M);
+
+/* df_dpd_backward with the tap-gradient partial sums in `scratch` (device
+ * memory of at least df_dpd_backward_scratch_elems(n, K, M) complex64
+ * elements, owned by the caller, else DF_EINVAL).  The call allocates
+ * nothing, so it may be captured in a CUDA graph when the caller's allocator
+ * is graph-aware (the torch binding passes a torch tensor).  Calls that
+ * overlap on the GPU need different scratch buffers.
+ * Defined by: the adjoint of the Sec. 4.2 predistorter (df_dpd_forward). */
+df_status df_dpd_backward_scratch(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                                  const int32_t *orders, const void *grad_y, void *grad_x,
+                                  void *grad_h, void *scratch, uint64_t scratch_elems,
+                                  void *cuda_stream);
 
 /* Same computation and results as df_dpd_backward, but it allocates nothing.
  * (The paper has no counterpart; this exists for callers that may not
@@ -360,9 +438,10 @@ df_status df_dpd_backward(const void *x, uint64_t n, const void *h, int32_t K, i
  * the library image: 131072 complex values (1 MiB) that every GPU loading the
  * library keeps until the process exits.  A call needs ceil(n/1024) * K * MT
  * of them (MT = M rounded up to 4, 8, M for 9..16, or 32); larger calls
- * return DF_ENOTSUP and do nothing.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the one
+ * return DF_ENOTSUP and do nothing.  Every call looks up the array's device
+ * address (cudaGetSymbolAddress) on the current device; the first lookup on a
+ * device may load the library's device code, so make the first call on each
+ * device before any stream capture.  All calls share the one
  * array, so calls whose kernels overlap on the GPU (other streams, other
  * threads) race and must be serialised by the caller.  Each call rewrites
  * every partial sum it reads, so nothing is carried over between calls. */

@@ -229,6 +229,7 @@ struct PersistOp {            // one entry of the device-side step program
   int kind;
   int n;                      // predistorter group size
   const void* args;           // CopyArgs / DpdArgs[n] / DynArgs / MdArgs / ImgArgs / SpillArgs[n]
+  const uint16_t* order;      // predistorter group: the body's actor order
 };
 
 // --------------------------------------- programmatic dependent launch ----
@@ -267,7 +268,7 @@ cudaError_t launch_copy(const CopyArgs& a, int n_sm, cudaStream_t s, cudaEvent_t
                         cudaEvent_t ev1 = nullptr);
 
 cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t s, bool pdl = false);
-cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile,
+cudaError_t launch_dpd_body(const DpdArgs* args_dev, const uint16_t* order, int n_actors, uint32_t tile,
                             uint32_t threads, int max_mt, int n_sm, cudaStream_t s, bool pdl = false);
 int dpd_supported_mt(int M);   // padded tap count used for M (0 = unsupported)
 cudaError_t dpd_prepare();     // one-time kernel attributes (outside graph capture)

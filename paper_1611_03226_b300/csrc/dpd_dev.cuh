@@ -53,6 +53,16 @@ __device__ __forceinline__ float2 psi_q(float2 x, int q) {
   return make_float2(p * x.x, p * x.y);
 }
 
+// u^q for a runtime q, by squaring
+__device__ __forceinline__ float upow(float u, int q) {
+  float p = (q & 1) ? u : 1.f;
+  for (int e = q >> 1; e; e >>= 1) {
+    u *= u;
+    if (e & 1) p *= u;
+  }
+  return p;
+}
+
 // ---------------------------------------------------------------- scans ----
 __device__ inline uint64_t block_exclusive_scan_u64(uint64_t v, uint64_t* sw, uint64_t* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -168,48 +178,6 @@ __device__ __forceinline__ void fir_branch(float2 (&acc)[R], const float2* zs, i
   }
 }
 
-// Packed form for the body kernel: two-lane FMAs (one instruction updates
-// the real and imaginary parts).  With taps staged as {hx, hx, hy, hy}, the
-// output is split into A = sum hx * z and B = sum hy * z (both lanes of z), so
-// that every product has the same tap value in both lanes; the complex result
-// is (A.x - B.y, A.y + B.x), formed once after all branches.
-template <int R, int MC>
-__device__ __forceinline__ void fir_causal_x2(float2 (&A)[R], float2 (&B)[R], const float2* __restrict__ zs,
-                                              int p, int shift, const float4* __restrict__ h4,
-                                              int m_valid) {
-  float2 hxx[MC], hyy[MC];
-#pragma unroll
-  for (int m = 0; m < MC; ++m) {
-    const float4 t = m < m_valid ? h4[m] : make_float4(0.f, 0.f, 0.f, 0.f);
-    hxx[m] = make_float2(t.x, t.y);
-    hyy[m] = make_float2(t.z, t.w);
-  }
-  const float2* zb = zs + p * (R + 1) + shift + shift / R;
-#pragma unroll
-  for (int s = 0; s < R + MC - 1; ++s) {
-    const float2 z = zb[s + s / R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int m = r + MC - 1 - s;
-      if (m >= 0 && m < MC) {
-        A[r] = __ffma2_rn(hxx[m], z, A[r]);
-        B[r] = __ffma2_rn(hyy[m], z, B[r]);
-      }
-    }
-  }
-}
-
-template <int R, int MT>
-__device__ __forceinline__ void fir_branch_x2(float2 (&A)[R], float2 (&B)[R], const float2* zs, int p,
-                                              const float4* h4, int M) {
-  if constexpr (MT <= 16) {
-    fir_causal_x2<R, MT>(A, B, zs, p, 0, h4, M);
-  } else {
-    fir_causal_x2<R, 16>(A, B, zs, p, 16, h4, M);
-    fir_causal_x2<R, 16>(A, B, zs, p, 0, h4 + 16, M - 16);
-  }
-}
-
 #define DPD_MT_CASES(X) X(4) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(32)
 
 // ----------------------------------------------------------------- plan ----
@@ -286,6 +254,26 @@ __device__ inline void dpd_plan_dev(const DpdArgs& a) {
 }
 
 // ----------------------------------------------------------------- body ----
+// The body is warp-granular: a work item is (actor, firing, chunk of 32 * R
+// consecutive output samples of the block), and every warp walks its own
+// items with its own shared memory, so no barrier spans more than one warp
+// after the kernel's start.  Items are dealt to warps interleaved across the
+// CTAs of the grid (warp w of CTA b is global warp w * gridDim + b), so
+// neighbouring chunks run on different SMs at the same time.
+//
+// Per item: the x window x[t0 - (MT-1) .. t0 + 32R) of the block (zeros
+// outside it) is staged by cp.async into one half of a double buffer while
+// the previous item computes.  Per active branch k, in ascending k:
+//   z-pass: lane l forms z = |x|^(o_k - 1) x for window positions l, l + 32,
+//           ..., stored as {zx, zx, zy, zy} (the first MT-1 positions of a
+//           block's first chunk come from branch k's own history instead:
+//           the previous block in which k was active, or the persisted
+//           history);
+//   FIR:    lane l accumulates outputs l*R .. l*R + R-1 with the taps
+//           {hx, hy} of branch k in registers, two-lane FMAs
+//           P += {hx, hy} * {zx, zx} and Q += {hx, hy} * {zy, zy}, so that
+//           y = (P.x - Q.y, P.y + Q.x) is the complex sum over taps and
+//           branches (the Adder), formed once at the end.
 __device__ __forceinline__ float2 hist_sample(const DpdArgs& a, const DpdPlanHdr& pl, uint32_t i,
                                               int k, int s) {
   const int H1 = a.MT - 1;
@@ -295,22 +283,6 @@ __device__ __forceinline__ float2 hist_sample(const DpdArgs& a, const DpdPlanHdr
     return reinterpret_cast<const float2*>(slot_ptr(a.data, pl.rd_data0 + f))[pos % a.L];
   }
   return a.hist[((size_t)pl.parity_in * a.K + k) * H1 + (H1 + pos)];
-}
-
-constexpr int kBranchGroup = 1;           // branch signals staged at once
-
-// u^q from the squares u, u^2, u^4, u^8 (q < 16), else by repeated products.
-__device__ __forceinline__ float pow_sq(float u, float u2, float u4, float u8, int q) {
-  if (q >= 16) {
-    float p = 1.f;
-    for (int i = 0; i < q; ++i) p *= u;
-    return p;
-  }
-  float p = (q & 1) ? u : 1.f;
-  if (q & 2) p *= u2;
-  if (q & 4) p *= u4;
-  if (q & 8) p *= u8;
-  return p;
 }
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
@@ -328,207 +300,293 @@ __device__ __forceinline__ const uint8_t* slot_at(const ChanDesc& c, uint64_t sl
   return c.ring + s * c.tok;
 }
 
-struct ItemRef {
-  int g;                    // actor within the group, -1 = none
-  uint32_t i;               // firing
-  uint32_t t0;              // first sample of the tile
-  int len;                  // samples of the tile inside the block
+// Shared memory of one warp (R outputs per lane, taps padded to at most MTMAX):
+//   xw[2][XW] float2  x window, double buffered (XW >= 32 (R + 1) and >= 32R + MTMAX - 1, even)
+//   zw[ZW]    float4  branch signal {zx, zx, zy, zy}; position v at v + v / R,
+//                     so that lanes reading at a stride of R positions hit
+//                     distinct banks
+//   hw[kMaxBranches * MTMAX + 2] float2  taps {hx, hy} of the warp's current
+//                     actor, then one byte per branch: q = (order - 1) / 2
+template <int R, int MTMAX>
+struct WarpSmem {
+  static constexpr int XW = 32 * (R + 1) > 32 * R + MTMAX - 1 ? 32 * (R + 1) : ((32 * R + MTMAX) & ~1);
+  static constexpr int ZW = XW + XW / R + 1;
+  static constexpr size_t x_bytes = 2 * (size_t)XW * sizeof(float2);
+  static constexpr size_t z_bytes = (size_t)ZW * sizeof(float4);
+  static constexpr size_t h_bytes = ((size_t)kMaxBranches * MTMAX + 2) * sizeof(float2);
+  static constexpr size_t bytes = x_bytes + z_bytes + h_bytes;
 };
 
-__device__ __forceinline__ ItemRef locate(const DpdArgs* args, const uint64_t* s_off, int G,
-                                          uint64_t item, uint64_t total, uint32_t T) {
-  ItemRef r{-1, 0, 0, 0};
+// Bytes before the per-warp areas: the work-list offsets of G actors and
+// their visiting order.
+__host__ __device__ constexpr size_t dpd_body_off_bytes(int G) {
+  return ((size_t)(G + 1) * sizeof(uint64_t) + (size_t)G * sizeof(uint16_t) + 15) & ~(size_t)15;
+}
+
+template <int R, int MTMAX>
+__host__ __device__ constexpr size_t dpd_body_smem(int warps, int G) {
+  return dpd_body_off_bytes(G) + (size_t)warps * WarpSmem<R, MTMAX>::bytes;
+}
+
+struct WItem {
+  int g;                    // actor within the group, -1 = none
+  uint32_t i;               // firing
+  uint32_t t0;              // first sample of the chunk
+  int len;                  // samples of the chunk inside the block
+};
+
+__device__ __forceinline__ WItem locate_w(const DpdArgs* args, const uint64_t* s_off, const uint16_t* s_ord,
+                                          int G, uint64_t item, uint64_t total, uint32_t WI) {
+  WItem r{-1, 0, 0, 0};
   if (item >= total) return r;
   int lo = 0, hi = G;                     // s_off[lo] <= item < s_off[hi]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (s_off[mid] <= item) lo = mid; else hi = mid;
   }
-  const DpdArgs& a = args[lo];
+  const int g = s_ord[lo];
+  const DpdArgs& a = args[g];
   const uint64_t local = item - s_off[lo];
-  const uint32_t nt = (a.L + T - 1) / T;
-  r.g = lo;
-  r.i = (uint32_t)(local / nt);
-  r.t0 = (uint32_t)(local % nt) * T;
-  r.len = (int)min(T, a.L - r.t0);
+  const uint32_t nt = (a.L + WI - 1) / WI;
+  r.g = g;
+  if (local < 0xffffffffull) {
+    const uint32_t l32 = (uint32_t)local;
+    r.i = l32 / nt;
+    r.t0 = (l32 - r.i * nt) * WI;
+  } else {
+    r.i = (uint32_t)(local / nt);
+    r.t0 = (uint32_t)(local % nt) * WI;
+  }
+  r.len = (int)min(WI, a.L - r.t0);
   return r;
 }
 
-// Copy the x window of `it` (x[t0 - (MT-1) .. t0 + T), zeros outside the block) into xs.
-__device__ __forceinline__ void prefetch_x(const DpdArgs& a, const ItemRef& it, float2* xs, uint32_t T) {
+// Stage the x window of `it` into xs: position v holds sample t0 - (MT-1) + v
+// of the block, zero outside [0, t0 + len).
+__device__ __forceinline__ void prefetch_w(const DpdArgs& a, const WItem& it, float2* xs, uint32_t WI,
+                                           int lane) {
   const DpdPlanHdr* pl = a.plan;
-  const float2* xb = reinterpret_cast<const float2*>(slot_at(a.data, pl->slot_data0, it.i)) + it.t0;
-  const int MT = a.MT;
-  const int W = (int)T + MT - 1;
-  for (int v = threadIdx.x; v < W; v += blockDim.x) {
-    const int pos = v - (MT - 1);
-    const bool valid = pos < it.len && (int)it.t0 + pos >= 0;
+  const float2* xb = reinterpret_cast<const float2*>(slot_at(a.data, pl->slot_data0, it.i));
+  const int H1 = a.MT - 1;
+  const int W = (int)WI + H1;
+  const int end = (int)it.t0 + it.len;
+  for (int v = lane; v < W; v += 32) {
+    const int pos = (int)it.t0 - H1 + v;
+    const bool valid = pos >= 0 && pos < end;
     cp_async8(xs + v, valid ? (const void*)(xb + pos) : (const void*)xb, valid);
   }
 }
 
-// u^Q by a fixed multiplication chain (Q known at compile time).
-template <int Q>
-__device__ __forceinline__ float pow_c(float u) {
-  if constexpr (Q == 0) {
-    return 1.f;
-  } else if constexpr (Q == 1) {
-    return u;
-  } else if constexpr (Q % 2 == 0) {
-    const float h = pow_c<Q / 2>(u);
-    return h * h;
-  } else {
-    return pow_c<Q - 1>(u) * u;
-  }
+__device__ __forceinline__ void zstore(float4* zw, int v, int R, float2 x, float p) {
+  const float zx = p * x.x, zy = p * x.y;
+  zw[v + v / R] = make_float4(zx, zx, zy, zy);
 }
 
-// zg[v + v/R] = |x_v|^(2Q) x_v for the window v < W (padded layout).
-template <int R, int Q>
-__device__ __forceinline__ void zpass(const float2* __restrict__ xs, float2* __restrict__ zg, int W) {
-  const int P = blockDim.x;
-#pragma unroll 4
-  for (int v = threadIdx.x; v < W; v += P) {
-    const float2 x = xs[v];
-    const float pw = pow_c<Q>(fmaf(x.x, x.x, x.y * x.y));
-    zg[v + v / R] = make_float2(pw * x.x, pw * x.y);
-  }
-}
-
+// z = u^Q x over the window positions lane, lane + 32, ... < W (W <= 32 (R+1)).
+// Position lane + 32 j of the padded buffer sits at lane + lane / R + j (32 + 32 / R)
+// (R divides 32), so every access is a fixed offset from one per-lane base.
+// z = u^q x over all 32 (R + 1) window positions lane, lane + 32, ...; the x
+// and z buffers hold that many, positions >= W hold stale x and are never
+// read by the FIR, so the pass is straight-line code: all loads, then the
+// arithmetic, then all stores.  Position lane + 32 j of the padded z buffer
+// sits at lane + lane / R + j (32 + 32 / R) (R divides 32): fixed offsets from
+// one per-lane base.  u^q is assembled from u, u^2 and u^4 by the bits of q
+// (q < 8, orders up to 15), by repeated products otherwise.
 template <int R>
-__device__ inline void zpass_any(const float2* __restrict__ xs, float2* __restrict__ zg, int W, int q) {
-  for (int v = threadIdx.x; v < W; v += blockDim.x) zg[v + v / R] = psi_q(xs[v], q);
+__device__ __forceinline__ void zpass_w(const float2* __restrict__ xs, float4* __restrict__ zw, int lane, int q) {
+  const float2* xb = xs + lane;
+  float4* zb = zw + lane + lane / R;
+  float2 x[R + 1];
+#pragma unroll
+  for (int j = 0; j <= R; ++j) x[j] = xb[32 * j];
+  float p[R + 1];
+  if (q < 8) {
+#pragma unroll
+    for (int j = 0; j <= R; ++j) {
+      const float u = fmaf(x[j].x, x[j].x, x[j].y * x[j].y);
+      const float u2 = u * u;
+      float v = (q & 1) ? u : 1.f;
+      if (q & 2) v *= u2;
+      if (q & 4) v *= u2 * u2;
+      p[j] = v;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j <= R; ++j) {
+      const float u = fmaf(x[j].x, x[j].x, x[j].y * x[j].y);
+      float v = 1.f;
+      for (int e = 0; e < q; ++e) v *= u;
+      p[j] = v;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j <= R; ++j) {
+    const float zx = p[j] * x[j].x, zy = p[j] * x[j].y;
+    zb[j * (32 + 32 / R)] = make_float4(zx, zx, zy, zy);
+  }
 }
 
-// Shared memory of one body CTA (T = R * blockDim.x samples per tile, W = T + MTmax - 1):
-//   xs[2][W] float2 | zb[kBranchGroup][Wp] float2 (Wp = W + W / R + 2) |
-//   hs[kMaxBranches * MTmax] float4 {hx, hx, hy, hy}
+// Two-lane FP32 FMA on 64-bit registers holding a pair of floats (element 0 in
+// the low half): d = a * b + d elementwise.  Keeping the operands in 64-bit
+// registers end to end means no register pairs have to be formed around the
+// instruction.
+__device__ __forceinline__ void ffma2_b64(unsigned long long& d, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ float2 unpack_b64(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
+// One branch's FIR into the accumulators of this lane's R outputs:
+// P[r] += {hx, hy} * {zx, zx}, Q[r] += {hx, hy} * {zy, zy} over the MT taps.
 template <int R, int MT>
-__device__ inline void dpd_compute(const DpdArgs& a, const ItemRef& it, const float2* xs, float2* zb,
-                            int Wp, const float4* hs, int* s_k, int* s_q) {
-  const int P = blockDim.x, p = threadIdx.x;
-  const uint32_t T = R * P;
+__device__ __forceinline__ void fir_w(unsigned long long (&P)[R], unsigned long long (&Q)[R],
+                                      const float4* __restrict__ zw, int lane, const float2* __restrict__ hk) {
+  unsigned long long h[MT];
+  const unsigned long long* hk64 = reinterpret_cast<const unsigned long long*>(hk);
+#pragma unroll
+  for (int m = 0; m < MT; ++m) h[m] = hk64[m];
+  const ulonglong2* zb = reinterpret_cast<const ulonglong2*>(zw) + lane * (R + 1);
+#pragma unroll
+  for (int s = 0; s < R + MT - 1; ++s) {
+    const ulonglong2 z = zb[s + s / R];        // {zx, zx}, {zy, zy}
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = r + MT - 1 - s;
+      if (m >= 0 && m < MT) {
+        ffma2_b64(P[r], h[m], z.x);
+        ffma2_b64(Q[r], h[m], z.y);
+      }
+    }
+  }
+}
+
+// Outputs o = lane*R + r of the chunk (o < len) at yb.
+template <int R>
+__device__ __forceinline__ void store_w(float2* yb, int len, int lane, const float2 (&y)[R]) {
+  const int o0 = lane * R;
+  if (len == 32 * R && (reinterpret_cast<uintptr_t>(yb) & 15) == 0) {
+#pragma unroll
+    for (int r = 0; r < R; r += 2)
+      *reinterpret_cast<float4*>(yb + o0 + r) = make_float4(y[r].x, y[r].y, y[r + 1].x, y[r + 1].y);
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (o0 + r < len) yb[o0 + r] = y[r];
+  }
+}
+
+template <int R, int MT>
+__device__ __noinline__ void dpd_item_w(const DpdArgs& a, const WItem& it, const float2* xs, float4* zw,
+                                        const float2* hw, int lane) {
   const DpdPlanHdr& pl = *a.plan;
   const uint32_t mask = a.masks[it.i];
   float2* yb = reinterpret_cast<float2*>(const_cast<uint8_t*>(slot_at(a.out, pl.slot_out0, it.i))) + it.t0;
-  if (mask == 0) {
-    for (int o = p; o < it.len; o += P) yb[o] = make_float2(0.f, 0.f);
-    return;
-  }
-  const int W = (int)T + MT - 1;
-  int nk = 0;
-  {
-    uint32_t rest = mask;
-    while (rest) {
-      const int k = __ffs(rest) - 1;
-      rest &= rest - 1;
-      if (p == 0) {
-        s_k[nk] = k;
-        s_q[nk] = (a.orders[k] - 1) >> 1;
-      }
-      ++nk;
-    }
-  }
-  __syncthreads();
-  float2 A[R], B[R];                      // sums of hx * z and hy * z (see fir_causal_x2)
+  unsigned long long P[R], Q[R];              // pairs of floats, +0.0f each
 #pragma unroll
-  for (int r = 0; r < R; ++r) A[r] = B[r] = make_float2(0.f, 0.f);
-  for (int g0 = 0; g0 < nk; g0 += kBranchGroup) {
-    const int ng = min(kBranchGroup, nk - g0);
-    // branch signals z = u^q x of this group for the whole window, one tight loop per branch
-    for (int g = 0; g < ng; ++g) {
-      float2* zg = zb + g * Wp;
-      switch (s_q[g0 + g]) {
-#define ZP(Q) case Q: zpass<R, Q>(xs, zg, W); break;
-        ZP(0) ZP(1) ZP(2) ZP(3) ZP(4) ZP(5) ZP(6) ZP(7)
-        ZP(8) ZP(9) ZP(10) ZP(11) ZP(12) ZP(13) ZP(14) ZP(15)
-#undef ZP
-        default: zpass_any<R>(xs, zg, W, s_q[g0 + g]); break;
-      }
+  for (int r = 0; r < R; ++r) P[r] = Q[r] = 0ull;
+  const uint8_t* qk = reinterpret_cast<const uint8_t*>(hw + a.K * MT);
+  uint32_t rest = mask;
+  while (rest) {
+    const int k = __ffs(rest) - 1;
+    rest &= rest - 1;
+    const int q = qk[k];
+    zpass_w<R>(xs, zw, lane, q);
+    if (it.t0 == 0 && lane < MT - 1) {
+      // the MT-1 samples before the block: branch k's own history
+      const float2 x = hist_sample(a, pl, it.i, k, lane);
+      zstore(zw, lane, R, x, upow(fmaf(x.x, x.x, x.y * x.y), q));
     }
-    if (it.t0 == 0) {
-      // tile 0: the MT-1 samples before the block come from each branch's own history
-      for (int e = p; e < ng * (MT - 1); e += P) {
-        const int g = e / (MT - 1), v = e - g * (MT - 1);
-        zb[g * Wp + v + v / R] = psi_q(hist_sample(a, pl, it.i, s_k[g0 + g], v), s_q[g0 + g]);
-      }
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int g = 0; g < ng; ++g) fir_branch_x2<R, MT>(A, B, zb + g * Wp, p, hs + s_k[g0 + g] * MT, MT);
-    __syncthreads();
+    __syncwarp();
+    fir_w<R, MT>(P, Q, zw, lane, hw + k * MT);
+    __syncwarp();
   }
+  float2 y[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) zb[p * (R + 1) + r] = make_float2(A[r].x - B[r].y, A[r].y + B[r].x);
-  __syncthreads();
-  for (int o = p; o < it.len; o += P) yb[o] = zb[o + o / R];
+  for (int r = 0; r < R; ++r) {
+    const float2 p = unpack_b64(P[r]), q = unpack_b64(Q[r]);
+    y[r] = make_float2(p.x - q.y, p.y + q.x);
+  }
+  store_w<R>(yb, it.len, lane, y);
 }
 
 constexpr int kMaxGroup = 1024;
 
+// `order` (may be null: identity) lists the group's actors in the order their
+// items are laid out; actors of equal padded tap count are kept together, so
+// that the warps of an SM, which work on neighbouring items, run the same
+// code at the same time.
 template <int R, int MTMAX>
-__device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, int G, Grid grid,
-                                    float4* smem_raw) {
+__device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint16_t* __restrict__ order,
+                                    int G, Grid grid, float4* smem_raw) {
+  using S = WarpSmem<R, MTMAX>;
   __shared__ uint64_t sw[32];
-  __shared__ int s_k[kMaxBranches], s_q[kMaxBranches];
-  const uint32_t T = R * blockDim.x;
-  const int Wm = (int)T + MTMAX - 1;
-  const int Wpm = Wm + Wm / R + 2;
-  // taps (float4, 16-byte aligned) follow the tile buffers; then the work-list
-  // offsets of the group's actors
-  const int hs_off = (2 * Wm + kBranchGroup * Wpm + 1) & ~1;          // in float2 units
-  uint64_t* s_off = reinterpret_cast<uint64_t*>(reinterpret_cast<float2*>(smem_raw) + hs_off +
-                                                2 * kMaxBranches * MTMAX);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  constexpr uint32_t WI = 32 * R;
+  uint64_t* s_off = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t carry = 0;
   for (int base = 0; base < G; base += blockDim.x) {
-    const int g = base + threadIdx.x;
+    const int j = base + threadIdx.x;
     uint64_t items = 0;
-    if (g < G) {
-      const DpdArgs& a = args[g];
-      items = a.plan->n * ((a.L + T - 1) / T);
+    if (j < G) {
+      const DpdArgs& a = args[order ? order[j] : j];
+      items = a.plan->n * ((a.L + WI - 1) / WI);
     }
     uint64_t tot;
     const uint64_t ex = block_exclusive_scan_u64(items, sw, &tot);
-    if (g < G) s_off[g] = carry + ex;
+    if (j < G) s_off[j] = carry + ex;
     carry += tot;
   }
   if (threadIdx.x == 0) s_off[G] = carry;
+  uint16_t* s_ord = reinterpret_cast<uint16_t*>(s_off + G + 1);
+  for (int j = threadIdx.x; j < G; j += blockDim.x) s_ord[j] = order ? order[j] : (uint16_t)j;
   __syncthreads();
   const uint64_t total = carry;
-  const int W = (int)T + MTMAX - 1;
-  const int Wp = W + W / R + 2;
-  float2* xsb = reinterpret_cast<float2*>(smem_raw);          // [2][W]
-  float2* zb = xsb + 2 * W;
-  float4* hs = reinterpret_cast<float4*>(xsb + hs_off);              // taps {hx, hx, hy, hy}
-  int taps_of = -1;                                            // actor whose taps are in hs
-  uint64_t item = grid.b;
-  ItemRef cur = locate(args, s_off, G, item, total, T);
-  if (cur.g >= 0) prefetch_x(args[cur.g], cur, xsb, T);
+  uint8_t* wb = reinterpret_cast<uint8_t*>(smem_raw) + dpd_body_off_bytes(G) + (size_t)wid * S::bytes;
+  float2* xw = reinterpret_cast<float2*>(wb);
+  float4* zw = reinterpret_cast<float4*>(wb + S::x_bytes);
+  float2* hw = reinterpret_cast<float2*>(wb + S::x_bytes + S::z_bytes);
+  const uint64_t stride = (uint64_t)grid.n * nwarp;
+  uint64_t item = (uint64_t)wid * grid.n + grid.b;
+  int taps_of = -1;                                  // actor whose taps are in hw
+  WItem cur = locate_w(args, s_off, s_ord, G, item, total, WI);
+  if (cur.g >= 0) prefetch_w(args[cur.g], cur, xw, WI, lane);
   cp_async_commit();
   int buf = 0;
   while (cur.g >= 0) {
-    const uint64_t next_item = item + grid.n;
-    const ItemRef nxt = locate(args, s_off, G, next_item, total, T);
-    if (nxt.g >= 0) prefetch_x(args[nxt.g], nxt, xsb + (buf ^ 1) * W, T);
+    const uint64_t next_item = item + stride;
+    const WItem nxt = locate_w(args, s_off, s_ord, G, next_item, total, WI);
+    if (nxt.g >= 0) prefetch_w(args[nxt.g], nxt, xw + (buf ^ 1) * S::XW, WI, lane);
     cp_async_commit();
+    const DpdArgs& a = args[cur.g];
     if (cur.g != taps_of) {
-      const DpdArgs& a = args[cur.g];
-      for (int e = threadIdx.x; e < a.K * a.MT; e += blockDim.x) {
-        const float2 h = a.h[e];
-        hs[e] = make_float4(h.x, h.x, h.y, h.y);
-      }
+      // taps {hx, hy} of every branch, then q = (order - 1) / 2 per branch (bytes)
+      for (int e = lane; e < a.K * a.MT; e += 32) hw[e] = a.h[e];
+      if (lane < a.K) reinterpret_cast<uint8_t*>(hw + a.K * a.MT)[lane] = (uint8_t)((a.orders[lane] - 1) >> 1);
       taps_of = cur.g;
     }
     cp_async_wait1();
-    __syncthreads();
-    const DpdArgs& a = args[cur.g];
-    switch (a.MT) {
+    __syncwarp();
+    const float2* xs = xw + buf * S::XW;
+    if (a.masks[cur.i] == 0) {
+      float2* yb = reinterpret_cast<float2*>(const_cast<uint8_t*>(slot_at(a.out, a.plan->slot_out0, cur.i))) +
+                   cur.t0;
+      float2 y[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) y[r] = make_float2(0.f, 0.f);
+      store_w<R>(yb, cur.len, lane, y);
+    } else {
+      switch (a.MT) {
 #define DPD_CASE(MTV) \
-      case MTV: if constexpr (MTV <= MTMAX) dpd_compute<R, MTV>(a, cur, xsb + buf * W, zb, Wp, hs, s_k, s_q); break;
-      DPD_MT_CASES(DPD_CASE)
+        case MTV: if constexpr (MTV <= MTMAX) dpd_item_w<R, MTV>(a, cur, xs, zw, hw, lane); break;
+        DPD_MT_CASES(DPD_CASE)
 #undef DPD_CASE
-      default: break;
+        default: break;
+      }
     }
-    __syncthreads();
+    __syncwarp();
     cur = nxt;
     item = next_item;
     buf ^= 1;

@@ -1,7 +1,7 @@
 // Predistorter adjoint that never allocates device memory.
 //
 // df_dpd_backward keeps its tap-gradient partial sums in a buffer the library
-// allocates with cudaMalloc (once per device, grown on demand).  Some callers
+// allocates with cudaMalloc (one per device and stream, grown on demand).  Some callers
 // cannot let a library do that: a real-time adaptation loop (for example a
 // radio front end refitting its predistorter between bursts) must not call
 // cudaMalloc, which may synchronise the device and block for an unbounded
@@ -12,10 +12,11 @@
 //
 // The array is a file-scope __device__ variable.  In host code its name only
 // stands in for the device object, so its device address is fetched with
-// cudaGetSymbolAddress once per device (with that device current) and passed
-// to the kernels.
-#include <mutex>
-
+// cudaGetSymbolAddress, with the calling device current, and passed to the
+// kernels.  The lookup is repeated on every call (it is not a stream
+// operation and costs far less than the kernels): an address cached across
+// calls would go stale if the caller reset the device and the library's
+// device code were loaded again.
 #include "common.cuh"
 
 namespace {
@@ -26,24 +27,12 @@ constexpr size_t kNoAllocScratchElems = 131072;
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocScratchElems];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-float2* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set up on first use).
+// Device address of the scratch array on the current device.
 cudaError_t scratch_on_current_device(float2** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<float2*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<float2*>(p);
   return cudaSuccess;
 }
 

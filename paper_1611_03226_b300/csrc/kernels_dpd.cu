@@ -23,10 +23,11 @@ __global__ void __launch_bounds__(256) k_dpd_plan(const DpdArgs* args) {
 }
 
 template <int R, int MTMAX>
-__global__ void __launch_bounds__(256) k_dpd_body(const DpdArgs* __restrict__ args, int G) {
+__global__ void __launch_bounds__(256, 2) k_dpd_body(const DpdArgs* __restrict__ args,
+                                                     const uint16_t* __restrict__ order, int G) {
   extern __shared__ float4 smem_raw[];
   griddep_wait();
-  dpd_body_dev<R, MTMAX>(args, G, Grid{blockIdx.x, gridDim.x}, smem_raw);
+  dpd_body_dev<R, MTMAX>(args, order, G, Grid{blockIdx.x, gridDim.x}, smem_raw);
 }
 
 cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t s, bool pdl) {
@@ -34,14 +35,12 @@ cudaError_t launch_dpd_plan(const DpdArgs* args_dev, int n_actors, cudaStream_t 
   return launch_k(pdl, k_dpd_plan, dim3(n_actors), dim3(256), 0, s, args_dev);
 }
 
-static size_t body_smem(uint32_t T, int R, int mtmax, int G) {
-  const size_t W = T + mtmax - 1;
-  const size_t Wp = W + W / R + 2;
-  return 2 * W * sizeof(float2) + kBranchGroup * Wp * sizeof(float2) +
-         (size_t)kMaxBranches * mtmax * sizeof(float4) + sizeof(float2) + (size_t)(G + 1) * sizeof(uint64_t);
+static size_t body_smem(int R, int mtmax, int warps, int G) {
+  if (R == 8) return mtmax == 16 ? dpd_body_smem<8, 16>(warps, G) : dpd_body_smem<8, 32>(warps, G);
+  return mtmax == 16 ? dpd_body_smem<16, 16>(warps, G) : dpd_body_smem<16, 32>(warps, G);
 }
 
-constexpr int kBodySmemMax = 200 * 1024;
+constexpr int kBodySmemMax = 226 * 1024;   // 227 KB per block less the static shared memory
 
 template <int R, int MTMAX>
 static cudaError_t body_attr() {
@@ -58,31 +57,31 @@ cudaError_t dpd_prepare() {
 }
 
 template <int R, int MTMAX>
-static cudaError_t body_launch(const DpdArgs* args_dev, int n_actors, uint32_t threads, size_t smem,
-                               int n_sm, cudaStream_t s, bool pdl) {
+static cudaError_t body_launch(const DpdArgs* args_dev, const uint16_t* order, int n_actors, uint32_t threads,
+                               size_t smem, int n_sm, cudaStream_t s, bool pdl) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dpd_body<R, MTMAX>, threads, smem);
   return launch_k(pdl, k_dpd_body<R, MTMAX>, dim3(n_sm * std::max(per_sm, 1)), dim3(threads), smem, s,
-                  args_dev, n_actors);
+                  args_dev, order, n_actors);
 }
 
-cudaError_t launch_dpd_body(const DpdArgs* args_dev, int n_actors, uint32_t tile, uint32_t threads,
-                            int max_mt, int n_sm, cudaStream_t s, bool pdl) {
+// tile = threads * R samples: every warp of the CTA takes chunks of 32 * R
+// outputs (R = 8 or 16); threads = 32 .. 256.
+cudaError_t launch_dpd_body(const DpdArgs* args_dev, const uint16_t* order, int n_actors, uint32_t tile,
+                            uint32_t threads, int max_mt, int n_sm, cudaStream_t s, bool pdl) {
   if (n_actors <= 0) return cudaSuccess;
-  if (n_actors > kMaxGroup) return cudaErrorInvalidValue;
+  if (n_actors > kMaxGroup || threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
   const int R = (int)(tile / threads);
+  if ((R != 8 && R != 16) || tile != (uint32_t)R * threads) return cudaErrorInvalidValue;
   const int mtmax = max_mt <= 16 ? 16 : 32;
-  const size_t smem = body_smem(tile, R, mtmax, n_actors);
+  const size_t smem = body_smem(R, mtmax, (int)threads / 32, n_actors);
   if (smem > (size_t)kBodySmemMax) return cudaErrorInvalidValue;
   if (R == 8) {
-    return mtmax == 16 ? body_launch<8, 16>(args_dev, n_actors, threads, smem, n_sm, s, pdl)
-                       : body_launch<8, 32>(args_dev, n_actors, threads, smem, n_sm, s, pdl);
+    return mtmax == 16 ? body_launch<8, 16>(args_dev, order, n_actors, threads, smem, n_sm, s, pdl)
+                       : body_launch<8, 32>(args_dev, order, n_actors, threads, smem, n_sm, s, pdl);
   }
-  if (R == 16) {
-    return mtmax == 16 ? body_launch<16, 16>(args_dev, n_actors, threads, smem, n_sm, s, pdl)
-                       : body_launch<16, 32>(args_dev, n_actors, threads, smem, n_sm, s, pdl);
-  }
-  return cudaErrorInvalidValue;
+  return mtmax == 16 ? body_launch<16, 16>(args_dev, order, n_actors, threads, smem, n_sm, s, pdl)
+                     : body_launch<16, 32>(args_dev, order, n_actors, threads, smem, n_sm, s, pdl);
 }
 
 // ------------------------------------------------- stateless operators ----
@@ -303,6 +302,15 @@ __global__ void __launch_bounds__(kGhThreads) k_gh_final(const float2* partial, 
   }
 }
 
+// Resident CTAs of the stateless kernels: 16 per SM of the current device.
+static uint64_t stateless_grid_cap() {
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1)
+    n_sm = 1;
+  return 16ull * (uint64_t)n_sm;
+}
+
 static uint64_t stateless_tiles(uint64_t n) {
   const uint64_t T = (uint64_t)kStatelessR * kStatelessP;
   return (n + T - 1) / T;
@@ -338,7 +346,7 @@ cudaError_t dpd_forward_stateless(const float2* x, uint64_t n, const float2* h, 
                            (int)smem);
   if (e != cudaSuccess) return e;
   const uint64_t nt = stateless_tiles(n);
-  const unsigned grid = (unsigned)std::min<uint64_t>(nt, 148ull * 16);
+  const unsigned grid = (unsigned)std::min<uint64_t>(nt, stateless_grid_cap());
   k_dpd_fwd<kStatelessR><<<grid, kStatelessP, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -364,7 +372,7 @@ cudaError_t dpd_backward_stateless(const float2* x, uint64_t n, const float2* h,
     e = cudaFuncSetAttribute(k_dpd_bwd<kStatelessR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)std::min<uint64_t>(nt, 148ull * 16);
+    const unsigned grid = (unsigned)std::min<uint64_t>(nt, stateless_grid_cap());
     k_dpd_bwd<kStatelessR><<<grid, kStatelessP, smem, s>>>(a);
   }
   k_gh_final<<<K * M, kGhThreads, 0, s>>>(a.partial, nt, K, M, a.MT, gh);

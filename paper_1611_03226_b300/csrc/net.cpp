@@ -61,6 +61,7 @@ struct Op {
   DpdArgs* dpd_dev = nullptr;        // group args (device)
   int dpd_n = 0;                      // actors in the group
   int dpd_first_actor = -1;           // actor id of the first member
+  const uint16_t* dpd_order = nullptr;  // the body's actor order (device; by padded tap count)
   int max_mt = 0;
   std::vector<SpillArgs> spills;      // Fig. 2 copies after the op's bodies
 };
@@ -383,7 +384,8 @@ df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
           const bool pdl = !ev.first;
           DF_CUDA(launch_dpd_plan(op.dpd_dev + i, per, s, pdl));
           if (ev.first) DF_CUDA(cudaEventRecord(ev.first, s));
-          DF_CUDA(launch_dpd_body(op.dpd_dev + i, per, tile, threads, op.max_mt, net->n_sm, s, pdl));
+          DF_CUDA(launch_dpd_body(op.dpd_dev + i, no_batch ? nullptr : op.dpd_order, per, tile, threads,
+                                  op.max_mt, net->n_sm, s, pdl));
           if (ev.second) DF_CUDA(cudaEventRecord(ev.second, s));
         }
         break;
@@ -396,12 +398,18 @@ df_status enqueue_step(df_net* net, bool no_batch, bool capturing = false) {
   return DF_OK;
 }
 
+// Tap-gradient partial sums of df_dpd_backward: one buffer per (device,
+// stream), so calls on different streams never share one, and calls on one
+// stream are ordered by it.  A buffer that is outgrown is retired, never
+// freed while the process runs: kernels already enqueued, and CUDA graphs
+// captured earlier, may still write to it.
 std::mutex g_scratch_mu;
 struct Scratch {
   void* ptr = nullptr;
   size_t bytes = 0;
 };
-std::map<int, Scratch> g_scratch;       // per device: backward tap-gradient partials
+std::map<std::pair<int, uintptr_t>, Scratch> g_scratch;
+std::vector<void*> g_scratch_retired;
 
 }  // namespace
 
@@ -454,6 +462,7 @@ df_status build_persistent(df_net* net) {
       p.kind = kPersistDpd;
       p.n = op.dpd_n;
       p.args = op.dpd_dev;
+      p.order = op.dpd_order;
       max_group = std::max(max_group, op.dpd_n);
       mtmax = std::max(mtmax, op.max_mt);
     }
@@ -583,8 +592,9 @@ df_status df_actor_add(df_net* net, int32_t kind, const void* params, size_t par
       if (!params || params_bytes != sizeof(df_img_params)) return DF_EINVAL;
       std::memcpy(&A.img, params, sizeof(df_img_params));
       const df_img_params& m = A.img;
-      if (m.width < 16 || m.width % 16 || m.width > kImgMaxWidth || m.height < 1 || m.height > 65536)
-        return DF_EINVAL;
+      if (m.width < 1 || m.height < 1 || m.height > 65536) return DF_EINVAL;
+      // valid frames the image kernels do not implement: 16-byte row vectors, 2048-pixel rows
+      if (m.width < 16 || m.width % 16 || m.width > kImgMaxWidth) return DF_ENOTSUP;
       if (kind == DF_THRES && (m.threshold < 0 || m.threshold > 255)) return DF_EINVAL;
       break;
     }
@@ -592,9 +602,11 @@ df_status df_actor_add(df_net* net, int32_t kind, const void* params, size_t par
       if (!params || params_bytes != sizeof(df_md_params)) return DF_EINVAL;
       std::memcpy(&A.md, params, sizeof(df_md_params));
       const df_md_params& m = A.md;
-      if (m.width < 32 || m.width % 32 || m.height < 1 || m.tile != 16) return DF_EINVAL;
+      if (m.width < 1 || m.height < 1 || m.tile < 1) return DF_EINVAL;
       if (m.width > 65536 || m.height > 65536 || m.threshold < 0 || m.threshold > 255)
         return DF_EINVAL;
+      // valid frames the detector does not implement: 32-pixel row words, 16x16 tiles
+      if (m.width % 32 || m.tile != 16) return DF_ENOTSUP;
       break;
     }
     default:
@@ -733,6 +745,7 @@ df_status df_net_finalize(df_net* net) {
     }
   }
   const Piece p_dpd_args = take(sizeof(DpdArgs) * std::max<size_t>(1, dp.size()));
+  const Piece p_dpd_order = take(sizeof(uint16_t) * std::max<size_t>(1, dp.size()));
   net->arena_bytes = off;
   if (cudaMalloc(&net->arena, std::max<size_t>(off, 256)) != cudaSuccess) {
     cudaGetLastError();
@@ -850,6 +863,8 @@ df_status df_net_finalize(df_net* net) {
     op.spills.push_back(sp);
   };
   std::vector<int> group;                 // current predistorter group (actor ids)
+  std::vector<std::vector<uint16_t>> host_orders;
+  std::vector<std::pair<uint16_t*, size_t>> order_copies;
   auto flush_group = [&]() {
     if (group.empty()) return;
     Op op{};
@@ -859,6 +874,17 @@ df_status df_net_finalize(df_net* net) {
     op.dpd_n = (int)group.size();
     op.dpd_first_actor = group[0];
     for (int a : group) op.max_mt = std::max(op.max_mt, net->dpd_host[net->dpd_index[a]].MT);
+    // the body lays out its items actor by actor in this order: equal padded
+    // tap counts together (stable), so neighbouring items share kernel code
+    std::vector<uint16_t> ord(group.size());
+    for (size_t j = 0; j < ord.size(); ++j) ord[j] = (uint16_t)j;
+    std::stable_sort(ord.begin(), ord.end(), [&](uint16_t x, uint16_t y) {
+      return net->dpd_host[net->dpd_index[group[x]]].MT < net->dpd_host[net->dpd_index[group[y]]].MT;
+    });
+    host_orders.push_back(std::move(ord));
+    uint16_t* od = reinterpret_cast<uint16_t*>(base + p_dpd_order.off) + net->dpd_index[group[0]];
+    order_copies.push_back({od, host_orders.size() - 1});
+    op.dpd_order = od;
     net->program.push_back(op);
     group.clear();
   };
@@ -990,6 +1016,10 @@ df_status df_net_finalize(df_net* net) {
     }
   }
   flush_group();
+  for (const auto& oc : order_copies)
+    DF_CUDA(cudaMemcpyAsync(oc.first, host_orders[oc.second].data(), host_orders[oc.second].size() * sizeof(uint16_t),
+                            cudaMemcpyHostToDevice, s));
+  DF_CUDA(cudaStreamSynchronize(s));
   if (!dp.empty()) DF_CUDA(dpd_prepare());  // also covers branch FIR actors
   for (const Op& op : net->program)
     if (op.kind == kOpImg) {
@@ -1582,7 +1612,7 @@ df_status df_autotune(df_net* net, uint64_t* n_firings) {
         for (int rep = 0; rep < 2; ++rep) {
           DF_CUDA(cudaEventRecord(e0, s));
           const cudaError_t le =
-              launch_dpd_body(op.dpd_dev, op.dpd_n, c[0], c[1], op.max_mt, net->n_sm, s);
+              launch_dpd_body(op.dpd_dev, op.dpd_order, op.dpd_n, c[0], c[1], op.max_mt, net->n_sm, s);
           if (le != cudaSuccess) {
             cudaGetLastError();            // configuration does not fit: skip it
             break;
@@ -1599,7 +1629,7 @@ df_status df_autotune(df_net* net, uint64_t* n_firings) {
         }
       }
       if (bt) {
-        DF_CUDA(launch_dpd_body(op.dpd_dev, op.dpd_n, bt, bth, op.max_mt, net->n_sm, s));
+        DF_CUDA(launch_dpd_body(op.dpd_dev, op.dpd_order, op.dpd_n, bt, bth, op.max_mt, net->n_sm, s));
         net->actors[op.dpd_first_actor].tile = bt;
         net->actors[op.dpd_first_actor].threads = bth;
       } else {
@@ -1642,41 +1672,63 @@ df_status df_dpd_forward(const void* x, uint64_t n, const void* h, int32_t K, in
                                            static_cast<cudaStream_t>(cuda_stream)));
 }
 
-df_status df_dpd_backward(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
-                          const int32_t* orders, const void* grad_y, void* grad_x, void* grad_h,
-                          void* cuda_stream) {
+static df_status check_dpd_args(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                                const int32_t* orders, const void* grad_y, const void* grad_h) {
   if (((!x || !grad_y) && n) || !grad_h) return DF_EINVAL;
   if (!h || !orders || K < 1 || K > DF_MAX_BRANCHES || M < 1 || M > DF_MAX_TAPS) return DF_EINVAL;
   for (int k = 0; k < K; ++k)
     if (orders[k] < 1 || orders[k] % 2 == 0 || orders[k] > 63) return DF_EINVAL;
+  return DF_OK;
+}
+
+df_status df_dpd_backward(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                          const int32_t* orders, const void* grad_y, void* grad_x, void* grad_h,
+                          void* cuda_stream) {
+  df_status st = check_dpd_args(x, n, h, K, M, orders, grad_y, grad_h);
+  if (st != DF_OK) return st;
   int dev = 0;
   DF_CUDA(cudaGetDevice(&dev));
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const size_t need = std::max<size_t>(1, dpd_backward_scratch_elems(n, K, M)) * sizeof(float2);
-  void* scratch = nullptr;
-  size_t have = 0;
-  {
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    Scratch& sc = g_scratch[dev];
-    if (sc.bytes < need) {
-      if (sc.ptr) {
-        cudaDeviceSynchronize();
-        cudaFree(sc.ptr);
-        sc.ptr = nullptr;
-        sc.bytes = 0;
-      }
-      if (cudaMalloc(&sc.ptr, need) != cudaSuccess) {
-        cudaGetLastError();
-        return DF_ENOMEM;
-      }
-      sc.bytes = need;
+  // the lock is held until the kernels are enqueued
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  Scratch& sc = g_scratch[{dev, reinterpret_cast<uintptr_t>(s)}];
+  if (sc.bytes < need) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DF_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return DF_ESTATE;   // no allocation inside a capture
+    const size_t grow = std::max(need, 2 * sc.bytes);
+    void* p = nullptr;
+    if (cudaMalloc(&p, grow) != cudaSuccess) {
+      cudaGetLastError();
+      return DF_ENOMEM;
     }
-    scratch = sc.ptr;
-    have = sc.bytes;
+    if (sc.ptr) g_scratch_retired.push_back(sc.ptr);
+    sc.ptr = p;
+    sc.bytes = grow;
   }
   return cuda_status(dpd_backward_stateless(
       static_cast<const float2*>(x), n, static_cast<const float2*>(h), K, M, orders,
       static_cast<const float2*>(grad_y), static_cast<float2*>(grad_x),
-      static_cast<float2*>(grad_h), static_cast<float2*>(scratch), have / sizeof(float2),
+      static_cast<float2*>(grad_h), static_cast<float2*>(sc.ptr), sc.bytes / sizeof(float2), s));
+}
+
+uint64_t df_dpd_backward_scratch_elems(uint64_t n, int32_t K, int32_t M) {
+  if (K < 1 || K > DF_MAX_BRANCHES || M < 1 || M > DF_MAX_TAPS) return 0;
+  return std::max<uint64_t>(1, dpd_backward_scratch_elems(n, K, M));
+}
+
+df_status df_dpd_backward_scratch(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                                  const int32_t* orders, const void* grad_y, void* grad_x,
+                                  void* grad_h, void* scratch, uint64_t scratch_elems,
+                                  void* cuda_stream) {
+  df_status st = check_dpd_args(x, n, h, K, M, orders, grad_y, grad_h);
+  if (st != DF_OK) return st;
+  if (!scratch || scratch_elems < df_dpd_backward_scratch_elems(n, K, M)) return DF_EINVAL;
+  return cuda_status(dpd_backward_stateless(
+      static_cast<const float2*>(x), n, static_cast<const float2*>(h), K, M, orders,
+      static_cast<const float2*>(grad_y), static_cast<float2*>(grad_x),
+      static_cast<float2*>(grad_h), static_cast<float2*>(scratch), scratch_elems,
       static_cast<cudaStream_t>(cuda_stream)));
 }
 

@@ -6,9 +6,10 @@
 // finish -> scatter per actor, actors in insertion order); a grid barrier
 // separates phases that consume another CTA's results.  The barrier is a
 // counter plus a generation word in the engine state; a CTA that waits longer
-// than the limit records DF_ETIMEOUT in the status word, and every CTA leaves
-// at its next barrier once the status word is set, so a wait that cannot
-// complete ends the kernel instead of hanging it.
+// than the limit records DF_ETIMEOUT in the status word, and every CTA that is
+// waiting, or reaches a barrier later, leaves as soon as it sees the status
+// word set, so a wait that cannot complete ends the kernel instead of hanging
+// it, after about one wait limit.
 #include "core_dev.cuh"
 #include "dpd_dev.cuh"
 #include "dyn_dev.cuh"
@@ -50,7 +51,13 @@ __device__ bool grid_barrier(EngineDev* e, unsigned int expected, long long limi
       atomicAdd(&e->barrier_gen, 1u);
     } else {
       const long long t0 = timer_ns();
+      volatile int32_t* status = &e->status;
       while (*gen == g0) {
+        // another CTA's timeout or error ends this wait at once
+        if (*status != 0) {
+          ok = 0;
+          break;
+        }
         if (timer_ns() - t0 > limit_ns) {
           set_status(e, DF_ETIMEOUT, kWhereGridBarrier);
           ok = 0;
@@ -95,7 +102,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp*
           __syncthreads();
         }
         if (!grid_barrier(eng, nb, limit_ns)) return;
-        dpd_body_dev<8, MTMAX>(args, op.n, g, smem);
+        dpd_body_dev<8, MTMAX>(args, op.order, op.n, g, smem);
       } else if (op.kind == kPersistDyn) {
         const DynArgs& a = *static_cast<const DynArgs*>(op.args);
         if (lead) dyn_plan_dev(a);
@@ -152,11 +159,8 @@ cudaError_t persistent_prepare(size_t smem) {
 }
 
 size_t persistent_smem(int mtmax, int max_group) {
-  const size_t T = 8 * kPersistThreads;
-  const size_t W = T + mtmax - 1;
-  const size_t Wp = W + W / 8 + 2;
-  return 2 * W * sizeof(float2) + kBranchGroup * Wp * sizeof(float2) +
-         (size_t)kMaxBranches * mtmax * sizeof(float4) + sizeof(float2) + (size_t)(max_group + 1) * sizeof(uint64_t);
+  return mtmax <= 16 ? dpd_body_smem<8, 16>(kPersistThreads / 32, max_group)
+                     : dpd_body_smem<8, 32>(kPersistThreads / 32, max_group);
 }
 
 cudaError_t launch_persistent(const PersistOp* ops, int n_ops, EngineDev* eng, int64_t n_steps,

@@ -52,12 +52,17 @@ def dpd_backward(x: torch.Tensor, h: torch.Tensor, orders, grad_y: torch.Tensor,
     K, M = h.shape
     gx = torch.empty_like(x) if need_x else None
     gh = torch.empty_like(h)
+    # the adjoint's tap-gradient partial sums come from torch's allocator, which
+    # orders them on this stream and keeps them valid inside CUDA graph capture
+    n_scratch = L.lib.df_dpd_backward_scratch_elems(x.numel(), K, M)
+    scratch = torch.empty(n_scratch, dtype=torch.complex64, device=x.device)
     stream = torch.cuda.current_stream(x.device).cuda_stream
-    L.check(L.lib.df_dpd_backward(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(h.data_ptr()),
-                                  K, M, _orders(orders), C.c_void_p(grad_y.data_ptr()),
-                                  C.c_void_p(gx.data_ptr()) if need_x else None,
-                                  C.c_void_p(gh.data_ptr()), C.c_void_p(stream)),
-            "df_dpd_backward")
+    L.check(L.lib.df_dpd_backward_scratch(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(h.data_ptr()),
+                                          K, M, _orders(orders), C.c_void_p(grad_y.data_ptr()),
+                                          C.c_void_p(gx.data_ptr()) if need_x else None,
+                                          C.c_void_p(gh.data_ptr()), C.c_void_p(scratch.data_ptr()),
+                                          n_scratch, C.c_void_p(stream)),
+            "df_dpd_backward_scratch")
     return gx, gh
 
 
@@ -87,6 +92,8 @@ class DPDMSEFunction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, u, h, target, orders):
+        if u.requires_grad or target.requires_grad:
+            raise ValueError("dpd_mse is differentiable in h only: u and target must not require grad")
         y = dpd_forward(u, h, orders)
         d = (y - target).contiguous()
         dr = torch.view_as_real(d).reshape(-1)

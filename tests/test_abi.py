@@ -73,3 +73,23 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_every_declared_function_cites_its_passage():
+    """Each entry point's comment names the passage of the paper that defines
+    the operation (a section, equation, figure or table), or says that the paper
+    has no counterpart."""
+    cite = re.compile(r"(Sec\.\s*\d|Eq\.\s*\d|Fig\.\s*\d|Table\s*\d|no counterpart)")
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        # block comments: those that open a line (not a field's trailing comment)
+        comments = [(m.start(), m.end(), m.group(0)) for m in re.finditer(r"/\*.*?\*/", text, flags=re.S)
+                    if text[text.rfind("\n", 0, m.start()) + 1:m.start()].strip() == ""]
+        code = re.sub(r"/\*.*?\*/", lambda m: " " * len(m.group(0)), text, flags=re.S)
+        for m in re.finditer(r"\b(df_[a-z0-9_]+)\s*\(", code):
+            before = [c for c in comments if c[1] <= m.start()]
+            assert before, m.group(1)
+            last = before[-1][2]
+            assert cite.search(last), f"{m.group(1)}: no citation in its comment"
