@@ -307,6 +307,7 @@ __device__ __forceinline__ const uint8_t* slot_at(const ChanDesc& c, uint64_t sl
 //                     distinct banks
 //   hw[kMaxBranches * MTMAX + 2] float2  taps {hx, hy} of the warp's current
 //                     actor, then one byte per branch: q = (order - 1) / 2
+//   mw[2] u32         control masks of the two buffered items (staged with x)
 template <int R, int MTMAX>
 struct WarpSmem {
   static constexpr int XW = 32 * (R + 1) > 32 * R + MTMAX - 1 ? 32 * (R + 1) : ((32 * R + MTMAX) & ~1);
@@ -314,7 +315,8 @@ struct WarpSmem {
   static constexpr size_t x_bytes = 2 * (size_t)XW * sizeof(float2);
   static constexpr size_t z_bytes = (size_t)ZW * sizeof(float4);
   static constexpr size_t h_bytes = ((size_t)kMaxBranches * MTMAX + 2) * sizeof(float2);
-  static constexpr size_t bytes = x_bytes + z_bytes + h_bytes;
+  static constexpr size_t m_bytes = 16;     // control masks of the two buffered items
+  static constexpr size_t bytes = x_bytes + z_bytes + h_bytes + m_bytes;
 };
 
 // Bytes before the per-warp areas: the work-list offsets of G actors and
@@ -361,10 +363,10 @@ __device__ __forceinline__ WItem locate_w(const DpdArgs* args, const uint64_t* s
   return r;
 }
 
-// Stage the x window of `it` into xs: position v holds sample t0 - (MT-1) + v
-// of the block, zero outside [0, t0 + len).
-__device__ __forceinline__ void prefetch_w(const DpdArgs& a, const WItem& it, float2* xs, uint32_t WI,
-                                           int lane) {
+// Stage the x window of `it` into xs (position v holds sample t0 - (MT-1) + v
+// of the block, zero outside [0, t0 + len)) and its control mask into mask_dst.
+__device__ __forceinline__ void prefetch_w(const DpdArgs& a, const WItem& it, float2* xs, uint32_t* mask_dst,
+                                           uint32_t WI, int lane) {
   const DpdPlanHdr* pl = a.plan;
   const float2* xb = reinterpret_cast<const float2*>(slot_at(a.data, pl->slot_data0, it.i));
   const int H1 = a.MT - 1;
@@ -374,6 +376,10 @@ __device__ __forceinline__ void prefetch_w(const DpdArgs& a, const WItem& it, fl
     const int pos = (int)it.t0 - H1 + v;
     const bool valid = pos >= 0 && pos < end;
     cp_async8(xs + v, valid ? (const void*)(xb + pos) : (const void*)xb, valid);
+  }
+  if (lane == 0) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(mask_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(a.masks + it.i) : "memory");
   }
 }
 
@@ -479,10 +485,9 @@ __device__ __forceinline__ void store_w(float2* yb, int len, int lane, const flo
 }
 
 template <int R, int MT>
-__device__ __noinline__ void dpd_item_w(const DpdArgs& a, const WItem& it, const float2* xs, float4* zw,
-                                        const float2* hw, int lane) {
+__device__ __noinline__ void dpd_item_w(const DpdArgs& a, const WItem& it, uint32_t mask, const float2* xs,
+                                        float4* zw, const float2* hw, int lane) {
   const DpdPlanHdr& pl = *a.plan;
-  const uint32_t mask = a.masks[it.i];
   float2* yb = reinterpret_cast<float2*>(const_cast<uint8_t*>(slot_at(a.out, pl.slot_out0, it.i))) + it.t0;
   unsigned long long P[R], Q[R];              // pairs of floats, +0.0f each
 #pragma unroll
@@ -548,17 +553,23 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
   float2* xw = reinterpret_cast<float2*>(wb);
   float4* zw = reinterpret_cast<float4*>(wb + S::x_bytes);
   float2* hw = reinterpret_cast<float2*>(wb + S::x_bytes + S::z_bytes);
-  const uint64_t stride = (uint64_t)grid.n * nwarp;
-  uint64_t item = (uint64_t)wid * grid.n + grid.b;
+  uint32_t* mw = reinterpret_cast<uint32_t*>(wb + S::x_bytes + S::z_bytes + S::h_bytes);
+  // Items are dealt to warps in runs of kRun consecutive items (a warp keeps
+  // its actor's taps for a run): run r of global warp gw holds items
+  // (r * NW + gw) * kRun .. + kRun - 1.
+  constexpr uint64_t kRun = 4;
+  const uint64_t NW = (uint64_t)grid.n * nwarp;
+  const uint64_t gw = (uint64_t)wid * grid.n + grid.b;
+  auto item_of = [&](uint64_t k) { return ((k / kRun) * NW + gw) * kRun + (k % kRun); };
+  uint64_t k = 0;
   int taps_of = -1;                                  // actor whose taps are in hw
-  WItem cur = locate_w(args, s_off, s_ord, G, item, total, WI);
-  if (cur.g >= 0) prefetch_w(args[cur.g], cur, xw, WI, lane);
+  WItem cur = locate_w(args, s_off, s_ord, G, item_of(0), total, WI);
+  if (cur.g >= 0) prefetch_w(args[cur.g], cur, xw, mw, WI, lane);
   cp_async_commit();
   int buf = 0;
   while (cur.g >= 0) {
-    const uint64_t next_item = item + stride;
-    const WItem nxt = locate_w(args, s_off, s_ord, G, next_item, total, WI);
-    if (nxt.g >= 0) prefetch_w(args[nxt.g], nxt, xw + (buf ^ 1) * S::XW, WI, lane);
+    const WItem nxt = locate_w(args, s_off, s_ord, G, item_of(k + 1), total, WI);
+    if (nxt.g >= 0) prefetch_w(args[nxt.g], nxt, xw + (buf ^ 1) * S::XW, mw + (buf ^ 1), WI, lane);
     cp_async_commit();
     const DpdArgs& a = args[cur.g];
     if (cur.g != taps_of) {
@@ -570,7 +581,8 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
     cp_async_wait1();
     __syncwarp();
     const float2* xs = xw + buf * S::XW;
-    if (a.masks[cur.i] == 0) {
+    const uint32_t mask = mw[buf];
+    if (mask == 0) {
       float2* yb = reinterpret_cast<float2*>(const_cast<uint8_t*>(slot_at(a.out, a.plan->slot_out0, cur.i))) +
                    cur.t0;
       float2 y[R];
@@ -580,7 +592,7 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
     } else {
       switch (a.MT) {
 #define DPD_CASE(MTV) \
-        case MTV: if constexpr (MTV <= MTMAX) dpd_item_w<R, MTV>(a, cur, xs, zw, hw, lane); break;
+        case MTV: if constexpr (MTV <= MTMAX) dpd_item_w<R, MTV>(a, cur, mask, xs, zw, hw, lane); break;
         DPD_MT_CASES(DPD_CASE)
 #undef DPD_CASE
         default: break;
@@ -588,7 +600,7 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
     }
     __syncwarp();
     cur = nxt;
-    item = next_item;
+    ++k;
     buf ^= 1;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");

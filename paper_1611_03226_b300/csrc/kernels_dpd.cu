@@ -22,9 +22,12 @@ __global__ void __launch_bounds__(256) k_dpd_plan(const DpdArgs* args) {
   dpd_plan_dev(args[blockIdx.x]);
 }
 
+// R = 8: two 256-thread CTAs per SM (128 registers); R = 16 holds twice the
+// accumulators and may use more registers (one 256-thread CTA per SM, which is
+// also what its shared memory allows).
 template <int R, int MTMAX>
-__global__ void __launch_bounds__(256, 2) k_dpd_body(const DpdArgs* __restrict__ args,
-                                                     const uint16_t* __restrict__ order, int G) {
+__global__ void __launch_bounds__(256, R == 8 ? 2 : 1) k_dpd_body(const DpdArgs* __restrict__ args,
+                                                                   const uint16_t* __restrict__ order, int G) {
   extern __shared__ float4 smem_raw[];
   griddep_wait();
   dpd_body_dev<R, MTMAX>(args, order, G, Grid{blockIdx.x, gridDim.x}, smem_raw);

@@ -117,54 +117,6 @@ def test_mask_bits_beyond_K_ignored(Net):
     check_blocks(yo, ye)
 
 
-def sampled_block_oracle(w, i, x_of):
-    """Oracle output of block i of a long stream computed on its own: branch k's
-    history is the tail of the last earlier block with k active (zeros if none).
-    The delay blocks are zero and precede block 0."""
-    d = w.delay
-    L = w.block_len
-    M = w.n_taps
-    xi = np.zeros(L, np.complex64) if i < d else x_of(i - d)
-    y = np.zeros(L, np.complex128)
-    for k in range(w.n_branches):
-        if not (int(w.masks[i]) >> k) & 1:
-            continue
-        prev = [j for j in range(i) if (int(w.masks[j]) >> k) & 1]
-        if prev and prev[-1] >= d:
-            tail = x_of(prev[-1] - d)[L - (M - 1):]
-        else:
-            tail = np.zeros(M - 1, np.complex64)
-        hist = D.psi(tail, w.orders[k])
-        yk, _ = D.fir(w.h[k], hist, D.psi(xi, w.orders[k]))
-        y += yk
-    return y
-
-
-@pytest.mark.slow
-def test_large_workload_full_size_sampled(Net):
-    """512 blocks x 2^20, K<=8 (orders 1..15), M=16, d=2, pushed whole, one run:
-    the bench launch configuration; sampled blocks against the oracle."""
-    import torch
-    w = synth.dpd_large()
-    L, n = w.block_len, w.n_blocks
-    enet, ei = EN.dpd_fused(Net, w.h, w.orders, L, w.delay, n + w.delay)
-    enet.push(ei["ctrl"], np.ascontiguousarray(w.masks))
-    chunk = 32
-    for b in range(0, n, chunk):
-        enet.push(ei["data"], np.ascontiguousarray(w.blocks(b, min(n, b + chunk))))
-    assert enet.run(-1) == n
-    out = torch.empty((n, L), dtype=torch.complex64, device="cuda")
-    _, got = enet.pop(ei["sink"], out=out)
-    assert got == n
-    for i in (0, 1, 2, 3, 100, 257, 510, 511):
-        ref = sampled_block_oracle(w, i, w.block)
-        assert D.rel_l2(out[i].cpu().numpy(), ref) <= TOL
-    for key in ("ch_ctrl", "ch_data", "ch_out"):
-        p, c, o = enet.counters(ei[key])
-        assert p + (w.delay if key == "ch_data" else 0) == c + o
-    enet.close()
-
-
 def test_stateless_forward_backward(Net):
     import torch
     from paper_1611_03226_b300 import dpd as G
