@@ -213,7 +213,8 @@ df_status df_run(df_net *net, int64_t n_steps, uint64_t *n_firings);
 /* Run flags for df_run_ex. */
 enum {
     DF_RUN_ASYNC = 1,        /* enqueue only (n_steps >= 0); no host sync, no firing count */
-    DF_RUN_GRAPH = 2,        /* replay a CUDA graph of n_steps steps (captured once per n) */
+    DF_RUN_GRAPH = 2,        /* replay a CUDA graph of n_steps steps (captured once per n); with
+                                DF_RUN_PERSISTENT the graph holds the one persistent launch */
     DF_RUN_PERSISTENT = 4,   /* one cooperative persistent kernel runs all steps (for n_steps < 0
                                 also the quiescence check); phases are separated by a grid
                                 barrier bounded by the wait limit (df_set_wait_limit) */
@@ -429,6 +430,19 @@ df_status df_dpd_backward_scratch(const void *x, uint64_t n, const void *h, int3
                                   const int32_t *orders, const void *grad_y, void *grad_x,
                                   void *grad_h, void *scratch, uint64_t scratch_elems,
                                   void *cuda_stream);
+
+/* df_dpd_forward and df_dpd_backward_scratch in float64 arithmetic on
+ * complex128 data (x, h, y, grad_y, grad_x, grad_h and the scratch, whose
+ * element count is df_dpd_backward_scratch_elems(n, K, M) complex128 values).
+ * They exist so that the hand-written adjoint can be checked against finite
+ * differences at full precision (torch.autograd.gradcheck); FP64 throughput
+ * on this GPU is a small fraction of FP32.
+ * Defined by: the Sec. 4.2 predistorter and its adjoint, as the float32 forms. */
+df_status df_dpd_forward_f64(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                             const int32_t *orders, void *y, void *cuda_stream);
+df_status df_dpd_backward_f64(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                              const int32_t *orders, const void *grad_y, void *grad_x, void *grad_h,
+                              void *scratch, uint64_t scratch_elems, void *cuda_stream);
 
 /* Same computation and results as df_dpd_backward, but it allocates nothing.
  * (The paper has no counterpart; this exists for callers that may not

@@ -96,6 +96,10 @@ _PROTOS = {
     "df_dpd_backward": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
                                     C.POINTER(C.c_int32), _P, _P, _P, _P]),
     "df_dpd_backward_scratch_elems": (C.c_uint64, [C.c_uint64, C.c_int32, C.c_int32]),
+    "df_dpd_forward_f64": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
+                                       C.POINTER(C.c_int32), _P, _P]),
+    "df_dpd_backward_f64": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
+                                        C.POINTER(C.c_int32), _P, _P, _P, _P, C.c_uint64, _P]),
     "df_dpd_backward_scratch": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
                                             C.POINTER(C.c_int32), _P, _P, _P, _P, C.c_uint64, _P]),
 }

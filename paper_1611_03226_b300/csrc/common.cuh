@@ -40,6 +40,7 @@ struct EngineDev {          // device-resident engine state
   int32_t status_where;     // which kernel / wait reported it
   unsigned int barrier_count;   // persistent-kernel grid barrier
   unsigned int barrier_gen;
+  unsigned int exit_count;      // persistent-kernel CTAs that have finished their last step
   unsigned long long total_snap;  // fired_total as the last CTA saw it when releasing a barrier
   // Published counters for concurrent host I/O: a copy of the counter array
   // taken when a step has finished (all its bodies done).  Plans commit a
@@ -307,5 +308,10 @@ cudaError_t dpd_backward_stateless(const float2* x, uint64_t n, const float2* h,
                                    const int* orders, const float2* gy, float2* gx, float2* gh,
                                    float2* scratch, size_t scratch_elems, cudaStream_t s);
 size_t dpd_backward_scratch_elems(uint64_t n, int K, int M);
+cudaError_t dpd_forward_stateless_f64(const double2* x, uint64_t n, const double2* h, int K, int M,
+                                      const int* orders, double2* y, cudaStream_t s);
+cudaError_t dpd_backward_stateless_f64(const double2* x, uint64_t n, const double2* h, int K, int M,
+                                       const int* orders, const double2* gy, double2* gx, double2* gh,
+                                       double2* scratch, size_t scratch_elems, cudaStream_t s);
 
 }  // namespace dfg

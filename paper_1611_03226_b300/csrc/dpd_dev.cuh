@@ -29,30 +29,6 @@
 namespace dfg {
 
 
-__device__ __forceinline__ float2 cmac(float2 acc, float2 h, float2 z) {
-  acc.x = fmaf(h.x, z.x, acc.x);
-  acc.x = fmaf(-h.y, z.y, acc.x);
-  acc.y = fmaf(h.x, z.y, acc.y);
-  acc.y = fmaf(h.y, z.x, acc.y);
-  return acc;
-}
-// acc += a * conj(b)
-__device__ __forceinline__ float2 cmac_conj_b(float2 acc, float2 a, float2 b) {
-  acc.x = fmaf(a.x, b.x, acc.x);
-  acc.x = fmaf(a.y, b.y, acc.x);
-  acc.y = fmaf(a.y, b.x, acc.y);
-  acc.y = fmaf(-a.x, b.y, acc.y);
-  return acc;
-}
-
-// |x|^(2q) x with u = |x|^2 raised by repeated products
-__device__ __forceinline__ float2 psi_q(float2 x, int q) {
-  const float u = fmaf(x.x, x.x, x.y * x.y);
-  float p = 1.f;
-  for (int i = 0; i < q; ++i) p *= u;
-  return make_float2(p * x.x, p * x.y);
-}
-
 // u^q for a runtime q, by squaring
 __device__ __forceinline__ float upow(float u, int q) {
   float p = (q & 1) ? u : 1.f;
@@ -88,94 +64,6 @@ __device__ inline uint64_t block_exclusive_scan_u64(uint64_t v, uint64_t* sw, ui
   *total = sw[nw - 1];
   __syncthreads();
   return before + x - v;
-}
-
-// ------------------------------------------------------------ FIR cores ----
-// Shared windows are padded with one element after every R elements so that
-// threads reading at stride R elements hit distinct banks.
-// Causal chunk: acc[r] += sum_{m<MC} h[m] * zs[v], v = p*R + shift + r - m + MC - 1.
-// Taps m >= m_valid are zero (unpadded tap rows).  The complex product is
-// issued as two passes over the R outputs (real tap part, then imaginary tap
-// part) so consecutive FMAs update different accumulators.
-template <int R, int MC>
-__device__ __forceinline__ void fir_causal(float2 (&acc)[R], const float2* __restrict__ zs, int p,
-                                           int shift, const float2* __restrict__ h, int m_valid) {
-  float2 hk[MC];
-#pragma unroll
-  for (int m = 0; m < MC; ++m) hk[m] = m < m_valid ? h[m] : make_float2(0.f, 0.f);
-  const float2* zb = zs + p * (R + 1) + shift + shift / R;
-#pragma unroll
-  for (int s = 0; s < R + MC - 1; ++s) {
-    const float2 z = zb[s + s / R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int m = r + MC - 1 - s;
-      if (m >= 0 && m < MC) {
-        acc[r].x = fmaf(hk[m].x, z.x, acc[r].x);
-        acc[r].y = fmaf(hk[m].x, z.y, acc[r].y);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int m = r + MC - 1 - s;
-      if (m >= 0 && m < MC) {
-        acc[r].x = fmaf(-hk[m].y, z.y, acc[r].x);
-        acc[r].y = fmaf(hk[m].y, z.x, acc[r].y);
-      }
-    }
-  }
-}
-
-// Anti-causal chunk with conjugated taps: acc[r] += sum_m conj(h[m]) * gs[v], v = p*R + shift + r + m.
-template <int R, int MC>
-__device__ __forceinline__ void fir_anticausal_conj(float2 (&acc)[R], const float2* __restrict__ gs,
-                                                    int p, int shift, const float2* __restrict__ h,
-                                                    int m_valid) {
-  float2 ck[MC];
-#pragma unroll
-  for (int m = 0; m < MC; ++m) {
-    const float2 t = m < m_valid ? __ldg(h + m) : make_float2(0.f, 0.f);
-    ck[m] = make_float2(t.x, -t.y);
-  }
-  const float2* gb = gs + p * (R + 1) + shift + shift / R;
-#pragma unroll
-  for (int s = 0; s < R + MC - 1; ++s) {
-    const float2 g = gb[s + s / R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int m = s - r;
-      if (m >= 0 && m < MC) acc[r] = cmac(acc[r], ck[m], g);
-    }
-  }
-}
-
-// Tap-gradient chunk: ph[m] += sum_r g[r] * conj(zs[v]), v = p*R + shift + r - m + MC - 1.
-template <int R, int MC>
-__device__ __forceinline__ void gh_chunk(float2 (&ph)[MC], const float2 (&gr)[R],
-                                         const float2* __restrict__ zs, int p, int shift) {
-  const float2* zb = zs + p * (R + 1) + shift + shift / R;
-#pragma unroll
-  for (int s = 0; s < R + MC - 1; ++s) {
-    const float2 z = zb[s + s / R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int m = r + MC - 1 - s;
-      if (m >= 0 && m < MC) ph[m] = cmac_conj_b(ph[m], gr[r], z);
-    }
-  }
-}
-
-// FIR of one branch over a staged window, MT <= 16 in one chunk, MT == 32 in two.
-// h points at the M valid taps of the branch (M <= MT).
-template <int R, int MT>
-__device__ __forceinline__ void fir_branch(float2 (&acc)[R], const float2* zs, int p,
-                                           const float2* h, int M) {
-  if constexpr (MT <= 16) {
-    fir_causal<R, MT>(acc, zs, p, 0, h, M);
-  } else {
-    fir_causal<R, 16>(acc, zs, p, 16, h, M);
-    fir_causal<R, 16>(acc, zs, p, 0, h + 16, M - 16);
-  }
 }
 
 #define DPD_MT_CASES(X) X(4) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(32)

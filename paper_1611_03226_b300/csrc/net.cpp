@@ -1177,7 +1177,7 @@ df_status df_push_ex(df_net* net, int32_t src_actor, const void* src, uint64_t n
 df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_firings) {
   if (!net) return DF_EINVAL;
   if (!net->finalized) return DF_ESTATE;
-  if ((flags & DF_RUN_PERSISTENT) && (flags & (DF_RUN_GRAPH | DF_RUN_NO_BATCH))) return DF_ENOTSUP;
+  if ((flags & DF_RUN_PERSISTENT) && (flags & DF_RUN_NO_BATCH)) return DF_ENOTSUP;
   DeviceGuard g(net->device);
   const bool no_batch = flags & DF_RUN_NO_BATCH;
   uint64_t before = 0;
@@ -1197,12 +1197,33 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
   if (flags & DF_RUN_PERSISTENT) {
     df_status st = build_persistent(net);
     if (st != DF_OK) return st;
-    const auto ev = prof_pair(net, DF_PROF_STEP, false);
-    if (ev.first) DF_CUDA(cudaEventRecord(ev.first, net->stream));
-    DF_CUDA(launch_persistent(net->d_persist_ops, net->persist_n_ops, net->d_eng, n_steps,
-                              net->wait_limit_ns, net->persist_mtmax, net->persist_smem, net->n_sm,
-                              net->stream));
-    if (ev.second) DF_CUDA(cudaEventRecord(ev.second, net->stream));
+    if (flags & DF_RUN_GRAPH) {
+      // one graph holding the persistent launch (its n_steps, or until quiescent)
+      auto key = std::make_pair(n_steps, 0x200u);
+      auto it = net->graphs.find(key);
+      if (it == net->graphs.end()) {
+        cudaGraph_t graph;
+        DF_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = launch_persistent(net->d_persist_ops, net->persist_n_ops, net->d_eng, n_steps,
+                                                 net->wait_limit_ns, net->persist_mtmax, net->persist_smem,
+                                                 net->n_sm, net->stream);
+        const cudaError_t ce = cudaStreamEndCapture(net->stream, &graph);
+        DF_CUDA(le);
+        DF_CUDA(ce);
+        cudaGraphExec_t exec;
+        DF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        cudaGraphDestroy(graph);
+        it = net->graphs.emplace(key, exec).first;
+      }
+      DF_CUDA(cudaGraphLaunch(it->second, net->stream));
+    } else {
+      const auto ev = prof_pair(net, DF_PROF_STEP, false);
+      if (ev.first) DF_CUDA(cudaEventRecord(ev.first, net->stream));
+      DF_CUDA(launch_persistent(net->d_persist_ops, net->persist_n_ops, net->d_eng, n_steps,
+                                net->wait_limit_ns, net->persist_mtmax, net->persist_smem, net->n_sm,
+                                net->stream));
+      if (ev.second) DF_CUDA(cudaEventRecord(ev.second, net->stream));
+    }
   } else if (n_steps >= 0) {
     if (flags & DF_RUN_GRAPH) {
       // the graph of a step ends with the counter publication once concurrent I/O is in use
@@ -1526,6 +1547,16 @@ df_status df_set_wait_limit(df_net* net, int64_t limit_ns) {
   net->wait_limit_ns = limit_ns;
   for (Op& op : net->program)
     if (op.kind == kOpMd) op.md.wait_limit_ns = limit_ns;
+  // captured graphs and the persistent kernel's program hold the old limit
+  DeviceGuard g(net->device);
+  DF_CUDA(cudaStreamSynchronize(net->stream));
+  for (auto& kv : net->graphs) cudaGraphExecDestroy(kv.second);
+  net->graphs.clear();
+  if (net->persist_mem) {
+    DF_CUDA(cudaFree(net->persist_mem));
+    net->persist_mem = nullptr;
+    net->d_persist_ops = nullptr;
+  }
   return DF_OK;
 }
 
@@ -1539,7 +1570,7 @@ df_status df_selftest_wait_timeout(df_net* net, int64_t limit_ns) {
   st = fail_if_device_error(net);
   // leave the network usable: clear the status word and the barrier state
   DF_CUDA(cudaMemsetAsync(&net->d_eng->status, 0, 2 * sizeof(int32_t), net->stream));
-  DF_CUDA(cudaMemsetAsync(&net->d_eng->barrier_count, 0, 2 * sizeof(unsigned int), net->stream));
+  DF_CUDA(cudaMemsetAsync(&net->d_eng->barrier_count, 0, 3 * sizeof(unsigned int), net->stream));
   DF_CUDA(cudaStreamSynchronize(net->stream));
   return st;
 }
@@ -1713,6 +1744,28 @@ df_status df_dpd_backward(const void* x, uint64_t n, const void* h, int32_t K, i
       static_cast<const float2*>(x), n, static_cast<const float2*>(h), K, M, orders,
       static_cast<const float2*>(grad_y), static_cast<float2*>(grad_x),
       static_cast<float2*>(grad_h), static_cast<float2*>(sc.ptr), sc.bytes / sizeof(float2), s));
+}
+
+df_status df_dpd_forward_f64(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                             const int32_t* orders, void* y, void* cuda_stream) {
+  if ((!x || !y) && n) return DF_EINVAL;
+  df_status st = check_dpd_args(x, n, h, K, M, orders, x, h);
+  if (st != DF_OK) return st;
+  return cuda_status(dpd_forward_stateless_f64(static_cast<const double2*>(x), n, static_cast<const double2*>(h),
+                                               K, M, orders, static_cast<double2*>(y),
+                                               static_cast<cudaStream_t>(cuda_stream)));
+}
+
+df_status df_dpd_backward_f64(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                              const int32_t* orders, const void* grad_y, void* grad_x, void* grad_h,
+                              void* scratch, uint64_t scratch_elems, void* cuda_stream) {
+  df_status st = check_dpd_args(x, n, h, K, M, orders, grad_y, grad_h);
+  if (st != DF_OK) return st;
+  if (!scratch || scratch_elems < df_dpd_backward_scratch_elems(n, K, M)) return DF_EINVAL;
+  return cuda_status(dpd_backward_stateless_f64(
+      static_cast<const double2*>(x), n, static_cast<const double2*>(h), K, M, orders,
+      static_cast<const double2*>(grad_y), static_cast<double2*>(grad_x), static_cast<double2*>(grad_h),
+      static_cast<double2*>(scratch), scratch_elems, static_cast<cudaStream_t>(cuda_stream)));
 }
 
 uint64_t df_dpd_backward_scratch_elems(uint64_t n, int32_t K, int32_t M) {

@@ -24,6 +24,12 @@ __device__ __forceinline__ long long timer_ns() {
   return t;
 }
 
+// Copy of the counters for concurrent host I/O once a step is over.
+__device__ void publish_counters(EngineDev* e) {
+  if (e->pub)
+    for (uint32_t i = 0; i < e->n_words; ++i) e->pub[i] = reinterpret_cast<volatile uint64_t*>(e->ctr)[i];
+}
+
 // Returns false when the status word is set (own timeout or another CTA's).
 // With snap, the CTA that releases the barrier records fired_total in
 // total_snap first, so every CTA reads the same value after the barrier (a
@@ -43,9 +49,7 @@ __device__ bool grid_barrier(EngineDev* e, unsigned int expected, long long limi
       if (snap) {
         e->total_snap = *reinterpret_cast<volatile unsigned long long*>(&e->fired_total);
         // the step is over: publish its counters for concurrent host I/O
-        if (e->pub)
-          for (uint32_t i = 0; i < e->n_words; ++i)
-            e->pub[i] = reinterpret_cast<volatile uint64_t*>(e->ctr)[i];
+        publish_counters(e);
       }
       __threadfence();
       atomicAdd(&e->barrier_gen, 1u);
@@ -74,7 +78,7 @@ __device__ bool grid_barrier(EngineDev* e, unsigned int expected, long long limi
 }
 
 template <int MTMAX>
-__global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp* __restrict__ ops,
+__global__ void __launch_bounds__(kPersistThreads, 2) k_persistent(const PersistOp* __restrict__ ops,
                                                                int n_ops, EngineDev* eng,
                                                                int64_t n_steps, long long limit_ns) {
   extern __shared__ float4 smem[];
@@ -82,11 +86,15 @@ __global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp*
   const unsigned int nb = gridDim.x;
   const bool lead = blockIdx.x == 0;
   const int64_t max_steps = n_steps < 0 ? (int64_t)1 << 20 : n_steps;
+  const bool until_quiet = n_steps < 0;
   volatile unsigned long long* snap = &eng->total_snap;
   if (n_ops == 0) return;
-  // the first barrier records the firing total before any commit
-  if (!grid_barrier(eng, nb, limit_ns, true)) return;
-  unsigned long long fired0 = *snap;
+  unsigned long long fired0 = 0;
+  if (until_quiet) {
+    // the first barrier records the firing total before any commit
+    if (!grid_barrier(eng, nb, limit_ns, true)) return;
+    fired0 = *snap;
+  }
   for (int64_t step = 0; step < max_steps; ++step) {
     for (int o = 0; o < n_ops; ++o) {
       const PersistOp op = ops[o];
@@ -127,13 +135,27 @@ __global__ void __launch_bounds__(kPersistThreads) k_persistent(const PersistOp*
         if (!grid_barrier(eng, nb, limit_ns)) return;
         md_emit_dev(a, g);
       }
-      // the step's last barrier records the total that ends the step
+      // the step's last barrier records the total that ends the step; after the
+      // last step of a fixed count the end of the kernel orders what follows
+      if (!until_quiet && o == n_ops - 1 && step == max_steps - 1) break;
       if (!grid_barrier(eng, nb, limit_ns, o == n_ops - 1)) return;
     }
-    // every CTA reads the same recorded total, so all take the same decision
-    const unsigned long long fired1 = *snap;
-    if (n_steps < 0 && fired1 == fired0) return;
-    fired0 = fired1;
+    if (until_quiet) {
+      // every CTA reads the same recorded total, so all take the same decision
+      const unsigned long long fired1 = *snap;
+      if (fired1 == fired0) return;
+      fired0 = fired1;
+    }
+  }
+  // fixed step count: the last CTA to finish publishes the counters
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&eng->exit_count, 1u) == nb - 1) {
+      __threadfence();
+      eng->total_snap = *reinterpret_cast<volatile unsigned long long*>(&eng->fired_total);
+      publish_counters(eng);
+    }
   }
 }
 
@@ -168,16 +190,25 @@ cudaError_t launch_persistent(const PersistOp* ops, int n_ops, EngineDev* eng, i
   const int idx = mtmax <= 16 ? 0 : 1;
   const int per_sm = g_persist_blocks[idx];
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaMemsetAsync(&eng->barrier_count, 0, 2 * sizeof(unsigned int), s);
+  cudaError_t e = cudaMemsetAsync(&eng->barrier_count, 0, 3 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&ops, (void*)&n_ops, (void*)&eng, (void*)&n_steps, (void*)&limit_ns};
-  const dim3 grid(n_sm * per_sm), block(kPersistThreads);
-  if (idx == 0) return cudaLaunchCooperativeKernel((void*)k_persistent<16>, grid, block, args, smem, s);
-  return cudaLaunchCooperativeKernel((void*)k_persistent<32>, grid, block, args, smem, s);
+  // a cooperative launch (all CTAs resident at once), also inside a CUDA graph capture
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(n_sm * per_sm);
+  cfg.blockDim = dim3(kPersistThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (idx == 0) return cudaLaunchKernelEx(&cfg, k_persistent<16>, ops, n_ops, eng, n_steps, limit_ns);
+  return cudaLaunchKernelEx(&cfg, k_persistent<32>, ops, n_ops, eng, n_steps, limit_ns);
 }
 
 cudaError_t launch_barrier_selftest(EngineDev* eng, long long limit_ns, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(&eng->barrier_count, 0, 2 * sizeof(unsigned int), s);
+  cudaError_t e = cudaMemsetAsync(&eng->barrier_count, 0, 3 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&eng, (void*)&limit_ns};
   return cudaLaunchCooperativeKernel((void*)k_barrier_selftest, dim3(4), dim3(32), args, 0, s);

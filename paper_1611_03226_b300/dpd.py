@@ -5,7 +5,8 @@ z_k = |x|^(orders[k]-1) x (every branch active, zero history) through
 df_dpd_forward; its gradient goes through the hand-written adjoint
 df_dpd_backward, which recomputes z_k from x instead of storing it.
 Gradients follow PyTorch's convention for complex tensors
-(dL/dRe + i dL/dIm).
+(dL/dRe + i dL/dIm).  complex64 tensors run the float32 kernels, complex128
+tensors the float64 instantiation of the same kernels.
 """
 from __future__ import annotations
 
@@ -22,8 +23,8 @@ def _orders(orders):
 
 
 def _check_inputs(x, h):
-    if x.dtype != torch.complex64 or h.dtype != torch.complex64:
-        raise TypeError("x and h must be complex64")
+    if x.dtype not in (torch.complex64, torch.complex128) or h.dtype != x.dtype:
+        raise TypeError("x and h must both be complex64 (float32 kernels) or both complex128 (float64)")
     if not (x.is_cuda and h.is_cuda):
         raise ValueError("x and h must be CUDA tensors")
     if x.dim() != 1 or h.dim() != 2:
@@ -37,9 +38,9 @@ def dpd_forward(x: torch.Tensor, h: torch.Tensor, orders) -> torch.Tensor:
     K, M = h.shape
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream(x.device).cuda_stream
-    L.check(L.lib.df_dpd_forward(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(h.data_ptr()),
-                                 K, M, _orders(orders), C.c_void_p(y.data_ptr()),
-                                 C.c_void_p(stream)), "df_dpd_forward")
+    fn = L.lib.df_dpd_forward if x.dtype == torch.complex64 else L.lib.df_dpd_forward_f64
+    L.check(fn(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(h.data_ptr()), K, M, _orders(orders),
+               C.c_void_p(y.data_ptr()), C.c_void_p(stream)), "df_dpd_forward")
     return y
 
 
@@ -48,21 +49,20 @@ def dpd_backward(x: torch.Tensor, h: torch.Tensor, orders, grad_y: torch.Tensor,
     _check_inputs(x, h)
     x = x.contiguous()
     h = h.contiguous()
-    grad_y = grad_y.contiguous().to(torch.complex64)
+    grad_y = grad_y.contiguous().to(x.dtype)
     K, M = h.shape
     gx = torch.empty_like(x) if need_x else None
     gh = torch.empty_like(h)
     # the adjoint's tap-gradient partial sums come from torch's allocator, which
     # orders them on this stream and keeps them valid inside CUDA graph capture
     n_scratch = L.lib.df_dpd_backward_scratch_elems(x.numel(), K, M)
-    scratch = torch.empty(n_scratch, dtype=torch.complex64, device=x.device)
+    scratch = torch.empty(n_scratch, dtype=x.dtype, device=x.device)
     stream = torch.cuda.current_stream(x.device).cuda_stream
-    L.check(L.lib.df_dpd_backward_scratch(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(h.data_ptr()),
-                                          K, M, _orders(orders), C.c_void_p(grad_y.data_ptr()),
-                                          C.c_void_p(gx.data_ptr()) if need_x else None,
-                                          C.c_void_p(gh.data_ptr()), C.c_void_p(scratch.data_ptr()),
-                                          n_scratch, C.c_void_p(stream)),
-            "df_dpd_backward_scratch")
+    fn = L.lib.df_dpd_backward_scratch if x.dtype == torch.complex64 else L.lib.df_dpd_backward_f64
+    L.check(fn(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(h.data_ptr()), K, M, _orders(orders),
+               C.c_void_p(grad_y.data_ptr()), C.c_void_p(gx.data_ptr()) if need_x else None,
+               C.c_void_p(gh.data_ptr()), C.c_void_p(scratch.data_ptr()), n_scratch, C.c_void_p(stream)),
+            "df_dpd_backward")
     return gx, gh
 
 

@@ -219,7 +219,9 @@ def test_batched_channels_match_oracle_and_per_channel_launches(Net):
         return outs
 
     variants = {"batched": run_once(0), "per_channel": run_once(L.DF_RUN_NO_BATCH),
-                "graph": run_once(L.DF_RUN_GRAPH), "autotuned": run_once(0, tune=True)}
+                "graph": run_once(L.DF_RUN_GRAPH), "autotuned": run_once(0, tune=True),
+                "persistent": run_once(L.DF_RUN_PERSISTENT),
+                "persistent_graph": run_once(L.DF_RUN_PERSISTENT | L.DF_RUN_GRAPH)}
     for name, outs in variants.items():
         for c in range(C):
             check_blocks(want[c], outs[c])
@@ -228,13 +230,15 @@ def test_batched_channels_match_oracle_and_per_channel_launches(Net):
         np.testing.assert_array_equal(variants["batched"][c], variants["graph"][c])
 
 
-def test_persistent_mode_streams_tiny_workload(Net):
+@pytest.mark.parametrize("graph", [False, True])
+def test_persistent_mode_streams_tiny_workload(Net, graph):
     """The 64 x 4096 workload through capacity-8 FIFOs, every step one
-    persistent-kernel launch."""
+    persistent-kernel launch (replayed from a CUDA graph, or launched)."""
     from paper_1611_03226_b300 import _lib as L
     w = synth.dpd_tiny()
+    flags = L.DF_RUN_PERSISTENT | (L.DF_RUN_GRAPH if graph else 0)
     yo, ye = stream_both(Net, w.h, w.orders, w.block_len, w.delay, w.capacity, w.masks,
-                         w.blocks(), 3, flags=L.DF_RUN_PERSISTENT)
+                         w.blocks(), 3, flags=flags)
     assert len(ye) == 64
     check_blocks(yo, ye)
 

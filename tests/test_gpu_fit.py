@@ -25,6 +25,42 @@ def test_gradcheck_small():
     assert torch.autograd.gradcheck(f, (x, h), eps=2e-3, atol=2e-2, rtol=2e-2, nondet_tol=0.0)
 
 
+@pytest.mark.parametrize("n,K,M,orders", [(64, 3, 5, (1, 3, 5)), (1500, 4, 10, (1, 3, 5, 7)),
+                                          (300, 2, 32, (1, 9))])
+def test_gradcheck_float64_default_tolerances(n, K, M, orders):
+    """The same kernels instantiated in float64 (complex128 tensors) pass
+    torch.autograd.gradcheck at its default step and tolerances, for the
+    input and the taps, across one and several tiles (1024 samples each),
+    and for the two-chunk tap path (M = 32)."""
+    import torch
+    from paper_1611_03226_b300.dpd import dpd
+    rng = np.random.default_rng(n + K)
+    x = torch.tensor(rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n), dtype=torch.complex128,
+                     device="cuda", requires_grad=True)
+    h = torch.tensor(rng.normal(0, .2, (K, M)) + 1j * rng.normal(0, .2, (K, M)), dtype=torch.complex128,
+                     device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda a, b: dpd(a, b, orders), (x, h), nondet_tol=0.0)
+
+
+def test_float64_forward_and_adjoint_match_the_oracle():
+    """The float64 kernels against the float64 oracle at 1e-12."""
+    import torch
+    from oracle import dpd as D
+    from paper_1611_03226_b300 import dpd as G
+    rng = np.random.default_rng(21)
+    n, K, M, orders = 5000, 4, 10, (1, 3, 5, 7)
+    x = rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n)
+    h = rng.normal(0, .1, (K, M)) + 1j * rng.normal(0, .1, (K, M))
+    g = rng.normal(size=n) + 1j * rng.normal(size=n)
+    xt, ht, gt = (torch.tensor(a, dtype=torch.complex128, device="cuda") for a in (x, h, g))
+    y = G.dpd_forward(xt, ht, orders).cpu().numpy()
+    assert D.rel_l2(y, D.dpd_stream(x, h, orders)) <= 1e-12
+    gx, gh = G.dpd_backward(xt, ht, orders, gt)
+    rx, rh = D.dpd_stream_backward(x, h, orders, g)
+    assert D.rel_l2(gx.cpu().numpy(), rx) <= 1e-12
+    assert D.rel_l2(gh.cpu().numpy(), rh) <= 1e-12
+
+
 def test_pa_model_matches_oracle():
     import torch
     from paper_1611_03226_b300 import fit as F
