@@ -865,8 +865,10 @@ def bench_dpd_batch(args, P, torch, pk):
         "autotuned_tile": {"samples": tuned[0], "threads": tuned[1]},
         "gpu_launches_per_step": {"batched": 2, "per_channel": 2 * C},
         "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": ach / peak_tf, "traffic": None, "kernel": "k_dpd_body",
-                     "algorithmic_flops_per_launch": flops},
+                     "frac": ach / peak_tf,
+                     "traffic": profiled_traffic("k_dpd_body__dpd_batch_256ch_x16blocks.md"),
+                     "kernel": "k_dpd_body", "algorithmic_flops_per_launch": flops,
+                     "algorithmic_bytes_per_launch": 16 * samples},
         "cpu_baseline": {"value": n_cpu / cpu_s / 1e6, "unit": "Msamples/s", "cores": 1,
                          "kind": "oracle", "sample": "channels 0-3, 16 blocks each", "host": host,
                          "processes": {"value": done / run_s / 1e6, "unit": "Msamples/s", "cores": procs,
