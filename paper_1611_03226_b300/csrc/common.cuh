@@ -116,6 +116,7 @@ struct ImgArgs {
   int n_out;
   int W, H, thr;
   int dedup;                // Thres: in[1] is in[0]'s stream delayed by one token (same broadcast writer)
+  int binary_in;            // Med: every input byte is 0 or 255 (written by Thres, initial tokens binary)
   uint64_t* ctr;
   EngineDev* eng;
   ImgPlan* plan;

@@ -82,10 +82,12 @@ __device__ __forceinline__ uint32_t med5_u16x2(uint32_t a, uint32_t b, uint32_t 
 __device__ __forceinline__ bool bytes_binary(uint32_t w) { return ((w ^ (w << 1)) & 0xfefefefeu) == 0; }
 
 // Bitwise majority of five words (at least 3 of 5 bits set): for bytes that
-// are 0x00 or 0xff this is the median of five.
+// are 0x00 or 0xff this is the median of five.  With k = the count among c, d,
+// e: a and b both set need k >= 1, one of them k >= 2, none k = 3 (and k = 3
+// suffices alone); every term is one 3-input logic operation.
 __device__ __forceinline__ uint32_t maj5(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e) {
   const uint32_t any3 = c | d | e, two3 = (c & d) | (c & e) | (d & e), all3 = c & d & e;
-  return (a & b & any3) | ((a ^ b) & two3) | (~(a | b) & all3);
+  return (a & b & any3) | ((a | b) & two3) | all3;
 }
 
 // Median of five per byte: even and odd bytes in 16-bit lanes.
@@ -373,20 +375,25 @@ __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, u
 // Any byte of w neither 0x00 nor 0xff: a nonzero word.
 __device__ __forceinline__ uint32_t nonbinary_bits(uint32_t w) { return (w ^ (w << 1)) & 0xfefefefeu; }
 
-// Med over bands of img_band(W) rows, 16 pixels per thread.  One vote per
-// band: when every input byte of the band and its halo rows is 0 or 255 (every
-// motion map) the median is a bitwise majority; otherwise the bytewise
-// min/max network runs.
+// Med over bands of img_band(W) rows, 16 pixels per thread.  When every input
+// byte of the band and its halo rows is 0 or 255 (every motion map) the median
+// is a bitwise majority; otherwise the bytewise min/max network runs.  The
+// test is one vote per band, skipped when the input is known to be binary
+// (its writer is Thres).
 __device__ inline void med_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
   const UnitMap um = unit_map(W);
+  const bool known_binary = a.binary_in != 0;
   for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
-    uint32_t nb = 0;
-    for_units(um, max(y0 - 1, 0), min(y1 + 1, H), [&](int y, int x) {
-      const uint4 c = *reinterpret_cast<const uint4*>(s + (y - y0 + 2) * W + x);
-      nb |= nonbinary_bits(c.x) | nonbinary_bits(c.y) | nonbinary_bits(c.z) | nonbinary_bits(c.w);
-    });
-    const bool binary = __syncthreads_or(nb != 0) == 0;
+    bool binary = true;
+    if (!known_binary) {
+      uint32_t nb = 0;
+      for_units(um, max(y0 - 1, 0), min(y1 + 1, H), [&](int y, int x) {
+        const uint4 c = *reinterpret_cast<const uint4*>(s + (y - y0 + 2) * W + x);
+        nb |= nonbinary_bits(c.x) | nonbinary_bits(c.y) | nonbinary_bits(c.z) | nonbinary_bits(c.w);
+      });
+      binary = __syncthreads_or(nb != 0) == 0;
+    }
     for_units(um, y0, y1, [&](int y, int x) {
       const uint8_t* row = s + (y - y0 + 2) * W;
       const uint4 c = *reinterpret_cast<const uint4*>(row + x);

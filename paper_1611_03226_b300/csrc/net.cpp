@@ -976,6 +976,14 @@ df_status df_net_finalize(df_net* net) {
                                wk == DF_MED5;
         m.dedup = (cur.src == prev.src && broadcast && cur.init == 0 && prev.init == 1) ? 1 : 0;
       }
+      if (A.kind == DF_MED5) {
+        // Thres writes only 0 and 255: with such initial tokens too, the
+        // median of five is a bitwise majority without a per-band check
+        const ChanH& in = net->chans[A.in[0]];
+        bool bin = net->actors[in.src].kind == DF_THRES;
+        for (uint8_t v : in.init_data) bin = bin && (v == 0 || v == 255);
+        m.binary_in = bin ? 1 : 0;
+      }
       m.ctr = net->d_ctr;
       m.eng = net->d_eng;
       m.plan = reinterpret_cast<ImgPlan*>(base + ip[img_index[a]].off);

@@ -150,3 +150,33 @@ def test_thres_input_wirings(Net, wiring):
     n = min(len(first), len(second)) // rate * rate
     assert len(got) == n
     np.testing.assert_array_equal(got, np.stack([MP.thres(first[i], second[i], t) for i in range(n)]))
+
+
+@pytest.mark.parametrize("binary_init", [True, False])
+def test_med_after_thres_with_initial_frame(Net, binary_init):
+    """Med reading Thres's 0/255 maps takes the bitwise-majority path without a
+    per-band check; an initial frame on its input channel that is not 0/255
+    keeps the general median (the engine decides this when it is built)."""
+    T, H, W, rate, t = 8, 24, 48, 2, 20
+    f = synth.uniform_frames(T, H, W, seed=31)
+    init = synth.uniform_frames(1, H, W, seed=32)[0]
+    if binary_init:
+        init = np.where(init > 127, 255, 0).astype(np.uint8)
+    fb = H * W
+    net = Net()
+    src, th, med, snk = net.add_source(), net.add_thres(W, H, t), net.add_med5(W, H), net.add_sink()
+    net.connect(src, 0, th, 0, fb, rate, T + 1)
+    net.connect(src, 1, th, 1, fb, rate, T + 1, 1)
+    net.connect(th, 0, med, 0, fb, rate, T + 2, 1, init)
+    net.connect(med, 0, snk, 0, fb, rate, T + 2)
+    net.finalize()
+    net.push(src, f)
+    net.run(-1)
+    got = net.pop(snk, dtype=np.uint8).reshape(-1, H, W)
+    net.close()
+    prev = np.concatenate([np.zeros((1, H, W), np.uint8), f[:-1]])
+    maps = np.stack([MP.thres(f[i], prev[i], t) for i in range(T)])
+    want = np.stack([MP.med5(x) for x in np.concatenate([init[None], maps])])
+    n = len(got)
+    assert n >= T - rate
+    np.testing.assert_array_equal(got, want[:n])
