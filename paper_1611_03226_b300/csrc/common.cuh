@@ -38,10 +38,11 @@ struct EngineDev {          // device-resident engine state
   unsigned long long fired_total;
   int32_t status;           // DF_OK or the first device-side error
   int32_t status_where;     // which kernel / wait reported it
-  unsigned int barrier_count;   // persistent-kernel grid barrier
-  unsigned int barrier_gen;
+  // Arrivals at the persistent kernel's grid barriers, never reset while the
+  // engine runs without an error (kBarrierError is added with every error).
+  unsigned long long bar_arrive;
   unsigned int exit_count;      // persistent-kernel CTAs that have finished their last step
-  unsigned long long total_snap;  // fired_total as the last CTA saw it when releasing a barrier
+  unsigned int pad_;
   // Published counters for concurrent host I/O: a copy of the counter array
   // taken when a step has finished (all its bodies done).  Plans commit a
   // step's counters before its bodies move the data, so a push or pop that
@@ -82,8 +83,14 @@ struct SpillArgs {
 };
 
 #ifdef __CUDACC__
+// Added to bar_arrive with every recorded error: CTAs waiting at a grid
+// barrier see it in the word they poll and leave.
+constexpr unsigned long long kBarrierError = 1ull << 62;
+
 __device__ inline void set_status(EngineDev* e, int32_t code, int32_t where) {
   if (atomicCAS(&e->status, 0, code) == 0) e->status_where = where;
+  __threadfence();
+  atomicAdd(&e->bar_arrive, kBarrierError);
 }
 #endif
 
@@ -147,6 +154,7 @@ struct DpdPlanHdr {
   uint64_t slot_out0;       // wr_out0 mod output capacity
   uint32_t parity_in;       // history buffer the body reads
   uint32_t pad;
+  int32_t last[kMaxBranches];  // latest firing of the step with branch k active, -1: none
 };
 
 struct DpdArgs {            // one per predistorter actor, stored in device memory
@@ -162,6 +170,7 @@ struct DpdArgs {            // one per predistorter actor, stored in device memo
   uint32_t* masks;          // [n_max]
   uint32_t* rank;           // [K][n_max]: active firings of branch k before firing i
   uint32_t* act;            // [K][n_max]: firing index of the a-th active block of k
+  int32_t* prev;            // [K][n_max]: latest earlier firing of the step with k active, -1: none
   uint32_t* cnt;            // [K]: active firings of k this step
   float2* hist;             // [2][K][MT-1]: raw input samples preceding the batch
   uint32_t* parity;         // which half of hist is current
@@ -300,7 +309,8 @@ size_t md_smem_bytes(int W);
 cudaError_t persistent_prepare(size_t smem);
 size_t persistent_smem(int mtmax, int max_group);
 cudaError_t launch_persistent(const PersistOp* ops, int n_ops, EngineDev* eng, int64_t n_steps,
-                              long long limit_ns, int mtmax, size_t smem, int n_sm, cudaStream_t s);
+                              long long limit_ns, int mtmax, size_t smem, int n_sm, bool publish,
+                              cudaStream_t s);
 cudaError_t launch_barrier_selftest(EngineDev* eng, long long limit_ns, cudaStream_t s);
 
 cudaError_t dpd_forward_stateless(const float2* x, uint64_t n, const float2* h, int K, int M,

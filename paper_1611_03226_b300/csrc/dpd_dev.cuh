@@ -6,22 +6,24 @@
 //   n     = min(control tokens, data tokens, free output slots)   (all rates 1)
 //   masks = the n control tokens
 //   for every branch k an exclusive scan over the n firings of bit k gives
-//   rank[k][i] (how many earlier firings of this step had k active) and the
-//   compaction act[k][a] (firing of the a-th active block of k).  These are
+//   rank[k][i] (how many earlier firings of this step had k active), the
+//   compaction act[k][a] (firing of the a-th active block of k) and
+//   prev[k][i] (the latest earlier firing with k active, -1: none).  These are
 //   the consumption / production counts of the internal Poly->FIR_k->Adder
 //   channels, whose rate is 0 or 1 per firing.
-//   The persistent history of branch k (the last MT-1 raw input samples of
-//   branch k's compacted stream) is advanced into the other half of a double
-//   buffer, and the channel counters are committed.
-// Body kernel (persistent grid, one launch for a whole group of actors):
-//   work item = (actor, firing, tile of T samples).  The x window with MT-1
-//   samples of halo is staged in shared memory; per active branch the branch
-//   signal z = |x|^(o-1) x is formed in a padded shared buffer (for tile 0
-//   the halo comes from the branch's own history: the previous block in which
-//   that branch was active, found through rank/act, or the persistent
-//   history); each thread accumulates R consecutive outputs of the M-tap
-//   complex FIR with the taps held in registers; the Adder is the running
-//   sum over branches in registers.
+//   The channel counters are committed.  The persistent history of branch k
+//   (the last MT-1 raw input samples of branch k's compacted stream) is
+//   advanced into the other half of a double buffer by the body kernel, off
+//   the step's critical path.
+// Body kernel (one launch for a whole group of actors, a grid sized to the
+//   SMs): work item = (actor, firing, chunk of 32 R output samples), taken by
+//   one warp.  The x window with MT-1 samples of halo is staged in the warp's
+//   shared memory; per active branch the branch signal z = |x|^(o-1) x is
+//   formed in a padded shared buffer (for a block's first chunk the halo comes
+//   from the branch's own history: the previous block in which that branch
+//   was active, found through rank/act, or the persistent history); each lane
+//   accumulates R consecutive outputs of the M-tap complex FIR with the taps in
+//   registers; the Adder is the running sum over branches in registers.
 #pragma once
 #include <algorithm>
 #include "common.cuh"
@@ -69,10 +71,12 @@ __device__ inline uint64_t block_exclusive_scan_u64(uint64_t v, uint64_t* sw, ui
 #define DPD_MT_CASES(X) X(4) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(32)
 
 // ----------------------------------------------------------------- plan ----
+// The plan decides the step and commits it; the persistent history it leaves
+// for the next step is advanced later, beside the body (dpd_hist_dev), since
+// this step's body does not read it.
 __device__ inline void dpd_plan_dev(const DpdArgs& a) {
   __shared__ uint64_t s_n, s_rdc, s_rdd, s_wro;
   __shared__ uint32_t s_par;
-  __shared__ uint64_t sw[32];
   uint64_t* ctr = a.ctr;
   const bool has_ctrl = a.ctrl.ring != nullptr;
   if (threadIdx.x == 0) {
@@ -89,43 +93,41 @@ __device__ inline void dpd_plan_dev(const DpdArgs& a) {
   __syncthreads();
   const uint32_t n = (uint32_t)s_n;
   const uint32_t kmask = a.K >= 32 ? 0xffffffffu : ((1u << a.K) - 1u);
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-    a.masks[i] = has_ctrl ? *reinterpret_cast<const uint32_t*>(slot_ptr(a.ctrl, s_rdc + i)) & kmask
-                          : kmask;
-  __syncthreads();
-  for (int k = 0; k < a.K; ++k) {
-    uint64_t carry = 0;
-    for (uint32_t base = 0; base < n; base += blockDim.x) {
-      const uint32_t i = base + threadIdx.x;
-      const uint32_t bit = i < n ? (a.masks[i] >> k) & 1u : 0u;
-      uint64_t tot;
-      const uint64_t ex = block_exclusive_scan_u64(bit, sw, &tot);
-      if (i < n) {
-        a.rank[(size_t)k * a.n_max + i] = (uint32_t)(carry + ex);
-        if (bit) a.act[(size_t)k * a.n_max + carry + ex] = i;
+  // Per branch k, the exclusive scan of its activity bits over the firings:
+  // one warp per branch (branches dealt round-robin to the warps), 32
+  // firings per ballot, each warp reading the control tokens itself, so no
+  // barrier separates reading them from the scans.  The warp of branch 0
+  // also stores the masks for the body.
+  {
+    const int lane = threadIdx.x & 31, nwarp = (int)(blockDim.x >> 5);
+    const uint32_t below = (1u << lane) - 1u;
+    for (int k = (int)(threadIdx.x >> 5); k < a.K; k += nwarp) {
+      uint32_t carry = 0;
+      int last = -1;
+      for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t i = base + lane;
+        uint32_t m = 0;
+        if (i < n)
+          m = has_ctrl ? *reinterpret_cast<const uint32_t*>(slot_ptr(a.ctrl, s_rdc + i)) & kmask : kmask;
+        if (k == 0 && i < n) a.masks[i] = m;
+        const bool bit = (m >> k) & 1u;
+        const uint32_t b = __ballot_sync(0xffffffffu, bit);
+        const uint32_t bb = b & below;
+        const uint32_t ex = carry + __popc(bb);
+        if (i < n) {
+          a.rank[(size_t)k * a.n_max + i] = ex;
+          a.prev[(size_t)k * a.n_max + i] = bb ? (int)base + 31 - __clz(bb) : last;
+          if (bit) a.act[(size_t)k * a.n_max + ex] = i;
+        }
+        carry += __popc(b);
+        if (b) last = (int)base + 31 - __clz(b);
       }
-      carry += tot;
-    }
-    if (threadIdx.x == 0) a.cnt[k] = (uint32_t)carry;
-  }
-  __syncthreads();
-  const int H1 = a.MT - 1;
-  if (n > 0 && H1 > 0) {
-    const uint32_t par = s_par;
-    for (int e = threadIdx.x; e < a.K * H1; e += blockDim.x) {
-      const int k = e / H1, s = e % H1;
-      const int64_t pos = (int64_t)a.cnt[k] * a.L - H1 + s;
-      float2 v;
-      if (pos >= 0) {
-        const uint32_t f = a.act[(size_t)k * a.n_max + (uint32_t)(pos / a.L)];
-        v = reinterpret_cast<const float2*>(slot_ptr(a.data, s_rdd + f))[pos % a.L];
-      } else {
-        v = a.hist[((size_t)par * a.K + k) * H1 + (H1 + pos)];
+      if (lane == 0) {
+        a.cnt[k] = carry;
+        a.plan->last[k] = last;
       }
-      a.hist[((size_t)(par ^ 1) * a.K + k) * H1 + s] = v;
     }
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
     a.plan->n = n;
     a.plan->rd_data0 = s_rdd;
@@ -138,6 +140,38 @@ __device__ inline void dpd_plan_dev(const DpdArgs& a) {
     *rd_ptr(ctr, a.data.id) = s_rdd + n;
     *wr_ptr(ctr, a.out.id) = s_wro + n;
     atomicAdd(&a.eng->fired_total, (unsigned long long)n);
+  }
+}
+
+// The persistent history of every branch after this step (the last MT-1
+// samples of its compacted input stream) into the other half of the double
+// buffer: the tail of the latest active firing, else the history carried in.
+// Runs by one CTA after the plan, beside or after the body (which reads only
+// the half the plan named), and before the next step's plan.
+__device__ inline void dpd_hist_dev(const DpdArgs& a) {
+  const DpdPlanHdr& pl = *a.plan;
+  const uint32_t n = (uint32_t)pl.n;
+  const int H1 = a.MT - 1;
+  if (n == 0 || H1 <= 0) return;
+  const uint32_t par = pl.parity_in;
+  for (int e = threadIdx.x; e < a.K * H1; e += blockDim.x) {
+    const int k = e / H1, s = e % H1;
+    float2 v;
+    if ((uint32_t)H1 <= a.L) {
+      const int f = pl.last[k];
+      v = f >= 0 ? reinterpret_cast<const float2*>(slot_ptr(a.data, pl.rd_data0 + (uint32_t)f))[a.L - H1 + s]
+                 : a.hist[((size_t)par * a.K + k) * H1 + s];
+    } else {
+      // history longer than a block: it spans several earlier firings
+      const int64_t pos = (int64_t)a.cnt[k] * a.L - H1 + s;
+      if (pos >= 0) {
+        const uint32_t f = a.act[(size_t)k * a.n_max + (uint32_t)(pos / a.L)];
+        v = reinterpret_cast<const float2*>(slot_ptr(a.data, pl.rd_data0 + f))[pos % a.L];
+      } else {
+        v = a.hist[((size_t)par * a.K + k) * H1 + (H1 + pos)];
+      }
+    }
+    a.hist[((size_t)(par ^ 1) * a.K + k) * H1 + s] = v;
   }
 }
 
@@ -372,6 +406,11 @@ __device__ __forceinline__ void store_w(float2* yb, int len, int lane, const flo
   }
 }
 
+// One work item.  A block's first chunk also needs, per active branch, the
+// MT-1 samples before the block in that branch's stream: the tail of the
+// latest earlier firing of this step with the branch active (prev, from the
+// plan), else the persisted history; blocks shorter than MT-1 samples take
+// them from several earlier firings (hist_sample).
 template <int R, int MT>
 __device__ __noinline__ void dpd_item_w(const DpdArgs& a, const WItem& it, uint32_t mask, const float2* xs,
                                         float4* zw, const float2* hw, int lane) {
@@ -381,16 +420,27 @@ __device__ __noinline__ void dpd_item_w(const DpdArgs& a, const WItem& it, uint3
 #pragma unroll
   for (int r = 0; r < R; ++r) P[r] = Q[r] = 0ull;
   const uint8_t* qk = reinterpret_cast<const uint8_t*>(hw + a.K * MT);
+  const bool first = it.t0 == 0;
+  const bool short_block = a.L < (uint32_t)(MT - 1);
+  int pv = -1;                                // lane k: prev[k][i]
+  if (first && lane < a.K) pv = a.prev[(size_t)lane * a.n_max + it.i];
   uint32_t rest = mask;
   while (rest) {
     const int k = __ffs(rest) - 1;
     rest &= rest - 1;
     const int q = qk[k];
     zpass_w<R>(xs, zw, lane, q);
-    if (it.t0 == 0 && lane < MT - 1) {
-      // the MT-1 samples before the block: branch k's own history
-      const float2 x = hist_sample(a, pl, it.i, k, lane);
-      zstore(zw, lane, R, x, upow(fmaf(x.x, x.x, x.y * x.y), q));
+    if (first) {
+      const int f = __shfl_sync(0xffffffffu, pv, k);
+      if (lane < MT - 1) {
+        float2 hx;
+        if (short_block) hx = hist_sample(a, pl, it.i, k, lane);
+        else
+          hx = f >= 0 ? reinterpret_cast<const float2*>(slot_at(a.data, pl.slot_data0, (uint32_t)f))
+                            [a.L - (MT - 1) + lane]
+                      : a.hist[((size_t)pl.parity_in * a.K + k) * (MT - 1) + lane];
+        zstore(zw, lane, R, hx, upow(fmaf(hx.x, hx.x, hx.y * hx.y), q));
+      }
     }
     __syncwarp();
     fir_w<R, MT>(P, Q, zw, lane, hw + k * MT);
@@ -444,11 +494,15 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
   uint32_t* mw = reinterpret_cast<uint32_t*>(wb + S::x_bytes + S::z_bytes + S::h_bytes);
   // Items are dealt to warps in runs of kRun consecutive items (a warp keeps
   // its actor's taps for a run): run r of global warp gw holds items
-  // (r * NW + gw) * kRun .. + kRun - 1.
-  constexpr uint64_t kRun = 4;
+  // (r * NW + gw) * kRun .. + kRun - 1.  Runs of 4 when there are at least
+  // 4 items per warp; a smaller step takes shorter runs, so that its items
+  // spread over more warps instead of queueing behind one another.
   const uint64_t NW = (uint64_t)grid.n * nwarp;
+  const int lg_run = total >= 4 * NW ? 2 : (total >= 2 * NW ? 1 : 0);      // kRun = 1 << lg_run
   const uint64_t gw = (uint64_t)wid * grid.n + grid.b;
-  auto item_of = [&](uint64_t k) { return ((k / kRun) * NW + gw) * kRun + (k % kRun); };
+  auto item_of = [&](uint64_t k) {
+    return (((k >> lg_run) * NW + gw) << lg_run) + (k & ((1u << lg_run) - 1u));
+  };
   uint64_t k = 0;
   int taps_of = -1;                                  // actor whose taps are in hw
   WItem cur = locate_w(args, s_off, s_ord, G, item_of(0), total, WI);
@@ -492,6 +546,9 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
     buf ^= 1;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
+  // the histories for the next step, one CTA per actor counted from the last
+  // CTA (the first CTAs take the first items, so a small step leaves these idle)
+  for (int j = (int)(grid.n - 1 - grid.b); j < G; j += (int)grid.n) dpd_hist_dev(args[j]);
 }
 
 }  // namespace dfg

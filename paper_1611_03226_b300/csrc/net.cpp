@@ -685,7 +685,7 @@ df_status df_net_finalize(df_net* net) {
     ring[c] = take((size_t)net->chans[c].slots() * net->chans[c].tok);
   const Piece p_ctr = take(2 * sizeof(uint64_t) * std::max<size_t>(1, net->chans.size()));
   const Piece p_eng = take(sizeof(EngineDev));
-  struct DpdPieces { Piece plan, masks, rank, act, cnt, hist, parity, h; };
+  struct DpdPieces { Piece plan, masks, rank, act, prev, cnt, hist, parity, h; };
   struct MdPieces { Piece plan, counts, tot, off; };
   std::vector<DpdPieces> dp;
   std::vector<MdPieces> mp;
@@ -722,6 +722,7 @@ df_status df_net_finalize(df_net* net) {
       q.masks = take(4ull * nmax);
       q.rank = take(4ull * nmax * K);
       q.act = take(4ull * nmax * K);
+      q.prev = take(4ull * nmax * K);
       q.cnt = take(4ull * K);
       q.hist = take(8ull * 2 * K * std::max(1, MT - 1));
       q.parity = take(4);
@@ -830,6 +831,7 @@ df_status df_net_finalize(df_net* net) {
       d.masks = reinterpret_cast<uint32_t*>(base + q.masks.off);
       d.rank = reinterpret_cast<uint32_t*>(base + q.rank.off);
       d.act = reinterpret_cast<uint32_t*>(base + q.act.off);
+      d.prev = reinterpret_cast<int32_t*>(base + q.prev.off);
       d.cnt = reinterpret_cast<uint32_t*>(base + q.cnt.off);
       d.hist = reinterpret_cast<float2*>(base + q.hist.off);
       d.parity = reinterpret_cast<uint32_t*>(base + q.parity.off);
@@ -1205,16 +1207,18 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
   if (flags & DF_RUN_PERSISTENT) {
     df_status st = build_persistent(net);
     if (st != DF_OK) return st;
+    const bool publish = net->io_used;
     if (flags & DF_RUN_GRAPH) {
-      // one graph holding the persistent launch (its n_steps, or until quiescent)
-      auto key = std::make_pair(n_steps, 0x200u);
+      // one graph holding the persistent launch (its n_steps, or until
+      // quiescent); it publishes the counters once concurrent I/O is in use
+      auto key = std::make_pair(n_steps, 0x200u | (publish ? 0x100u : 0u));
       auto it = net->graphs.find(key);
       if (it == net->graphs.end()) {
         cudaGraph_t graph;
         DF_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
         const cudaError_t le = launch_persistent(net->d_persist_ops, net->persist_n_ops, net->d_eng, n_steps,
                                                  net->wait_limit_ns, net->persist_mtmax, net->persist_smem,
-                                                 net->n_sm, net->stream);
+                                                 net->n_sm, publish, net->stream);
         const cudaError_t ce = cudaStreamEndCapture(net->stream, &graph);
         DF_CUDA(le);
         DF_CUDA(ce);
@@ -1229,7 +1233,7 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
       if (ev.first) DF_CUDA(cudaEventRecord(ev.first, net->stream));
       DF_CUDA(launch_persistent(net->d_persist_ops, net->persist_n_ops, net->d_eng, n_steps,
                                 net->wait_limit_ns, net->persist_mtmax, net->persist_smem, net->n_sm,
-                                net->stream));
+                                publish, net->stream));
       if (ev.second) DF_CUDA(cudaEventRecord(ev.second, net->stream));
     }
   } else if (n_steps >= 0) {
@@ -1578,7 +1582,8 @@ df_status df_selftest_wait_timeout(df_net* net, int64_t limit_ns) {
   st = fail_if_device_error(net);
   // leave the network usable: clear the status word and the barrier state
   DF_CUDA(cudaMemsetAsync(&net->d_eng->status, 0, 2 * sizeof(int32_t), net->stream));
-  DF_CUDA(cudaMemsetAsync(&net->d_eng->barrier_count, 0, 3 * sizeof(unsigned int), net->stream));
+  DF_CUDA(cudaMemsetAsync(&net->d_eng->bar_arrive, 0, sizeof(unsigned long long) + sizeof(unsigned int),
+                          net->stream));
   DF_CUDA(cudaStreamSynchronize(net->stream));
   return st;
 }
