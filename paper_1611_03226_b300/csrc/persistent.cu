@@ -79,6 +79,10 @@ __device__ bool grid_barrier(EngineDev* e, GridBarrier& g, long long limit_ns) {
     unsigned int polls = 0;
     long long t0 = 0;
     while ((v = ld_acquire_u64(&e->bar_arrive)) < g.target) {
+      // a short pause between polls: hundreds of CTAs polling one word back to
+      // back slow the memory accesses of the CTAs still working (measured on
+      // a one-actor step: its plan ran 0.6 us faster)
+      __nanosleep(256);
       if ((++polls & 63u) == 0) {
         const long long t = timer_ns();
         if (t0 == 0) {
