@@ -134,12 +134,13 @@ struct ImgArgs {
 __host__ __device__ constexpr int img_band(int W) { return W <= 1024 ? 32 : 16; }
 constexpr int kImgThreads = 256;
 constexpr int kImgMaxWidth = 2048;
-// shared memory of an image body CTA: two staging buffers of input rows
-// (band + 2-row halo each side) and, for the Gaussian, the vertical sums as
-// u16 rows of W + 16 (8 leading elements hold the 2 clamped left columns, so
-// pixel 0 starts 16-byte aligned; the 2 clamped right columns follow pixel W-1)
+// staging buffers of an image body CTA: the band being computed and the
+// bands being loaded
+constexpr int kImgStages = 2;
+// shared memory of an image body CTA: kImgStages staging buffers of input
+// rows (band + 2-row halo each side)
 __host__ __device__ constexpr size_t img_smem_bytes(int W) {
-  return 2 * (size_t)(img_band(W) + 4) * W + (size_t)img_band(W) * (W + 16) * 2 + 16;
+  return kImgStages * (size_t)(img_band(W) + 4) * W + 16;
 }
 
 // --------------------------------------------------- fused predistorter ----

@@ -207,7 +207,10 @@ __device__ __forceinline__ void stage_rows(const uint8_t* frame, uint8_t* s, int
   }
 }
 __device__ __forceinline__ void img_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void img_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// all but the kImgStages - 1 most recent groups complete: the oldest staged item is in
+__device__ __forceinline__ void img_wait_stages() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(kImgStages - 1) : "memory");
+}
 
 // A thread's walk over the 16-pixel units of W-pixel rows: unit e = tid +
 // k * blockDim.x of a row range is (row e / q, column e % q), q = W / 16.
@@ -237,9 +240,10 @@ __device__ __forceinline__ void for_units(const UnitMap& m, int ya, int yb, F&& 
 }
 
 // Band items (frame, band of img_band(W) rows) of this CTA with the input
-// rows of the next item staged while the current one is computed (two
-// buffers).  Items g.b, g.b + g.n, ..: (frame, band) advances by a fixed
-// step, so it is carried along instead of divided out per item.
+// rows of the next kImgStages - 1 items staged while the current one is
+// computed (a ring of kImgStages buffers).  Items g.b, g.b + g.n, ..:
+// (frame, band) advances by a fixed step, so it is carried along instead of
+// divided out per item.
 template <typename F>
 __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem,
                                                F&& compute) {
@@ -247,9 +251,6 @@ __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& 
   const uint64_t frames = pl.n * a.in[0].rate;
   const uint32_t bands = (uint32_t)((H + band - 1) / band);
   const size_t sb = (size_t)(band + 4) * W;                        // one staging buffer
-  uint64_t f;
-  uint32_t b;
-  div_item(g.b, bands, f, b);
   uint64_t fq;
   uint32_t fr;
   div_item(g.n, bands, fq, fr);
@@ -262,28 +263,37 @@ __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& 
     }
   };
   __shared__ uint8_t* out_frames[kMaxPorts];
-  int buf = 0;
-  if (f < frames) stage_rows(img_frame(a.in[0], pl.slot_in[0], f), smem, W, H, (int)b * band, band);
-  img_commit();
-  while (f < frames) {
-    uint64_t f1 = f;
-    uint32_t b1 = b;
-    next(f1, b1);
-    if (f1 < frames) stage_rows(img_frame(a.in[0], pl.slot_in[0], f1), smem + (buf ^ 1) * sb, W, H, (int)b1 * band, band);
+  // cur: the item computed next; ahead: the next item to stage
+  uint64_t f, fa;
+  uint32_t b, ba;
+  div_item(g.b, bands, f, b);
+  fa = f;
+  ba = b;
+  int slot = 0;
+#pragma unroll
+  for (int i = 0; i < kImgStages - 1; ++i) {
+    if (fa < frames) stage_rows(img_frame(a.in[0], pl.slot_in[0], fa), smem + i * sb, W, H, (int)ba * band, band);
     img_commit();
+    next(fa, ba);
+  }
+  while (f < frames) {
+    // stage the item kImgStages - 1 ahead into the buffer freed last round
+    const int sa = (slot + kImgStages - 1) % kImgStages;
+    if (fa < frames) stage_rows(img_frame(a.in[0], pl.slot_in[0], fa), smem + sa * sb, W, H, (int)ba * band, band);
+    img_commit();
+    next(fa, ba);
     const int y0 = (int)b * band;
     // this item's output frames, one per port
     if (threadIdx.x < a.n_out) {
       const int p = threadIdx.x;
       out_frames[p] = img_frame(a.out[p], pl.slot_out[p], f);
     }
-    img_wait_prev();
+    img_wait_stages();
     __syncthreads();
-    compute(y0, min(y0 + band, H), smem + buf * sb, out_frames);
+    compute(y0, min(y0 + band, H), smem + slot * sb, out_frames);
     __syncthreads();
-    buf ^= 1;
-    f = f1;
-    b = b1;
+    slot = (slot + 1) % kImgStages;
+    next(f, b);
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -298,73 +308,57 @@ __device__ __forceinline__ void vsum5(uint32_t a, uint32_t b, uint32_t c, uint32
        4u * (__byte_perm(b, 0, 0x4341) + __byte_perm(d, 0, 0x4341)) + 6u * __byte_perm(c, 0, 0x4341);
 }
 
-// Horizontal pass of 4 pixels from the vertical sums v[x-2] .. v[x+5] as four
-// u16 pairs: pairs (v_i, v_{i+2}) for the even pixels x, x+2 and the odd
-// pixels x+1, x+3; each 16-bit lane of the weighted sum stays below 65536.
-__device__ __forceinline__ uint32_t hsum5(uint32_t w01, uint32_t w23, uint32_t w45, uint32_t w67) {
-  const uint32_t s02 = __byte_perm(w01, w23, 0x5410), s13 = __byte_perm(w01, w23, 0x7632);
-  const uint32_t s24 = __byte_perm(w23, w45, 0x5410), s35 = __byte_perm(w23, w45, 0x7632);
-  const uint32_t s46 = __byte_perm(w45, w67, 0x5410), s57 = __byte_perm(w45, w67, 0x7632);
-  const uint32_t he = s02 + 4 * s13 + 6 * s24 + 4 * s35 + s46 + 0x00800080u;
-  const uint32_t ho = s13 + 4 * s24 + 6 * s35 + 4 * s46 + s57 + 0x00800080u;
+// Horizontal (1, 4, 6, 4, 1) of 4 pixels from the vertical sums of their word
+// (lo: pixels 0 and 2 in 16-bit lanes, hi: pixels 1 and 3) and of the words
+// before and after; + 128, >> 8 (each 16-bit lane stays below 65536).
+__device__ __forceinline__ uint32_t hsum5w(uint32_t lo_p, uint32_t hi_p, uint32_t lo, uint32_t hi, uint32_t lo_n,
+                                           uint32_t hi_n) {
+  const uint32_t A = __byte_perm(lo_p, lo, 0x5432);               // (v-2, v0)
+  const uint32_t B = __byte_perm(hi_p, hi, 0x5432);               // (v-1, v1)
+  const uint32_t E = __byte_perm(lo, lo_n, 0x5432);               // (v2, v4)
+  const uint32_t F = __byte_perm(hi, hi_n, 0x5432);               // (v3, v5)
+  const uint32_t he = A + 4u * (B + hi) + 6u * lo + E + 0x00800080u;  // pixels 0, 2
+  const uint32_t ho = B + 4u * (lo + E) + 6u * hi + F + 0x00800080u;  // pixels 1, 3
   return ((he >> 8) & 0x00ff00ffu) | (((ho >> 8) & 0x00ff00ffu) << 8);
 }
 
-// Vertical sums: u16 rows of kImgVPitch(W) elements, pixel x at index x + 8
-// (16-byte aligned for x % 16 == 0), clamped columns -2, -1 at 6, 7 and W, W+1
-// at W + 8, W + 9.
-__host__ __device__ constexpr int kImgVPitch(int W) { return W + 16; }
-
-// Gauss over bands of img_band(W) rows, 16 pixels per thread and pass.  Vertical
-// sums of the 5 rows go to shared memory; the horizontal pass then weights 5
-// neighbouring sums, adds 128 and shifts right by 8.
+// Gauss over bands of img_band(W) rows, 16 pixels per thread: from the staged
+// rows y-2 .. y+2, the unit's 16 pixels and one word on each side give the
+// vertical sums in registers, then the horizontal pass; one pass per band, no
+// second barrier.  Columns -2, -1 and W, W+1 repeat columns 0 and W-1; rows
+// 0, 1, H-2, H-1 are copied.
 __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
-  uint16_t* v = reinterpret_cast<uint16_t*>(smem + 2 * (size_t)(img_band(W) + 4) * W);
-  const int vw = kImgVPitch(W);
   const UnitMap um = unit_map(W);
   for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
-    // vertical pass over the band's filtered rows (2 <= y < H-2)
-    const int fa = max(y0, 2), fb = min(y1, H - 2);
-    for_units(um, fa, fb, [&](int yr, int x) {
-      const uint8_t* col = s + (yr - y0) * W + x;                   // row yr-2
-      const uint4 r0 = *reinterpret_cast<const uint4*>(col);
-      const uint4 r1 = *reinterpret_cast<const uint4*>(col + W);
-      const uint4 r2 = *reinterpret_cast<const uint4*>(col + 2 * W);
-      const uint4 r3 = *reinterpret_cast<const uint4*>(col + 3 * W);
-      const uint4 r4 = *reinterpret_cast<const uint4*>(col + 4 * W);
-      uint32_t lo[4], hi[4];
-      vsum5(r0.x, r1.x, r2.x, r3.x, r4.x, lo[0], hi[0]);
-      vsum5(r0.y, r1.y, r2.y, r3.y, r4.y, lo[1], hi[1]);
-      vsum5(r0.z, r1.z, r2.z, r3.z, r4.z, lo[2], hi[2]);
-      vsum5(r0.w, r1.w, r2.w, r3.w, r4.w, lo[3], hi[3]);
-      uint16_t* vr = v + (yr - y0) * vw + 8;
-      const uint4 p0 = make_uint4(__byte_perm(lo[0], hi[0], 0x5410), __byte_perm(lo[0], hi[0], 0x7632),
-                                  __byte_perm(lo[1], hi[1], 0x5410), __byte_perm(lo[1], hi[1], 0x7632));
-      const uint4 p1 = make_uint4(__byte_perm(lo[2], hi[2], 0x5410), __byte_perm(lo[2], hi[2], 0x7632),
-                                  __byte_perm(lo[3], hi[3], 0x5410), __byte_perm(lo[3], hi[3], 0x7632));
-      *reinterpret_cast<uint4*>(vr + x) = p0;
-      *reinterpret_cast<uint4*>(vr + x + 8) = p1;
-      if (x == 0) vr[-1] = vr[-2] = (uint16_t)p0.x;                 // clamped columns -1, -2
-      if (x + 16 == W) vr[W] = vr[W + 1] = (uint16_t)(p1.w >> 16);  // clamped columns W, W+1
-    });
-    __syncthreads();
-    // horizontal pass and the unfiltered rows
     for_units(um, y0, y1, [&](int y, int x) {
       uint4 out;
+      const uint8_t* row = s + (y - y0 + 2) * W + x;                // row y
       if (y < 2 || y >= H - 2) {
-        out = *reinterpret_cast<const uint4*>(s + (y - y0 + 2) * W + x);
+        out = *reinterpret_cast<const uint4*>(row);
       } else {
-        // v[x-2] .. v[x+17] as ten u16 pairs
-        const uint16_t* vr = v + (y - y0) * vw + 8 + x;
-        const uint32_t w1 = *reinterpret_cast<const uint32_t*>(vr - 2);
-        const uint4 qa = *reinterpret_cast<const uint4*>(vr);
-        const uint4 qb = *reinterpret_cast<const uint4*>(vr + 8);
-        const uint32_t w10 = *reinterpret_cast<const uint32_t*>(vr + 16);
-        out.x = hsum5(w1, qa.x, qa.y, qa.z);
-        out.y = hsum5(qa.y, qa.z, qa.w, qb.x);
-        out.z = hsum5(qa.w, qb.x, qb.y, qb.z);
-        out.w = hsum5(qb.y, qb.z, qb.w, w10);
+        uint4 m[5];
+        uint32_t l[5], r[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          const uint8_t* ri = row + (i - 2) * W;
+          m[i] = *reinterpret_cast<const uint4*>(ri);
+          l[i] = x > 0 ? *reinterpret_cast<const uint32_t*>(ri - 4) : 0u;
+          r[i] = x + 16 < W ? *reinterpret_cast<const uint32_t*>(ri + 16) : 0u;
+        }
+        uint32_t lo[6], hi[6];
+        vsum5(l[0], l[1], l[2], l[3], l[4], lo[0], hi[0]);
+        vsum5(m[0].x, m[1].x, m[2].x, m[3].x, m[4].x, lo[1], hi[1]);
+        vsum5(m[0].y, m[1].y, m[2].y, m[3].y, m[4].y, lo[2], hi[2]);
+        vsum5(m[0].z, m[1].z, m[2].z, m[3].z, m[4].z, lo[3], hi[3]);
+        vsum5(m[0].w, m[1].w, m[2].w, m[3].w, m[4].w, lo[4], hi[4]);
+        vsum5(r[0], r[1], r[2], r[3], r[4], lo[5], hi[5]);
+        if (x == 0) lo[0] = hi[0] = lo[1] << 16;                     // v-2 = v-1 = v0
+        if (x + 16 == W) lo[5] = hi[5] = hi[4] >> 16;                // vW = vW+1 = vW-1
+        out = make_uint4(hsum5w(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]),
+                         hsum5w(lo[1], hi[1], lo[2], hi[2], lo[3], hi[3]),
+                         hsum5w(lo[2], hi[2], lo[3], hi[3], lo[4], hi[4]),
+                         hsum5w(lo[3], hi[3], lo[4], hi[4], lo[5], hi[5]));
       }
       const size_t o = (size_t)y * W + x;
       for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint4*>(of[p] + o) = out;
