@@ -308,18 +308,16 @@ __device__ __forceinline__ void vsum5(uint32_t a, uint32_t b, uint32_t c, uint32
        4u * (__byte_perm(b, 0, 0x4341) + __byte_perm(d, 0, 0x4341)) + 6u * __byte_perm(c, 0, 0x4341);
 }
 
-// Horizontal (1, 4, 6, 4, 1) of 4 pixels from the vertical sums of their word
-// (lo: pixels 0 and 2 in 16-bit lanes, hi: pixels 1 and 3) and of the words
-// before and after; + 128, >> 8 (each 16-bit lane stays below 65536).
-__device__ __forceinline__ uint32_t hsum5w(uint32_t lo_p, uint32_t hi_p, uint32_t lo, uint32_t hi, uint32_t lo_n,
-                                           uint32_t hi_n) {
-  const uint32_t A = __byte_perm(lo_p, lo, 0x5432);               // (v-2, v0)
-  const uint32_t B = __byte_perm(hi_p, hi, 0x5432);               // (v-1, v1)
-  const uint32_t E = __byte_perm(lo, lo_n, 0x5432);               // (v2, v4)
-  const uint32_t F = __byte_perm(hi, hi_n, 0x5432);               // (v3, v5)
-  const uint32_t he = A + 4u * (B + hi) + 6u * lo + E + 0x00800080u;  // pixels 0, 2
-  const uint32_t ho = B + 4u * (lo + E) + 6u * hi + F + 0x00800080u;  // pixels 1, 3
-  return ((he >> 8) & 0x00ff00ffu) | (((ho >> 8) & 0x00ff00ffu) << 8);
+// Horizontal (1, 4, 6, 4, 1) of 4 pixels x .. x+3 from 16-bit pairs of
+// vertical sums: A = (v[x-2], v[x]), B = (v[x-1], v[x+1]), lo = (v[x], v[x+2]),
+// hi = (v[x+1], v[x+3]), E = (v[x+2], v[x+4]), F = (v[x+3], v[x+5]); + 128, >> 8
+// (each 16-bit lane stays below 65536), the four result bytes picked out by
+// one byte permute.
+__device__ __forceinline__ uint32_t hsum5p(uint32_t A, uint32_t B, uint32_t lo, uint32_t hi, uint32_t E,
+                                           uint32_t F) {
+  const uint32_t he = A + 4u * (B + hi) + 6u * lo + E + 0x00800080u;  // pixels x, x+2
+  const uint32_t ho = B + 4u * (lo + E) + 6u * hi + F + 0x00800080u;  // pixels x+1, x+3
+  return __byte_perm(he, ho, 0x7351);
 }
 
 // Gauss over bands of img_band(W) rows, 16 pixels per thread: from the staged
@@ -337,28 +335,47 @@ __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, u
       if (y < 2 || y >= H - 2) {
         out = *reinterpret_cast<const uint4*>(row);
       } else {
+        // rows y-2 .. y+2: the unit's 16 pixels, and pixels x-2, x-1, x+16,
+        // x+17 gathered into one word per row
         uint4 m[5];
-        uint32_t l[5], r[5];
+        uint32_t e[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
           const uint8_t* ri = row + (i - 2) * W;
           m[i] = *reinterpret_cast<const uint4*>(ri);
-          l[i] = x > 0 ? *reinterpret_cast<const uint32_t*>(ri - 4) : 0u;
-          r[i] = x + 16 < W ? *reinterpret_cast<const uint32_t*>(ri + 16) : 0u;
+          const uint32_t l = x > 0 ? *reinterpret_cast<const uint32_t*>(ri - 4) : 0u;
+          const uint32_t r = x + 16 < W ? *reinterpret_cast<const uint32_t*>(ri + 16) : 0u;
+          e[i] = __byte_perm(l, r, 0x5432);
         }
-        uint32_t lo[6], hi[6];
-        vsum5(l[0], l[1], l[2], l[3], l[4], lo[0], hi[0]);
-        vsum5(m[0].x, m[1].x, m[2].x, m[3].x, m[4].x, lo[1], hi[1]);
-        vsum5(m[0].y, m[1].y, m[2].y, m[3].y, m[4].y, lo[2], hi[2]);
-        vsum5(m[0].z, m[1].z, m[2].z, m[3].z, m[4].z, lo[3], hi[3]);
-        vsum5(m[0].w, m[1].w, m[2].w, m[3].w, m[4].w, lo[4], hi[4]);
-        vsum5(r[0], r[1], r[2], r[3], r[4], lo[5], hi[5]);
-        if (x == 0) lo[0] = hi[0] = lo[1] << 16;                     // v-2 = v-1 = v0
-        if (x + 16 == W) lo[5] = hi[5] = hi[4] >> 16;                // vW = vW+1 = vW-1
-        out = make_uint4(hsum5w(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]),
-                         hsum5w(lo[1], hi[1], lo[2], hi[2], lo[3], hi[3]),
-                         hsum5w(lo[2], hi[2], lo[3], hi[3], lo[4], hi[4]),
-                         hsum5w(lo[3], hi[3], lo[4], hi[4], lo[5], hi[5]));
+        // vertical sums: lo[w] = (v[4w], v[4w+2]), hi[w] = (v[4w+1], v[4w+3]);
+        // le = (v[-2], v[16]), he_ = (v[-1], v[17])
+        uint32_t lo[4], hi[4], le, he_;
+        vsum5(m[0].x, m[1].x, m[2].x, m[3].x, m[4].x, lo[0], hi[0]);
+        vsum5(m[0].y, m[1].y, m[2].y, m[3].y, m[4].y, lo[1], hi[1]);
+        vsum5(m[0].z, m[1].z, m[2].z, m[3].z, m[4].z, lo[2], hi[2]);
+        vsum5(m[0].w, m[1].w, m[2].w, m[3].w, m[4].w, lo[3], hi[3]);
+        vsum5(e[0], e[1], e[2], e[3], e[4], le, he_);
+        if (x == 0) {                                                       // v[-2] = v[-1] = v[0]
+          le = (le & 0xffff0000u) | (lo[0] & 0xffffu);
+          he_ = (he_ & 0xffff0000u) | (lo[0] & 0xffffu);
+        }
+        if (x + 16 == W) {                                                  // v[16] = v[17] = v[15]
+          le = (le & 0xffffu) | (hi[3] & 0xffff0000u);
+          he_ = (he_ & 0xffffu) | (hi[3] & 0xffff0000u);
+        }
+        // pairs (v[4w-2], v[4w]) and (v[4w-1], v[4w+1]), w = 0 .. 4
+        uint32_t A[5], B[5];
+        A[0] = __byte_perm(le, lo[0], 0x5410);
+        B[0] = __byte_perm(he_, hi[0], 0x5410);
+#pragma unroll
+        for (int w = 1; w < 4; ++w) {
+          A[w] = __byte_perm(lo[w - 1], lo[w], 0x5432);
+          B[w] = __byte_perm(hi[w - 1], hi[w], 0x5432);
+        }
+        A[4] = __byte_perm(lo[3], le, 0x7632);
+        B[4] = __byte_perm(hi[3], he_, 0x7632);
+        out = make_uint4(hsum5p(A[0], B[0], lo[0], hi[0], A[1], B[1]), hsum5p(A[1], B[1], lo[1], hi[1], A[2], B[2]),
+                         hsum5p(A[2], B[2], lo[2], hi[2], A[3], B[3]), hsum5p(A[3], B[3], lo[3], hi[3], A[4], B[4]));
       }
       const size_t o = (size_t)y * W + x;
       for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint4*>(of[p] + o) = out;
