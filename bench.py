@@ -1085,6 +1085,89 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """--case NAME: that workload's engine network alone, args.warmup + args.steps
+    eager steps of push, run(1), pop (no headline, no CPU baselines, no JSON line).
+    The ncu summaries under profiles/ are taken on this command, the kernel
+    filtered by name and the warm-up launches skipped (-s)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1611_03226_b300 as P
+    work = torch.cuda.Stream()
+    with torch.cuda.stream(work):
+        net = P.Net(stream=work.cuda_stream)
+        if args.case == "dpd_large":
+            nb = args.case_blocks
+            w = synth.dpd_large(n_blocks=nb)
+            Lb = w.block_len
+            dev = torch.from_numpy(np.stack(gen_parallel(w.block, nb))).to("cuda")
+            masks = torch.from_numpy(w.masks.copy()).to("cuda")
+            c, d, a, s = net.add_source(), net.add_source(), net.add_dpd(w.h, w.orders, Lb), net.add_sink()
+            net.connect(c, 0, a, 0, 4, 1, nb + w.delay)
+            net.connect(d, 0, a, 1, Lb * 8, 1, nb + w.delay, w.delay)
+            net.connect(a, 0, s, 0, Lb * 8, 1, nb + w.delay)
+            net.finalize()
+            net.set_tile(a, 4096, 256)
+            out = torch.empty((nb + w.delay, Lb), dtype=torch.complex64, device="cuda")
+            push = lambda: (net.push(c, masks), net.push(d, dev))
+            pop = lambda: net.pop(s, out=out)
+        elif args.case == "dpd_batch":
+            w = synth.dpd_batch()
+            C, nb = w.n_channels, w.blocks_per_channel
+            pairs = [(ch, b) for ch in range(C) for b in range(nb)]
+            blocks = gen_parallel(lambda i: w.block(*pairs[i]), len(pairs))
+            dev = [torch.from_numpy(np.stack(blocks[ch * nb:(ch + 1) * nb])).to("cuda") for ch in range(C)]
+            masks = [torch.full((nb,), int(w.masks[ch]), dtype=torch.int32, device="cuda") for ch in range(C)]
+            outs = [torch.empty_like(x) for x in dev]
+            ids = []
+            for ch in range(C):
+                Lc = int(w.lengths[ch])
+                ids.append((net.add_source(), net.add_source(), net.add_dpd(w.h[ch], w.orders, Lc), net.add_sink()))
+                cs, ds, a, sk = ids[-1]
+                net.connect(cs, 0, a, 0, 4, 1, nb)
+                net.connect(ds, 0, a, 1, Lc * 8, 1, nb)
+                net.connect(a, 0, sk, 0, Lc * 8, 1, nb)
+            net.finalize()
+            for cs, ds, a, sk in ids:
+                net.set_tile(a, 4096, 256)
+
+            def push():
+                for ch, (cs, ds, a, sk) in enumerate(ids):
+                    net.push(cs, masks[ch])
+                    net.push(ds, dev[ch])
+
+            def pop():
+                for ch, (cs, ds, a, sk) in enumerate(ids):
+                    net.pop(sk, out=outs[ch])
+        else:                                      # md_paper
+            T, H, W, rate, thr = 4096, 240, 320, 4, 20
+            wm = synth.motion(n_frames=T, height=H, width=W)
+            dev = torch.from_numpy(np.stack(gen_parallel(wm.frame, T))).to("cuda")
+            out = torch.empty_like(dev)
+            src, g, t, m, snk = (net.add_source(), net.add_gauss5(W, H), net.add_thres(W, H, thr),
+                                 net.add_med5(W, H), net.add_sink())
+            fb = H * W
+            net.connect(src, 0, g, 0, fb, rate, T + 1)
+            net.connect(g, 0, t, 0, fb, rate, T + 1)
+            net.connect(g, 1, t, 1, fb, rate, T + 1, 1)
+            net.connect(t, 0, m, 0, fb, rate, T + 1)
+            net.connect(m, 0, snk, 0, fb, rate, T + 1)
+            net.finalize()
+            push = lambda: net.push(src, dev)
+            pop = lambda: net.pop(snk, out=out)
+        ms = []
+        for i in range(args.warmup + args.steps):
+            push()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            net.run(1)
+            ms.append(1e3 * (time.perf_counter() - t0))
+            pop()
+        net.close()
+    print(f"{args.case}: {args.steps} steps after {args.warmup} warm-up, host-timed step "
+          f"{statistics.mean(ms[args.warmup:]):.3f} ms")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1095,9 +1178,15 @@ def main():
     ap.add_argument("--only", default=None,
                     help="comma-separated secondary workloads to run besides the motion headline "
                          "(dpd_large, dpd_tiny, dpd_batch, dpd_fit, md_paper; 'motion' = none)")
+    ap.add_argument("--case", default=None, choices=["dpd_large", "dpd_batch", "md_paper"],
+                    help="run one workload's network alone for a profiler capture (no JSON line)")
+    ap.add_argument("--case-blocks", type=int, default=64, help="blocks of the dpd_large case")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:
