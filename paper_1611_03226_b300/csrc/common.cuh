@@ -53,7 +53,7 @@ struct EngineDev {          // device-resident engine state
 };
 
 // where-codes for EngineDev::status_where
-enum : int32_t { kWhereMdPipe = 1, kWhereGridBarrier = 2, kWhereDpd = 3 };
+enum : int32_t { kWhereMdPipe = 1, kWhereGridBarrier = 2, kWhereDpd = 3, kWhereImgStage = 4 };
 
 // Virtual grid: block index and block count of a phase (the launch's own grid
 // for the per-phase kernels, the persistent kernel's grid otherwise).
@@ -124,6 +124,7 @@ struct ImgArgs {
   int W, H, thr;
   int dedup;                // Thres: in[1] is in[0]'s stream delayed by one token (same broadcast writer)
   int binary_in;            // Med: every input byte is 0 or 255 (written by Thres, initial tokens binary)
+  long long wait_limit_ns;  // bound of every device-side wait
   uint64_t* ctr;
   EngineDev* eng;
   ImgPlan* plan;
@@ -134,13 +135,10 @@ struct ImgArgs {
 __host__ __device__ constexpr int img_band(int W) { return W <= 1024 ? 32 : 16; }
 constexpr int kImgThreads = 256;
 constexpr int kImgMaxWidth = 2048;
-// staging buffers of an image body CTA: the band being computed and the
-// bands being loaded
-constexpr int kImgStages = 2;
-// shared memory of an image body CTA: kImgStages staging buffers of input
-// rows (band + 2-row halo each side)
+// shared memory of an image body CTA: two staging buffers of input rows
+// (band + 2-row halo each side), the band being computed and the next one
 __host__ __device__ constexpr size_t img_smem_bytes(int W) {
-  return kImgStages * (size_t)(img_band(W) + 4) * W + 16;
+  return 2 * (size_t)(img_band(W) + 4) * W + 16;
 }
 
 // --------------------------------------------------- fused predistorter ----

@@ -192,65 +192,91 @@ __device__ inline void thres_body(const ImgArgs& a, const ImgPlan& pl, Grid g) {
   }
 }
 
-// Start copying input rows y0-2 .. y0+band+1 (those inside the frame) of
-// one frame into s (row y at s + (y - y0 + 2) * W) with 16-byte asynchronous
-// copies; the caller commits and waits.
-__device__ __forceinline__ void stage_rows(const uint8_t* frame, uint8_t* s, int W, int H, int y0, int band) {
+// ---------------------------------------------------- band staging ----
+// The input rows of a band item (band rows plus a 2-row halo each side, those
+// inside the frame) are contiguous in the frame, so one bulk asynchronous
+// copy, issued by one thread and completing on an mbarrier, stages them.
+__device__ __forceinline__ uint32_t img_smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ long long img_timer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool img_bar_done(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait until the phase of the given parity has completed, at most limit_ns.
+__device__ __forceinline__ bool img_bar_wait(uint32_t bar, uint32_t parity, long long limit_ns) {
+  if (img_bar_done(bar, parity)) return true;
+  const long long t0 = img_timer_ns();
+  while (!img_bar_done(bar, parity))
+    if (img_timer_ns() - t0 > limit_ns) return false;
+  return true;
+}
+// Thread 0: the rows of item (frame f, band starting at row y0) into buffer s
+// (row y at s + (y - y0 + 2) * W), completing on bar.
+__device__ __forceinline__ void img_stage(const uint8_t* frame, uint8_t* s, int W, int H, int y0, int band,
+                                          uint32_t bar) {
   const int ya = max(y0 - 2, 0), yb = min(y0 + band + 2, H);
-  const int vpr = W / 16;
-  const int nv = (yb - ya) * vpr;
-  const uint8_t* src = frame + (size_t)ya * W;
-  uint8_t* dst = s + (size_t)(ya - y0 + 2) * W;
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + 16 * v));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + 16 * v) : "memory");
-  }
-}
-__device__ __forceinline__ void img_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// all but the kImgStages - 1 most recent groups complete: the oldest staged item is in
-__device__ __forceinline__ void img_wait_stages() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(kImgStages - 1) : "memory");
+  const uint32_t bytes = (uint32_t)(yb - ya) * (uint32_t)W;        // a multiple of 16 (W is)
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   img_smem_addr(s + (size_t)(ya - y0 + 2) * W)),
+               "l"(frame + (size_t)ya * W), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
-// A thread's walk over the 16-pixel units of W-pixel rows: unit e = tid +
-// k * blockDim.x of a row range is (row e / q, column e % q), q = W / 16.
-// The start and the stride are fixed per thread, so they are computed once.
-struct UnitMap {
-  int row0, col0, drow, dcol, q;
+// The 16-pixel units of one band that a thread takes: units e = tid, tid +
+// blockDim, .. of the band's band * q units (q = W / 16) are (row e / q,
+// column 16 (e % q)); the first and the step are fixed per thread, so they
+// are computed once and the walk steps instead of dividing.
+struct BandUnits {
+  int n;                       // units of this thread in a full band
+  int dy0, c0;                 // first unit: row within the band, column / 16
+  int drow, dcol, q;           // step between the thread's units
 };
-__device__ __forceinline__ UnitMap unit_map(int W) {
-  const int q = W / 16;
-  return UnitMap{(int)threadIdx.x / q, (int)threadIdx.x % q, (int)blockDim.x / q, (int)blockDim.x % q, q};
+__device__ __forceinline__ BandUnits band_units(int W, int band) {
+  const int q = W / 16, total = band * q, t = (int)threadIdx.x, nt = (int)blockDim.x;
+  return BandUnits{t < total ? (total - t + nt - 1) / nt : 0, t / q, t % q, nt / q, nt % q, q};
 }
 
-// Calls f(y, x) for every row y in [ya, yb) and 16-pixel unit x = 0, 16, ..
-// of the row, spread over the CTA's threads as the map says.
-template <typename F>
-__device__ __forceinline__ void for_units(const UnitMap& m, int ya, int yb, F&& f) {
-  int y = ya + m.row0, c = m.col0;
-  while (y < yb) {
-    f(y, 16 * c);
-    y += m.drow;
-    c += m.dcol;
-    if (c >= m.q) {
-      c -= m.q;
-      ++y;
-    }
-  }
-}
-
-// Band items (frame, band of img_band(W) rows) of this CTA with the input
-// rows of the next kImgStages - 1 items staged while the current one is
-// computed (a ring of kImgStages buffers).  Items g.b, g.b + g.n, ..:
-// (frame, band) advances by a fixed step, so it is carried along instead of
-// divided out per item.
+// Band items (frame, band of img_band(W) rows) of this CTA, the next item's
+// rows staged while the current one is computed (two buffers, two
+// mbarriers).  Items g.b, g.b + g.n, ..: (frame, band) advances by a fixed
+// step, so it is carried along instead of divided out per item.  unit(y, x,
+// row) returns the 16 output pixels of unit (y, x), row = its row y in the
+// staging buffer; they are stored to every output frame.  Every wait is
+// bounded: one that runs out records DF_ETIMEOUT, and thread 0 waits (bounded)
+// for the copies still in flight before the CTA leaves.
 template <typename F>
 __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem,
-                                               F&& compute) {
+                                               F&& unit) {
   const int W = a.W, H = a.H, band = img_band(W);
   const uint64_t frames = pl.n * a.in[0].rate;
   const uint32_t bands = (uint32_t)((H + band - 1) / band);
   const size_t sb = (size_t)(band + 4) * W;                        // one staging buffer
+  const long long limit = a.wait_limit_ns;
+  __shared__ __align__(8) unsigned long long s_bar[2];
+  __shared__ uint8_t* out_frames[kMaxPorts];
+  const uint32_t bar0 = img_smem_addr(&s_bar[0]);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  const BandUnits bu = band_units(W, band);
   uint64_t fq;
   uint32_t fr;
   div_item(g.n, bands, fq, fr);
@@ -262,40 +288,75 @@ __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& 
       ++nf;
     }
   };
-  __shared__ uint8_t* out_frames[kMaxPorts];
-  // cur: the item computed next; ahead: the next item to stage
-  uint64_t f, fa;
-  uint32_t b, ba;
+  uint64_t f;
+  uint32_t b;
   div_item(g.b, bands, f, b);
-  fa = f;
-  ba = b;
-  int slot = 0;
-#pragma unroll
-  for (int i = 0; i < kImgStages - 1; ++i) {
-    if (fa < frames) stage_rows(img_frame(a.in[0], pl.slot_in[0], fa), smem + i * sb, W, H, (int)ba * band, band);
-    img_commit();
-    next(fa, ba);
+  uint32_t phase = 0;                  // bit i: parity of buffer i's next phase
+  uint32_t pending = 0;                // bit i: a copy into buffer i not yet waited for
+  int buf = 0;
+  if (f < frames) {
+    if (threadIdx.x == 0)
+      img_stage(img_frame(a.in[0], pl.slot_in[0], f), smem, W, H, (int)b * band, band, bar0);
+    pending = 1;
   }
+  bool ok = true;
   while (f < frames) {
-    // stage the item kImgStages - 1 ahead into the buffer freed last round
-    const int sa = (slot + kImgStages - 1) % kImgStages;
-    if (fa < frames) stage_rows(img_frame(a.in[0], pl.slot_in[0], fa), smem + sa * sb, W, H, (int)ba * band, band);
-    img_commit();
-    next(fa, ba);
-    const int y0 = (int)b * band;
-    // this item's output frames, one per port
-    if (threadIdx.x < a.n_out) {
-      const int p = threadIdx.x;
-      out_frames[p] = img_frame(a.out[p], pl.slot_out[p], f);
+    uint64_t f1 = f;
+    uint32_t b1 = b;
+    next(f1, b1);
+    if (f1 < frames) {
+      // the buffer was released by the barrier at the end of the last item
+      if (threadIdx.x == 0)
+        img_stage(img_frame(a.in[0], pl.slot_in[0], f1), smem + (buf ^ 1) * sb, W, H, (int)b1 * band, band,
+                  bar0 + 8 * (buf ^ 1));
+      pending |= 1u << (buf ^ 1);
     }
-    img_wait_stages();
+    if (threadIdx.x < a.n_out) out_frames[threadIdx.x] = img_frame(a.out[threadIdx.x], pl.slot_out[threadIdx.x], f);
+    const bool arrived = img_bar_wait(bar0 + 8 * buf, (phase >> buf) & 1u, limit);
+    if (!__syncthreads_and(arrived)) {
+      ok = false;
+      break;
+    }
+    phase ^= 1u << buf;
+    pending &= ~(1u << buf);
+    const int y0 = (int)b * band, y1 = min(y0 + band, H);
+    const uint8_t* s = smem + buf * sb;
+    uint8_t* o0 = out_frames[0] + (size_t)y0 * W;
+    uint8_t* o1 = a.n_out > 1 ? out_frames[1] + (size_t)y0 * W : nullptr;
+    int dy = bu.dy0, c = bu.c0;
+    for (int k = 0; k < bu.n; ++k) {
+      if (y0 + dy < y1) {
+        const int x = 16 * c;
+        const int o = dy * W + x;                      // within the band's rows
+        const uint4 out = unit(y0 + dy, x, s + 2 * W + o);
+        *reinterpret_cast<uint4*>(o0 + o) = out;
+        if (o1) *reinterpret_cast<uint4*>(o1 + o) = out;
+        for (int p = 2; p < a.n_out; ++p) *reinterpret_cast<uint4*>(out_frames[p] + (size_t)y0 * W + o) = out;
+      }
+      dy += bu.drow;
+      c += bu.dcol;
+      if (c >= bu.q) {
+        c -= bu.q;
+        ++dy;
+      }
+    }
     __syncthreads();
-    compute(y0, min(y0 + band, H), smem + slot * sb, out_frames);
-    __syncthreads();
-    slot = (slot + 1) % kImgStages;
-    next(f, b);
+    buf ^= 1;
+    f = f1;
+    b = b1;
   }
-  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (!ok && threadIdx.x == 0) {
+    set_status(a.eng, DF_ETIMEOUT, kWhereImgStage);
+    for (int i = 0; i < 2; ++i)
+      if (pending & (1u << i)) img_bar_wait(bar0 + 8 * i, (phase >> i) & 1u, limit);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the barriers may be initialised again by a later call (persistent kernel)
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0 + 8) : "memory");
+  }
+  __syncthreads();
 }
 
 // Weighted vertical sum (1, 4, 6, 4, 1) of five rows' 4-pixel words: pixels
@@ -327,11 +388,8 @@ __device__ __forceinline__ uint32_t hsum5p(uint32_t A, uint32_t B, uint32_t lo, 
 // 0, 1, H-2, H-1 are copied.
 __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
-  const UnitMap um = unit_map(W);
-  for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
-    for_units(um, y0, y1, [&](int y, int x) {
+  for_band_items(a, pl, g, smem, [&](int y, int x, const uint8_t* row) -> uint4 {
       uint4 out;
-      const uint8_t* row = s + (y - y0 + 2) * W + x;                // row y
       if (y < 2 || y >= H - 2) {
         out = *reinterpret_cast<const uint4*>(row);
       } else {
@@ -377,64 +435,53 @@ __device__ inline void gauss_body(const ImgArgs& a, const ImgPlan& pl, Grid g, u
         out = make_uint4(hsum5p(A[0], B[0], lo[0], hi[0], A[1], B[1]), hsum5p(A[1], B[1], lo[1], hi[1], A[2], B[2]),
                          hsum5p(A[2], B[2], lo[2], hi[2], A[3], B[3]), hsum5p(A[3], B[3], lo[3], hi[3], A[4], B[4]));
       }
-      const size_t o = (size_t)y * W + x;
-      for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint4*>(of[p] + o) = out;
-    });
+      return out;
   });
 }
 
 // Any byte of w neither 0x00 nor 0xff: a nonzero word.
 __device__ __forceinline__ uint32_t nonbinary_bits(uint32_t w) { return (w ^ (w << 1)) & 0xfefefefeu; }
 
-// Med over bands of img_band(W) rows, 16 pixels per thread.  When every input
-// byte of the band and its halo rows is 0 or 255 (every motion map) the median
-// is a bitwise majority; otherwise the bytewise min/max network runs.  The
-// test is one vote per band, skipped when the input is known to be binary
-// (its writer is Thres).
+// Med over bands of img_band(W) rows, 16 pixels per thread.  When the input
+// is known to be binary (its writer is Thres and its initial tokens are 0 or
+// 255), or every word a unit reads is, the median of five is a bitwise
+// majority; otherwise the bytewise min/max network runs.  Rows 0 and H-1 and
+// columns 0 and W-1 are copied.
 __device__ inline void med_body(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem) {
   const int W = a.W, H = a.H;
-  const UnitMap um = unit_map(W);
   const bool known_binary = a.binary_in != 0;
-  for_band_items(a, pl, g, smem, [&](int y0, int y1, const uint8_t* s, uint8_t* const* of) {
-    bool binary = true;
-    if (!known_binary) {
-      uint32_t nb = 0;
-      for_units(um, max(y0 - 1, 0), min(y1 + 1, H), [&](int y, int x) {
-        const uint4 c = *reinterpret_cast<const uint4*>(s + (y - y0 + 2) * W + x);
-        nb |= nonbinary_bits(c.x) | nonbinary_bits(c.y) | nonbinary_bits(c.z) | nonbinary_bits(c.w);
-      });
-      binary = __syncthreads_or(nb != 0) == 0;
+  for_band_items(a, pl, g, smem, [&](int y, int x, const uint8_t* row) -> uint4 {
+    const uint4 c = *reinterpret_cast<const uint4*>(row);
+    if (y < 1 || y >= H - 1) return c;
+    const uint4 up = *reinterpret_cast<const uint4*>(row - W);
+    const uint4 dn = *reinterpret_cast<const uint4*>(row + W);
+    const uint32_t pw = x > 0 ? *reinterpret_cast<const uint32_t*>(row - 4) : 0u;
+    const uint32_t nw = x + 16 < W ? *reinterpret_cast<const uint32_t*>(row + 16) : 0u;
+    const uint32_t cw[6] = {pw, c.x, c.y, c.z, c.w, nw};
+    const uint32_t uw[4] = {up.x, up.y, up.z, up.w}, dw[4] = {dn.x, dn.y, dn.z, dn.w};
+    bool binary = known_binary;
+    if (!binary) {
+      uint32_t nb = nonbinary_bits(pw) | nonbinary_bits(nw);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) nb |= nonbinary_bits(uw[j]) | nonbinary_bits(dw[j]) | nonbinary_bits(cw[j + 1]);
+      binary = nb == 0;
     }
-    for_units(um, y0, y1, [&](int y, int x) {
-      const uint8_t* row = s + (y - y0 + 2) * W;
-      const uint4 c = *reinterpret_cast<const uint4*>(row + x);
-      uint4 out = c;
-      if (y >= 1 && y < H - 1) {
-        const uint4 up = *reinterpret_cast<const uint4*>(row - W + x);
-        const uint4 dn = *reinterpret_cast<const uint4*>(row + W + x);
-        const uint32_t pw = x > 0 ? *reinterpret_cast<const uint32_t*>(row + x - 4) : 0u;
-        const uint32_t nw = x + 16 < W ? *reinterpret_cast<const uint32_t*>(row + x + 16) : 0u;
-        const uint32_t cw[6] = {pw, c.x, c.y, c.z, c.w, nw};
-        const uint32_t uw[4] = {up.x, up.y, up.z, up.w}, dw[4] = {dn.x, dn.y, dn.z, dn.w};
-        uint32_t m[4];
-        if (binary) {
+    uint32_t m[4];
+    if (binary) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            m[j] = maj5(uw[j], dw[j], __funnelshift_l(cw[j], cw[j + 1], 8), __funnelshift_r(cw[j + 1], cw[j + 2], 8),
-                        cw[j + 1]);
-        } else {
+      for (int j = 0; j < 4; ++j)
+        m[j] = maj5(uw[j], dw[j], __funnelshift_l(cw[j], cw[j + 1], 8), __funnelshift_r(cw[j + 1], cw[j + 2], 8),
+                    cw[j + 1]);
+    } else {
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            m[j] = med5_bytes(uw[j], dw[j], __funnelshift_l(cw[j], cw[j + 1], 8),
-                              __funnelshift_r(cw[j + 1], cw[j + 2], 8), cw[j + 1]);
-        }
-        out = make_uint4(m[0], m[1], m[2], m[3]);
-        if (x == 0) out.x = (out.x & 0xffffff00u) | (c.x & 0xffu);                 // column 0 copied
-        if (x + 16 == W) out.w = (out.w & 0x00ffffffu) | (c.w & 0xff000000u);      // column W-1 copied
-      }
-      const size_t o = (size_t)y * W + x;
-      for (int p = 0; p < a.n_out; ++p) *reinterpret_cast<uint4*>(of[p] + o) = out;
-    });
+      for (int j = 0; j < 4; ++j)
+        m[j] = med5_bytes(uw[j], dw[j], __funnelshift_l(cw[j], cw[j + 1], 8), __funnelshift_r(cw[j + 1], cw[j + 2], 8),
+                          cw[j + 1]);
+    }
+    uint4 out = make_uint4(m[0], m[1], m[2], m[3]);
+    if (x == 0) out.x = (out.x & 0xffffff00u) | (c.x & 0xffu);                 // column 0 copied
+    if (x + 16 == W) out.w = (out.w & 0x00ffffffu) | (c.w & 0xff000000u);      // column W-1 copied
+    return out;
   });
 }
 

@@ -986,6 +986,7 @@ df_status df_net_finalize(df_net* net) {
         for (uint8_t v : in.init_data) bin = bin && (v == 0 || v == 255);
         m.binary_in = bin ? 1 : 0;
       }
+      m.wait_limit_ns = net->wait_limit_ns;
       m.ctr = net->d_ctr;
       m.eng = net->d_eng;
       m.plan = reinterpret_cast<ImgPlan*>(base + ip[img_index[a]].off);
@@ -1559,6 +1560,7 @@ df_status df_set_wait_limit(df_net* net, int64_t limit_ns) {
   net->wait_limit_ns = limit_ns;
   for (Op& op : net->program)
     if (op.kind == kOpMd) op.md.wait_limit_ns = limit_ns;
+    else if (op.kind == kOpImg) op.img.wait_limit_ns = limit_ns;
   // captured graphs and the persistent kernel's program hold the old limit
   DeviceGuard g(net->device);
   DF_CUDA(cudaStreamSynchronize(net->stream));
