@@ -135,10 +135,13 @@ struct ImgArgs {
 __host__ __device__ constexpr int img_band(int W) { return W <= 1024 ? 32 : 16; }
 constexpr int kImgThreads = 256;
 constexpr int kImgMaxWidth = 2048;
-// shared memory of an image body CTA: two staging buffers of input rows
-// (band + 2-row halo each side), the band being computed and the next one
+// staging buffers of an image body CTA: the band being computed and the
+// next kImgBufs - 1 being loaded
+constexpr int kImgBufs = 2;
+// shared memory of an image body CTA: kImgBufs staging buffers of input rows
+// (band + 2-row halo each side)
 __host__ __device__ constexpr size_t img_smem_bytes(int W) {
-  return 2 * (size_t)(img_band(W) + 4) * W + 16;
+  return kImgBufs * (size_t)(img_band(W) + 4) * W + 16;
 }
 
 // --------------------------------------------------- fused predistorter ----

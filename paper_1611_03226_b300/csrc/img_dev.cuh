@@ -250,28 +250,29 @@ __device__ __forceinline__ BandUnits band_units(int W, int band) {
   return BandUnits{t < total ? (total - t + nt - 1) / nt : 0, t / q, t % q, nt / q, nt % q, q};
 }
 
-// Band items (frame, band of img_band(W) rows) of this CTA, the next item's
-// rows staged while the current one is computed (two buffers, two
-// mbarriers).  Items g.b, g.b + g.n, ..: (frame, band) advances by a fixed
-// step, so it is carried along instead of divided out per item.  unit(y, x,
-// row) returns the 16 output pixels of unit (y, x), row = its row y in the
-// staging buffer; they are stored to every output frame.  Every wait is
-// bounded: one that runs out records DF_ETIMEOUT, and thread 0 waits (bounded)
-// for the copies still in flight before the CTA leaves.
+// Band items (frame, band of img_band(W) rows) of this CTA, the rows of the
+// next kImgBufs - 1 items staged while the current one is computed (a ring of
+// kImgBufs buffers, one mbarrier each).  Items g.b, g.b + g.n, ..: (frame,
+// band) advances by a fixed step, so it is carried along instead of divided
+// out per item.  unit(y, x, row) returns the 16 output pixels of unit (y, x),
+// row = its row y in the staging buffer; they are stored to every output
+// frame.  Every wait is bounded: one that runs out records DF_ETIMEOUT, and
+// thread 0 waits (bounded) for the copies still in flight before the CTA
+// leaves.
 template <typename F>
 __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& pl, Grid g, uint8_t* smem,
                                                F&& unit) {
+  constexpr int NB = kImgBufs;
   const int W = a.W, H = a.H, band = img_band(W);
   const uint64_t frames = pl.n * a.in[0].rate;
   const uint32_t bands = (uint32_t)((H + band - 1) / band);
   const size_t sb = (size_t)(band + 4) * W;                        // one staging buffer
   const long long limit = a.wait_limit_ns;
-  __shared__ __align__(8) unsigned long long s_bar[2];
+  __shared__ __align__(8) unsigned long long s_bar[NB];
   __shared__ uint8_t* out_frames[kMaxPorts];
   const uint32_t bar0 = img_smem_addr(&s_bar[0]);
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+    for (int i = 0; i < NB; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * i) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -288,29 +289,34 @@ __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& 
       ++nf;
     }
   };
-  uint64_t f;
-  uint32_t b;
+  uint64_t f, fa;                      // the item computed next; the next item to stage
+  uint32_t b, ba;
   div_item(g.b, bands, f, b);
+  fa = f;
+  ba = b;
   uint32_t phase = 0;                  // bit i: parity of buffer i's next phase
   uint32_t pending = 0;                // bit i: a copy into buffer i not yet waited for
-  int buf = 0;
-  if (f < frames) {
-    if (threadIdx.x == 0)
-      img_stage(img_frame(a.in[0], pl.slot_in[0], f), smem, W, H, (int)b * band, band, bar0);
-    pending = 1;
+  for (int i = 0; i < NB - 1; ++i) {
+    if (fa < frames) {
+      if (threadIdx.x == 0)
+        img_stage(img_frame(a.in[0], pl.slot_in[0], fa), smem + i * sb, W, H, (int)ba * band, band, bar0 + 8 * i);
+      pending |= 1u << i;
+    }
+    next(fa, ba);
   }
+  int buf = 0;
   bool ok = true;
   while (f < frames) {
-    uint64_t f1 = f;
-    uint32_t b1 = b;
-    next(f1, b1);
-    if (f1 < frames) {
-      // the buffer was released by the barrier at the end of the last item
+    // the buffer computed last (released by the barrier that ended it) takes
+    // the item NB - 1 ahead
+    const int sa = buf == 0 ? NB - 1 : buf - 1;
+    if (fa < frames) {
       if (threadIdx.x == 0)
-        img_stage(img_frame(a.in[0], pl.slot_in[0], f1), smem + (buf ^ 1) * sb, W, H, (int)b1 * band, band,
-                  bar0 + 8 * (buf ^ 1));
-      pending |= 1u << (buf ^ 1);
+        img_stage(img_frame(a.in[0], pl.slot_in[0], fa), smem + sa * sb, W, H, (int)ba * band, band,
+                  bar0 + 8 * sa);
+      pending |= 1u << sa;
     }
+    next(fa, ba);
     if (threadIdx.x < a.n_out) out_frames[threadIdx.x] = img_frame(a.out[threadIdx.x], pl.slot_out[threadIdx.x], f);
     const bool arrived = img_bar_wait(bar0 + 8 * buf, (phase >> buf) & 1u, limit);
     if (!__syncthreads_and(arrived)) {
@@ -341,20 +347,18 @@ __device__ __forceinline__ void for_band_items(const ImgArgs& a, const ImgPlan& 
       }
     }
     __syncthreads();
-    buf ^= 1;
-    f = f1;
-    b = b1;
+    buf = buf == NB - 1 ? 0 : buf + 1;
+    next(f, b);
   }
   if (!ok && threadIdx.x == 0) {
     set_status(a.eng, DF_ETIMEOUT, kWhereImgStage);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < NB; ++i)
       if (pending & (1u << i)) img_bar_wait(bar0 + 8 * i, (phase >> i) & 1u, limit);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     // the barriers may be initialised again by a later call (persistent kernel)
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0 + 8) : "memory");
+    for (int i = 0; i < NB; ++i) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0 + 8 * i) : "memory");
   }
   __syncthreads();
 }
