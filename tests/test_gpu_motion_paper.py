@@ -91,10 +91,14 @@ def test_whole_video_in_one_run(Net):
 
 
 @pytest.mark.parametrize("kind", ["gauss", "med"])
-@pytest.mark.parametrize("H,W", [(240, 320), (19, 48), (3, 16)])
-def test_single_actor_on_gray_frames(Net, kind, H, W):
+@pytest.mark.parametrize("H,W,n_out", [
+    (240, 320, 2), (19, 48, 2), (3, 16, 2),
+    (37, 1040, 3),     # wider than 1024: 16-row bands, 65 units a row, a ragged last band, a third output
+    (20, 2048, 1),     # the widest frame: 2048 units a band, 8 a thread
+])
+def test_single_actor_on_gray_frames(Net, kind, H, W, n_out):
     """Gauss or Med alone on arbitrary 8-bit frames (the median's general path,
-    not only the 0/255 maps the pipeline feeds it), two output channels."""
+    not only the 0/255 maps the pipeline feeds it), one to three output channels."""
     T, rate = 6, 2
     f = synth.uniform_frames(T, H, W, seed=11) if H < 16 else synth.motion(n_frames=T, height=H, width=W).frames()
     if kind == "med":
@@ -103,15 +107,15 @@ def test_single_actor_on_gray_frames(Net, kind, H, W):
     fb = H * W
     src = net.add_source()
     act = net.add_gauss5(W, H) if kind == "gauss" else net.add_med5(W, H)
-    s0, s1 = net.add_sink(), net.add_sink()
+    sinks = [net.add_sink() for _ in range(n_out)]
     net.connect(src, 0, act, 0, fb, rate, T)
-    net.connect(act, 0, s0, 0, fb, rate, T)
-    net.connect(act, 1, s1, 0, fb, rate, T)
+    for p, s in enumerate(sinks):
+        net.connect(act, p, s, 0, fb, rate, T)
     net.finalize()
     net.push(src, f)
     assert net.run(-1) == T // rate
     want = np.stack([(MP.gauss5 if kind == "gauss" else MP.med5)(x) for x in f])
-    for s in (s0, s1):
+    for s in sinks:
         np.testing.assert_array_equal(net.pop(s, dtype=np.uint8).reshape(T, H, W), want)
     net.close()
 
