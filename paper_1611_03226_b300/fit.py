@@ -52,22 +52,27 @@ def adam_fit(u: torch.Tensor, target: torch.Tensor, h0: torch.Tensor, orders, st
 
     graph=True records one whole training step (forward, loss, adjoint, Adam update)
     as a CUDA graph and replays it `steps` times, so the host issues one launch
-    per step instead of a few dozen; graph=False runs the same step eagerly."""
-    h = h0.detach().clone().requires_grad_(True)
+    per step instead of a few dozen; graph=False runs the same step eagerly.
+    The captured step's update is torch's fused Adam (one kernel) on the real
+    view of the taps."""
+    # the taps as a real (K, M, 2) leaf: Adam's moments are then per real and
+    # imaginary part (the oracle's update), and in the captured step torch's
+    # fused Adam (one kernel) does the update
+    hr = torch.view_as_real(h0.detach()).clone().requires_grad_(True)
     if not graph:
-        opt = torch.optim.Adam([h], lr=lr)
+        opt = torch.optim.Adam([hr], lr=lr)
         losses = []
         for _ in range(steps):
             opt.zero_grad(set_to_none=True)
-            loss = dpd_mse(u, h, target, orders)
+            loss = dpd_mse(u, torch.view_as_complex(hr), target, orders)
             loss.backward()
             opt.step()
             losses.append(loss.detach())
-        return h.detach(), torch.stack(losses).cpu().numpy()
-    opt = torch.optim.Adam([h], lr=lr, capturable=True)
+        return torch.view_as_complex(hr.detach()).clone(), torch.stack(losses).cpu().numpy()
+    opt = torch.optim.Adam([hr], lr=lr, capturable=True, fused=True)
 
     def train_step():
-        loss = dpd_mse(u, h, target, orders)
+        loss = dpd_mse(u, torch.view_as_complex(hr), target, orders)
         loss.backward()
         opt.step()
         return loss.detach()
@@ -81,8 +86,8 @@ def adam_fit(u: torch.Tensor, target: torch.Tensor, h0: torch.Tensor, orders, st
             opt.zero_grad(set_to_none=True)
             train_step()
         with torch.no_grad():
-            h.copy_(h0)
-            for st in opt.state[h].values():
+            hr.copy_(torch.view_as_real(h0))
+            for st in opt.state[hr].values():
                 st.zero_()
     torch.cuda.current_stream(u.device).wait_stream(side)
     g = torch.cuda.CUDAGraph()
@@ -93,7 +98,7 @@ def adam_fit(u: torch.Tensor, target: torch.Tensor, h0: torch.Tensor, orders, st
     for i in range(steps):
         g.replay()
         losses[i].copy_(static_loss)
-    return h.detach().clone(), losses.cpu().numpy()
+    return torch.view_as_complex(hr.detach()).clone(), losses.cpu().numpy()
 
 
 def ila_fit(x: torch.Tensor, K=4, M=10, orders=(1, 3, 5, 7), steps=200, lr=1e-3,
