@@ -356,8 +356,8 @@ df_status df_profile_get(df_net *net, int32_t what, double *total_ms, uint64_t *
 /* Upper bound, in nanoseconds, of every device-side wait of the network (the
  * persistent kernel's grid barrier, the motion kernel's and the image actors'
  * staging waits); default one second.  A wait that runs out records
- * DF_ETIMEOUT in the status word and the kernel returns; later steps then do
- * nothing until the status word is cleared.
+ * DF_ETIMEOUT in the status word and the kernel returns; the status word stays
+ * set (df_run returns it, and persistent launches do nothing while it is set).
  * The paper has no counterpart (its actors block on mutexes, Sec. 3.3). */
 df_status df_set_wait_limit(df_net *net, int64_t limit_ns);
 
