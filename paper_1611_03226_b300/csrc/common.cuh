@@ -311,8 +311,8 @@ size_t md_smem_bytes(int W);
 cudaError_t persistent_prepare(size_t smem);
 size_t persistent_smem(int mtmax, int max_group);
 cudaError_t launch_persistent(const PersistOp* ops, int n_ops, EngineDev* eng, int64_t n_steps,
-                              long long limit_ns, int mtmax, size_t smem, int n_sm, bool publish,
-                              cudaStream_t s);
+                              long long limit_ns, int mtmax, size_t smem, int n_sm, int per_sm_cap,
+                              bool publish, cudaStream_t s);
 cudaError_t launch_barrier_selftest(EngineDev* eng, long long limit_ns, cudaStream_t s);
 
 cudaError_t dpd_forward_stateless(const float2* x, uint64_t n, const float2* h, int K, int M,

@@ -115,6 +115,7 @@ struct df_net {
   void* persist_mem = nullptr;
   PersistOp* d_persist_ops = nullptr;
   int persist_n_ops = 0, persist_mtmax = 16;
+  int persist_per_sm = 0;             // CTAs per SM of the persistent grid (0: as many as fit)
   size_t persist_smem = 0;
 };
 
@@ -437,6 +438,13 @@ df_status build_persistent(df_net* net) {
   size_t off = 0;
   int max_group = 1, mtmax = 1;
   size_t img_smem = 0;
+  // A program of predistorter groups alone whose largest step has no more
+  // items (chunks of 256 outputs) than a one-CTA-per-SM grid has warps runs
+  // on that grid: its steps are latency bound, and half the CTAs make the
+  // launch and every grid barrier cheaper (a 64 x 4096-sample stream through
+  // capacity-8 FIFOs: 19.2 -> 17.1 us per step).
+  bool dpd_only = true;
+  uint64_t max_items = 0;
   for (const Op& op : net->program) {
     PersistOp p{};
     if (op.kind == kOpCopy) {
@@ -467,7 +475,13 @@ df_status build_persistent(df_net* net) {
       p.order = op.dpd_order;
       max_group = std::max(max_group, op.dpd_n);
       mtmax = std::max(mtmax, op.max_mt);
+      const int i0 = net->dpd_index[op.dpd_first_actor];
+      for (int i = 0; i < op.dpd_n; ++i) {
+        const DpdArgs& d = net->dpd_host[i0 + i];
+        max_items += (uint64_t)d.n_max * ((d.L + 255) / 256);
+      }
     }
+    if (op.kind != kOpDpd) dpd_only = false;
     ops.push_back(p);
     if (!op.spills.empty()) {
       DF_CUDA(cudaMemcpyAsync(base + off, op.spills.data(), sizeof(SpillArgs) * op.spills.size(),
@@ -487,6 +501,7 @@ df_status build_persistent(df_net* net) {
   net->persist_n_ops = (int)ops.size();
   net->persist_mtmax = mtmax <= 16 ? 16 : 32;
   net->persist_smem = std::max(persistent_smem(net->persist_mtmax, max_group), img_smem);
+  net->persist_per_sm = dpd_only && max_items <= (uint64_t)net->n_sm * (kPersistThreads / 32) ? 1 : 0;
   DF_CUDA(persistent_prepare(net->persist_smem));
   DF_CUDA(cudaStreamSynchronize(net->stream));
   return DF_OK;
@@ -1219,7 +1234,7 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
         DF_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
         const cudaError_t le = launch_persistent(net->d_persist_ops, net->persist_n_ops, net->d_eng, n_steps,
                                                  net->wait_limit_ns, net->persist_mtmax, net->persist_smem,
-                                                 net->n_sm, publish, net->stream);
+                                                 net->n_sm, net->persist_per_sm, publish, net->stream);
         const cudaError_t ce = cudaStreamEndCapture(net->stream, &graph);
         DF_CUDA(le);
         DF_CUDA(ce);
@@ -1234,7 +1249,7 @@ df_status df_run_ex(df_net* net, int64_t n_steps, uint32_t flags, uint64_t* n_fi
       if (ev.first) DF_CUDA(cudaEventRecord(ev.first, net->stream));
       DF_CUDA(launch_persistent(net->d_persist_ops, net->persist_n_ops, net->d_eng, n_steps,
                                 net->wait_limit_ns, net->persist_mtmax, net->persist_smem, net->n_sm,
-                                publish, net->stream));
+                                net->persist_per_sm, publish, net->stream));
       if (ev.second) DF_CUDA(cudaEventRecord(ev.second, net->stream));
     }
   } else if (n_steps >= 0) {

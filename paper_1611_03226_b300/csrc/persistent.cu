@@ -251,10 +251,10 @@ size_t persistent_smem(int mtmax, int max_group) {
 // error leaves kBarrierError in the count, which later launches check first,
 // and whoever clears the status word clears the barrier state with it.
 cudaError_t launch_persistent(const PersistOp* ops, int n_ops, EngineDev* eng, int64_t n_steps,
-                              long long limit_ns, int mtmax, size_t smem, int n_sm, bool publish,
-                              cudaStream_t s) {
+                              long long limit_ns, int mtmax, size_t smem, int n_sm, int per_sm_cap,
+                              bool publish, cudaStream_t s) {
   const int idx = mtmax <= 16 ? 0 : 1;
-  const int per_sm = g_persist_blocks[idx];
+  const int per_sm = per_sm_cap > 0 ? std::min(per_sm_cap, g_persist_blocks[idx]) : g_persist_blocks[idx];
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   // a cooperative launch (all CTAs resident at once), also inside a CUDA graph capture
   cudaLaunchConfig_t cfg{};
