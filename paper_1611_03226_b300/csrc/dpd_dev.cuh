@@ -257,11 +257,12 @@ struct WItem {
   uint32_t i;               // firing
   uint32_t t0;              // first sample of the chunk
   int len;                  // samples of the chunk inside the block
+  int shift;                // staged window starts this many elements into its buffer
 };
 
 __device__ __forceinline__ WItem locate_w(const DpdArgs* args, const uint64_t* s_off, const uint16_t* s_ord,
                                           int G, uint64_t item, uint64_t total, uint32_t WI) {
-  WItem r{-1, 0, 0, 0};
+  WItem r{-1, 0, 0, 0, 0};
   if (item >= total) return r;
   int lo = 0, hi = G;                     // s_off[lo] <= item < s_off[hi]
   while (hi - lo > 1) {
@@ -285,19 +286,36 @@ __device__ __forceinline__ WItem locate_w(const DpdArgs* args, const uint64_t* s
   return r;
 }
 
-// Stage the x window of `it` into xs (position v holds sample t0 - (MT-1) + v
-// of the block, zero outside [0, t0 + len)) and its control mask into mask_dst.
-__device__ __forceinline__ void prefetch_w(const DpdArgs& a, const WItem& it, float2* xs, uint32_t* mask_dst,
+// Stage the x window of `it` into the buffer xb0 (position v holds sample
+// t0 - (MT-1) + v of the block, zero outside [0, t0 + len)) and its control
+// mask into mask_dst.  The window is copied as 16-byte pairs of samples from
+// the first 16-byte boundary at or before its start, so that every copy but
+// the edge pairs is a 16-byte one; it.shift records where position 0 landed.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void prefetch_w(const DpdArgs& a, WItem& it, float2* xb0, uint32_t* mask_dst,
                                            uint32_t WI, int lane) {
   const DpdPlanHdr* pl = a.plan;
   const float2* xb = reinterpret_cast<const float2*>(slot_at(a.data, pl->slot_data0, it.i));
   const int H1 = a.MT - 1;
   const int W = (int)WI + H1;
   const int end = (int)it.t0 + it.len;
-  for (int v = lane; v < W; v += 32) {
-    const int pos = (int)it.t0 - H1 + v;
-    const bool valid = pos >= 0 && pos < end;
-    cp_async8(xs + v, valid ? (const void*)(xb + pos) : (const void*)xb, valid);
+  const int pos0 = (int)it.t0 - H1;
+  const int par = (reinterpret_cast<uintptr_t>(xb) & 15) == 0 ? 0 : 1;   // sample indices on a 16-byte boundary
+  const int a0 = pos0 - ((pos0 - par) & 1);
+  it.shift = pos0 - a0;
+  const int npairs = (W + it.shift + 1) / 2;
+  for (int p = lane; p < npairs; p += 32) {
+    const int idx = a0 + 2 * p;
+    const bool v0 = idx >= 0 && idx < end, v1 = idx + 1 >= 0 && idx + 1 < end;
+    if (v0 && v1) {
+      cp_async16(xb0 + 2 * p, xb + idx);
+    } else {
+      cp_async8(xb0 + 2 * p, v0 ? (const void*)(xb + idx) : (const void*)xb, v0);
+      cp_async8(xb0 + 2 * p + 1, v1 ? (const void*)(xb + idx + 1) : (const void*)xb, v1);
+    }
   }
   if (lane == 0) {
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(mask_dst));
@@ -510,7 +528,7 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
   cp_async_commit();
   int buf = 0;
   while (cur.g >= 0) {
-    const WItem nxt = locate_w(args, s_off, s_ord, G, item_of(k + 1), total, WI);
+    WItem nxt = locate_w(args, s_off, s_ord, G, item_of(k + 1), total, WI);
     if (nxt.g >= 0) prefetch_w(args[nxt.g], nxt, xw + (buf ^ 1) * S::XW, mw + (buf ^ 1), WI, lane);
     cp_async_commit();
     const DpdArgs& a = args[cur.g];
@@ -522,7 +540,7 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
     }
     cp_async_wait1();
     __syncwarp();
-    const float2* xs = xw + buf * S::XW;
+    const float2* xs = xw + buf * S::XW + cur.shift;
     const uint32_t mask = mw[buf];
     if (mask == 0) {
       float2* yb = reinterpret_cast<float2*>(const_cast<uint8_t*>(slot_at(a.out, a.plan->slot_out0, cur.i))) +
