@@ -417,6 +417,14 @@ __device__ __forceinline__ void store_w(float2* yb, int len, int lane, const flo
 #pragma unroll
     for (int r = 0; r < R; r += 2)
       *reinterpret_cast<float4*>(yb + o0 + r) = make_float4(y[r].x, y[r].y, y[r + 1].x, y[r + 1].y);
+  } else if (len == 32 * R) {
+    // 8 bytes off a 16-byte boundary (a block of odd length in every other
+    // ring slot): one sample, 16-byte pairs, one sample
+    yb[o0] = y[0];
+#pragma unroll
+    for (int r = 1; r < R - 1; r += 2)
+      *reinterpret_cast<float4*>(yb + o0 + r) = make_float4(y[r].x, y[r].y, y[r + 1].x, y[r + 1].y);
+    yb[o0 + R - 1] = y[R - 1];
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r)
