@@ -227,8 +227,8 @@ __device__ __forceinline__ const uint8_t* slot_at(const ChanDesc& c, uint64_t sl
 //   zw[ZW]    float4  branch signal {zx, zx, zy, zy}; position v at v + v / R,
 //                     so that lanes reading at a stride of R positions hit
 //                     distinct banks
-//   hw[kMaxBranches * MTMAX + 2] float2  taps {hx, hy} of the warp's current
-//                     actor, then one byte per branch: q = (order - 1) / 2
+//   hw[kMaxBranches * MTMAX + 8] float2  taps {hx, hy} of the warp's current
+//                     actor, then its branch orders (int32)
 //   mw[2] u32         control masks of the two buffered items (staged with x)
 template <int R, int MTMAX>
 struct WarpSmem {
@@ -236,7 +236,7 @@ struct WarpSmem {
   static constexpr int ZW = XW + XW / R + 1;
   static constexpr size_t x_bytes = 2 * (size_t)XW * sizeof(float2);
   static constexpr size_t z_bytes = (size_t)ZW * sizeof(float4);
-  static constexpr size_t h_bytes = ((size_t)kMaxBranches * MTMAX + 2) * sizeof(float2);
+  static constexpr size_t h_bytes = ((size_t)kMaxBranches * MTMAX + kMaxBranches / 2) * sizeof(float2);
   static constexpr size_t m_bytes = 16;     // control masks of the two buffered items
   static constexpr size_t bytes = x_bytes + z_bytes + h_bytes + m_bytes;
 };
@@ -445,7 +445,7 @@ __device__ __noinline__ void dpd_item_w(const DpdArgs& a, const WItem& it, uint3
   unsigned long long P[R], Q[R];              // pairs of floats, +0.0f each
 #pragma unroll
   for (int r = 0; r < R; ++r) P[r] = Q[r] = 0ull;
-  const uint8_t* qk = reinterpret_cast<const uint8_t*>(hw + a.K * MT);
+  const int32_t* ok = reinterpret_cast<const int32_t*>(hw + a.K * MT);   // branch orders
   const bool first = it.t0 == 0;
   const bool short_block = a.L < (uint32_t)(MT - 1);
   int pv = -1;                                // lane k: prev[k][i]
@@ -454,7 +454,7 @@ __device__ __noinline__ void dpd_item_w(const DpdArgs& a, const WItem& it, uint3
   while (rest) {
     const int k = __ffs(rest) - 1;
     rest &= rest - 1;
-    const int q = qk[k];
+    const int q = (ok[k] - 1) >> 1;
     zpass_w<R>(xs, zw, lane, q);
     if (first) {
       const int f = __shfl_sync(0xffffffffu, pv, k);
@@ -536,17 +536,23 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
   cp_async_commit();
   int buf = 0;
   while (cur.g >= 0) {
+    const DpdArgs& a = args[cur.g];
+    if (cur.g != taps_of) {
+      // taps {hx, hy} of every branch, then the branch orders, by asynchronous
+      // copies waited for together with this item's x window
+      for (int e = lane; e < a.K * a.MT; e += 32) cp_async8(hw + e, a.h + e, true);
+      if (lane < a.K) {
+        const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(
+            reinterpret_cast<int32_t*>(hw + a.K * a.MT) + lane));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(a.orders + lane) : "memory");
+      }
+      taps_of = cur.g;
+    }
+    cp_async_commit();
     WItem nxt = locate_w(args, s_off, s_ord, G, item_of(k + 1), total, WI);
     if (nxt.g >= 0) prefetch_w(args[nxt.g], nxt, xw + (buf ^ 1) * S::XW, mw + (buf ^ 1), WI, lane);
     cp_async_commit();
-    const DpdArgs& a = args[cur.g];
-    if (cur.g != taps_of) {
-      // taps {hx, hy} of every branch, then q = (order - 1) / 2 per branch (bytes)
-      for (int e = lane; e < a.K * a.MT; e += 32) hw[e] = a.h[e];
-      if (lane < a.K) reinterpret_cast<uint8_t*>(hw + a.K * a.MT)[lane] = (uint8_t)((a.orders[lane] - 1) >> 1);
-      taps_of = cur.g;
-    }
-    cp_async_wait1();
+    cp_async_wait1();                                  // all but the next item's window
     __syncwarp();
     const float2* xs = xw + buf * S::XW + cur.shift;
     const uint32_t mask = mw[buf];
