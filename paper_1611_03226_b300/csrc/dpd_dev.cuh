@@ -450,22 +450,36 @@ __device__ __noinline__ void dpd_item_w(const DpdArgs& a, const WItem& it, uint3
   const bool short_block = a.L < (uint32_t)(MT - 1);
   int pv = -1;                                // lane k: prev[k][i]
   if (first && lane < a.K) pv = a.prev[(size_t)lane * a.n_max + it.i];
+  // the branch's MT-1 history samples (first chunks): with 8 outputs per lane
+  // loaded before the z-pass, which then hides their latency; with 16 the
+  // extra live registers across the z-pass cost more than that, so after it
+  auto head = [&](int k) {
+    float2 hx = make_float2(0.f, 0.f);
+    const int f = __shfl_sync(0xffffffffu, pv, k);
+    if (lane < MT - 1) {
+      if (short_block) hx = hist_sample(a, pl, it.i, k, lane);
+      else
+        hx = f >= 0 ? reinterpret_cast<const float2*>(slot_at(a.data, pl.slot_data0, (uint32_t)f))
+                          [a.L - (MT - 1) + lane]
+                    : a.hist[((size_t)pl.parity_in * a.K + k) * (MT - 1) + lane];
+    }
+    return hx;
+  };
   uint32_t rest = mask;
   while (rest) {
     const int k = __ffs(rest) - 1;
     rest &= rest - 1;
     const int q = (ok[k] - 1) >> 1;
-    zpass_w<R>(xs, zw, lane, q);
-    if (first) {
-      const int f = __shfl_sync(0xffffffffu, pv, k);
-      if (lane < MT - 1) {
-        float2 hx;
-        if (short_block) hx = hist_sample(a, pl, it.i, k, lane);
-        else
-          hx = f >= 0 ? reinterpret_cast<const float2*>(slot_at(a.data, pl.slot_data0, (uint32_t)f))
-                            [a.L - (MT - 1) + lane]
-                      : a.hist[((size_t)pl.parity_in * a.K + k) * (MT - 1) + lane];
-        zstore(zw, lane, R, hx, upow(fmaf(hx.x, hx.x, hx.y * hx.y), q));
+    if constexpr (R == 8) {
+      float2 hx = make_float2(0.f, 0.f);
+      if (first) hx = head(k);
+      zpass_w<R>(xs, zw, lane, q);
+      if (first && lane < MT - 1) zstore(zw, lane, R, hx, upow(fmaf(hx.x, hx.x, hx.y * hx.y), q));
+    } else {
+      zpass_w<R>(xs, zw, lane, q);
+      if (first) {
+        const float2 hx = head(k);
+        if (lane < MT - 1) zstore(zw, lane, R, hx, upow(fmaf(hx.x, hx.x, hx.y * hx.y), q));
       }
     }
     __syncwarp();
