@@ -260,29 +260,59 @@ struct WItem {
   int shift;                // staged window starts this many elements into its buffer
 };
 
+// Where item `item` of the group's work list is: a binary search over the
+// actors' first items, then firing and chunk by division.  The warp's last
+// answer is kept (LocHint): the next item of a run is the next chunk of the
+// same block or the first chunk of the next firing, and an item in the same
+// actor needs no search.
+struct LocHint {
+  int lo = -1;                  // position in the ordered actor list, -1: none
+  int g = -1;
+  uint32_t nt = 0, L = 0;       // chunks per block, samples per block
+  uint64_t beg = 0, end = 0;    // the actor's items [beg, end)
+  uint64_t item = ~0ull;        // last item located
+  uint32_t i = 0, t0 = 0;       // its firing and first sample
+};
+
 __device__ __forceinline__ WItem locate_w(const DpdArgs* args, const uint64_t* s_off, const uint16_t* s_ord,
-                                          int G, uint64_t item, uint64_t total, uint32_t WI) {
+                                          int G, uint64_t item, uint64_t total, uint32_t WI, LocHint& h) {
   WItem r{-1, 0, 0, 0, 0};
   if (item >= total) return r;
-  int lo = 0, hi = G;                     // s_off[lo] <= item < s_off[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (s_off[mid] <= item) lo = mid; else hi = mid;
-  }
-  const int g = s_ord[lo];
-  const DpdArgs& a = args[g];
-  const uint64_t local = item - s_off[lo];
-  const uint32_t nt = (a.L + WI - 1) / WI;
-  r.g = g;
-  if (local < 0xffffffffull) {
-    const uint32_t l32 = (uint32_t)local;
-    r.i = l32 / nt;
-    r.t0 = (l32 - r.i * nt) * WI;
+  if (h.lo >= 0 && item == h.item + 1 && item < h.end) {
+    h.t0 += WI;
+    if (h.t0 >= h.L) {
+      h.t0 = 0;
+      ++h.i;
+    }
   } else {
-    r.i = (uint32_t)(local / nt);
-    r.t0 = (uint32_t)(local % nt) * WI;
+    if (h.lo < 0 || item < h.beg || item >= h.end) {
+      int lo = 0, hi = G;                     // s_off[lo] <= item < s_off[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= item) lo = mid; else hi = mid;
+      }
+      h.lo = lo;
+      h.g = s_ord[lo];
+      h.L = args[h.g].L;
+      h.nt = (h.L + WI - 1) / WI;
+      h.beg = s_off[lo];
+      h.end = s_off[lo + 1];
+    }
+    const uint64_t local = item - h.beg;
+    if (local < 0xffffffffull) {
+      const uint32_t l32 = (uint32_t)local;
+      h.i = l32 / h.nt;
+      h.t0 = (l32 - h.i * h.nt) * WI;
+    } else {
+      h.i = (uint32_t)(local / h.nt);
+      h.t0 = (uint32_t)(local % h.nt) * WI;
+    }
   }
-  r.len = (int)min(WI, a.L - r.t0);
+  h.item = item;
+  r.g = h.g;
+  r.i = h.i;
+  r.t0 = h.t0;
+  r.len = (int)min(WI, h.L - h.t0);
   return r;
 }
 
@@ -545,7 +575,8 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
   };
   uint64_t k = 0;
   int taps_of = -1;                                  // actor whose taps are in hw
-  WItem cur = locate_w(args, s_off, s_ord, G, item_of(0), total, WI);
+  LocHint hint;
+  WItem cur = locate_w(args, s_off, s_ord, G, item_of(0), total, WI, hint);
   if (cur.g >= 0) prefetch_w(args[cur.g], cur, xw, mw, WI, lane);
   cp_async_commit();
   int buf = 0;
@@ -563,7 +594,7 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
       taps_of = cur.g;
     }
     cp_async_commit();
-    WItem nxt = locate_w(args, s_off, s_ord, G, item_of(k + 1), total, WI);
+    WItem nxt = locate_w(args, s_off, s_ord, G, item_of(k + 1), total, WI, hint);
     if (nxt.g >= 0) prefetch_w(args[nxt.g], nxt, xw + (buf ^ 1) * S::XW, mw + (buf ^ 1), WI, lane);
     cp_async_commit();
     cp_async_wait1();                                  // all but the next item's window
