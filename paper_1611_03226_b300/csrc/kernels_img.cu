@@ -4,7 +4,12 @@
 
 namespace dfg {
 
+// The plan and the body are launched as programmatic dependents: each waits
+// (griddep_wait) for its predecessor before touching anything it writes, and
+// the plan lets the body launch at once, so the body's launch overlaps the plan.
 __global__ void k_img_plan(const __grid_constant__ ImgArgs a) {
+  griddep_wait();
+  griddep_launch();
   if (threadIdx.x == 0) img_plan_dev(a);
 }
 
@@ -13,6 +18,7 @@ template <int KIND>
 __global__ void __launch_bounds__(kImgThreads) k_img_body(const __grid_constant__ ImgArgs a) {
   extern __shared__ float4 img_smem[];
   __shared__ ImgPlan s_pl;
+  griddep_wait();
   if (threadIdx.x == 0) s_pl = *a.plan;
   __syncthreads();
   if (s_pl.n == 0) return;
@@ -46,14 +52,14 @@ cudaError_t img_prepare() {
 }
 
 cudaError_t launch_img(const ImgArgs& a, int n_sm, cudaStream_t s) {
-  k_img_plan<<<1, 32, 0, s>>>(a);
+  cudaError_t e = launch_k(true, k_img_plan, dim3(1), dim3(32), 0, s, a);
+  if (e != cudaSuccess) return e;
   const int slot = a.kind == DF_GAUSS5 ? 0 : (a.kind == DF_THRES ? 1 : 2);
   const dim3 grid(n_sm * std::max(g_img_blocks_per_sm[slot], 1));
   const size_t smem = a.kind == DF_THRES ? 0 : img_smem_bytes(a.W);
-  if (a.kind == DF_GAUSS5) k_img_body<DF_GAUSS5><<<grid, kImgThreads, smem, s>>>(a);
-  else if (a.kind == DF_THRES) k_img_body<DF_THRES><<<grid, kImgThreads, smem, s>>>(a);
-  else k_img_body<DF_MED5><<<grid, kImgThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  if (a.kind == DF_GAUSS5) return launch_k(true, k_img_body<DF_GAUSS5>, grid, dim3(kImgThreads), smem, s, a);
+  if (a.kind == DF_THRES) return launch_k(true, k_img_body<DF_THRES>, grid, dim3(kImgThreads), smem, s, a);
+  return launch_k(true, k_img_body<DF_MED5>, grid, dim3(kImgThreads), smem, s, a);
 }
 
 }  // namespace dfg
