@@ -446,6 +446,39 @@ df_status df_dpd_backward_f64(const void *x, uint64_t n, const void *h, int32_t 
                               const int32_t *orders, const void *grad_y, void *grad_x, void *grad_h,
                               void *scratch, uint64_t scratch_elems, void *cuda_stream);
 
+/* The loss of the differentiable fit in the same kernels: resid = P_h(x) -
+ * target (complex64, n values, P_h as df_dpd_forward), *loss = mean |resid|^2
+ * (one float32 on the device), the tile sums of |resid|^2 added in a fixed
+ * order through `partial` (device memory of at least
+ * df_dpd_mse_partial_elems(n) float32, owned by the caller).  DF_EINVAL on a
+ * missing pointer or a short `partial`.
+ * Defined by: the indirect-learning fit of the Sec. 4.2 predistorter (the
+ * paper has no loss; it is what fits the taps). */
+uint64_t df_dpd_mse_partial_elems(uint64_t n);
+df_status df_dpd_mse_forward(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                             const int32_t *orders, const void *target, void *resid, void *loss,
+                             void *partial, uint64_t partial_elems, void *cuda_stream);
+/* Gradient of that loss with respect to the taps: grad_h as df_dpd_backward
+ * with grad_y = resid * (2 g / n), g = *grad_loss (one float32 on the device,
+ * dL'/dloss of the caller's objective), without materialising grad_y; scratch
+ * as df_dpd_backward_scratch.
+ * Defined by: the indirect-learning fit of the Sec. 4.2 predistorter, as
+ * df_dpd_mse_forward. */
+df_status df_dpd_mse_backward(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                              const int32_t *orders, const void *resid, const void *grad_loss, void *grad_h,
+                              void *scratch, uint64_t scratch_elems, void *cuda_stream);
+/* df_dpd_mse_forward / df_dpd_mse_backward in float64 arithmetic on
+ * complex128 data (loss, partial and grad_loss float64), for the
+ * finite-difference check.
+ * Defined by: the indirect-learning fit of the Sec. 4.2 predistorter, as
+ * df_dpd_mse_forward. */
+df_status df_dpd_mse_forward_f64(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                                 const int32_t *orders, const void *target, void *resid, void *loss,
+                                 void *partial, uint64_t partial_elems, void *cuda_stream);
+df_status df_dpd_mse_backward_f64(const void *x, uint64_t n, const void *h, int32_t K, int32_t M,
+                                  const int32_t *orders, const void *resid, const void *grad_loss,
+                                  void *grad_h, void *scratch, uint64_t scratch_elems, void *cuda_stream);
+
 /* Same computation and results as df_dpd_backward, but it allocates nothing.
  * (The paper has no counterpart; this exists for callers that may not
  * allocate device memory, e.g. a real-time adaptation loop where cudaMalloc

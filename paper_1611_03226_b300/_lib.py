@@ -102,6 +102,15 @@ _PROTOS = {
                                         C.POINTER(C.c_int32), _P, _P, _P, _P, C.c_uint64, _P]),
     "df_dpd_backward_scratch": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
                                             C.POINTER(C.c_int32), _P, _P, _P, _P, C.c_uint64, _P]),
+    "df_dpd_mse_partial_elems": (C.c_uint64, [C.c_uint64]),
+    "df_dpd_mse_forward": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
+                                       C.POINTER(C.c_int32), _P, _P, _P, _P, C.c_uint64, _P]),
+    "df_dpd_mse_forward_f64": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
+                                           C.POINTER(C.c_int32), _P, _P, _P, _P, C.c_uint64, _P]),
+    "df_dpd_mse_backward": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
+                                        C.POINTER(C.c_int32), _P, _P, _P, _P, C.c_uint64, _P]),
+    "df_dpd_mse_backward_f64": (C.c_int32, [_P, C.c_uint64, _P, C.c_int32, C.c_int32,
+                                            C.POINTER(C.c_int32), _P, _P, _P, _P, C.c_uint64, _P]),
 }
 
 

@@ -321,6 +321,18 @@ cudaError_t dpd_backward_stateless(const float2* x, uint64_t n, const float2* h,
                                    const int* orders, const float2* gy, float2* gx, float2* gh,
                                    float2* scratch, size_t scratch_elems, cudaStream_t s);
 size_t dpd_backward_scratch_elems(uint64_t n, int K, int M);
+size_t dpd_mse_partial_elems(uint64_t n);
+cudaError_t dpd_mse_forward(const float2* x, uint64_t n, const float2* h, int K, int M, const int* orders,
+                            const float2* target, float2* resid, float* loss, float* partial, cudaStream_t s);
+cudaError_t dpd_mse_forward_f64(const double2* x, uint64_t n, const double2* h, int K, int M, const int* orders,
+                                const double2* target, double2* resid, double* loss, double* partial,
+                                cudaStream_t s);
+cudaError_t dpd_mse_backward(const float2* x, uint64_t n, const float2* h, int K, int M, const int* orders,
+                             const float2* resid, const float* grad_loss, float2* gh, float2* scratch,
+                             size_t scratch_elems, cudaStream_t s);
+cudaError_t dpd_mse_backward_f64(const double2* x, uint64_t n, const double2* h, int K, int M, const int* orders,
+                                 const double2* resid, const double* grad_loss, double2* gh, double2* scratch,
+                                 size_t scratch_elems, cudaStream_t s);
 cudaError_t dpd_forward_stateless_f64(const double2* x, uint64_t n, const double2* h, int K, int M,
                                       const int* orders, double2* y, cudaStream_t s);
 cudaError_t dpd_backward_stateless_f64(const double2* x, uint64_t n, const double2* h, int K, int M,

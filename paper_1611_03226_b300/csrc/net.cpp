@@ -1798,6 +1798,57 @@ df_status df_dpd_backward_f64(const void* x, uint64_t n, const void* h, int32_t 
       static_cast<double2*>(scratch), scratch_elems, static_cast<cudaStream_t>(cuda_stream)));
 }
 
+uint64_t df_dpd_mse_partial_elems(uint64_t n) { return dpd_mse_partial_elems(n); }
+
+df_status df_dpd_mse_forward(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                             const int32_t* orders, const void* target, void* resid, void* loss, void* partial,
+                             uint64_t partial_elems, void* cuda_stream) {
+  df_status st = check_dpd_args(x, n, h, K, M, orders, target, resid);
+  if (st != DF_OK) return st;
+  if (!loss || !partial || partial_elems < dpd_mse_partial_elems(n)) return DF_EINVAL;
+  return cuda_status(dpd_mse_forward(static_cast<const float2*>(x), n, static_cast<const float2*>(h), K, M, orders,
+                                     static_cast<const float2*>(target), static_cast<float2*>(resid),
+                                     static_cast<float*>(loss), static_cast<float*>(partial),
+                                     static_cast<cudaStream_t>(cuda_stream)));
+}
+
+df_status df_dpd_mse_forward_f64(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                                 const int32_t* orders, const void* target, void* resid, void* loss,
+                                 void* partial, uint64_t partial_elems, void* cuda_stream) {
+  df_status st = check_dpd_args(x, n, h, K, M, orders, target, resid);
+  if (st != DF_OK) return st;
+  if (!loss || !partial || partial_elems < dpd_mse_partial_elems(n)) return DF_EINVAL;
+  return cuda_status(dpd_mse_forward_f64(static_cast<const double2*>(x), n, static_cast<const double2*>(h), K, M,
+                                         orders, static_cast<const double2*>(target), static_cast<double2*>(resid),
+                                         static_cast<double*>(loss), static_cast<double*>(partial),
+                                         static_cast<cudaStream_t>(cuda_stream)));
+}
+
+df_status df_dpd_mse_backward(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                              const int32_t* orders, const void* resid, const void* grad_loss, void* grad_h,
+                              void* scratch, uint64_t scratch_elems, void* cuda_stream) {
+  df_status st = check_dpd_args(x, n, h, K, M, orders, resid, grad_h);
+  if (st != DF_OK) return st;
+  if (!grad_loss || !scratch || scratch_elems < df_dpd_backward_scratch_elems(n, K, M)) return DF_EINVAL;
+  return cuda_status(dpd_mse_backward(static_cast<const float2*>(x), n, static_cast<const float2*>(h), K, M, orders,
+                                      static_cast<const float2*>(resid), static_cast<const float*>(grad_loss),
+                                      static_cast<float2*>(grad_h), static_cast<float2*>(scratch), scratch_elems,
+                                      static_cast<cudaStream_t>(cuda_stream)));
+}
+
+df_status df_dpd_mse_backward_f64(const void* x, uint64_t n, const void* h, int32_t K, int32_t M,
+                                  const int32_t* orders, const void* resid, const void* grad_loss, void* grad_h,
+                                  void* scratch, uint64_t scratch_elems, void* cuda_stream) {
+  df_status st = check_dpd_args(x, n, h, K, M, orders, resid, grad_h);
+  if (st != DF_OK) return st;
+  if (!grad_loss || !scratch || scratch_elems < df_dpd_backward_scratch_elems(n, K, M)) return DF_EINVAL;
+  return cuda_status(dpd_mse_backward_f64(static_cast<const double2*>(x), n, static_cast<const double2*>(h), K, M,
+                                          orders, static_cast<const double2*>(resid),
+                                          static_cast<const double*>(grad_loss), static_cast<double2*>(grad_h),
+                                          static_cast<double2*>(scratch), scratch_elems,
+                                          static_cast<cudaStream_t>(cuda_stream)));
+}
+
 uint64_t df_dpd_backward_scratch_elems(uint64_t n, int32_t K, int32_t M) {
   if (K < 1 || K > DF_MAX_BRANCHES || M < 1 || M > DF_MAX_TAPS) return 0;
   return std::max<uint64_t>(1, dpd_backward_scratch_elems(n, K, M));

@@ -12,6 +12,10 @@
 // CTA into partial[tile][k][m]; gz_k[j] = sum_m conj(h[k,m]) g[j+m] gives
 // grad_x by the chain rule through z = u^q x (u = |x|^2).  A second kernel
 // sums the tile partials of each tap in a fixed order.
+// Fused loss of the fit (L = mean |P_h(x) - t|^2): the forward writes the
+// residual d = y - t instead of y and each tile's sum of |d|^2, a second
+// kernel sums the tiles in a fixed order; the adjoint then takes
+// dL/dy = d * (2 g / n) with the upstream scalar g read from device memory.
 #include <algorithm>
 #include "dpd_dev.cuh"
 
@@ -136,16 +140,41 @@ constexpr int kStatelessP = 128;
 
 template <class V>
 struct StatelessArgs {
+  using S = typename Cx<V>::S;
   const V* x;
   const V* gy;
-  V* y;                 // forward output or grad_x
+  V* y;                 // forward output (the residual with target) or grad_x
   V* partial;           // [tiles][K][MT] tap-gradient partial sums
   V* gh;                // [K][M]
   const V* h;           // [K][M] taps (unpadded: tap m >= M contributes zero)
+  const V* target;      // forward: y - target is written, with per-tile sums of its |.|^2
+  S* loss_partial;      // [tiles]
+  const S* gscale;      // adjoint: gy is scaled by gmult * gscale[0] when set
+  S gmult;
   uint64_t n;
   int K, M, MT;
   int orders[kMaxBranches];
 };
+
+// Deterministic block sum of one value per thread (thread 0 gets the result).
+template <class V> __device__ V block_sum(V v, V* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  V s = czero<V>();
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) {
+      s.x += red[w].x;
+      s.y += red[w].y;
+    }
+  __syncthreads();
+  return s;
+}
 
 template <class V, int R, int MT>
 __device__ void fwd_tile(const StatelessArgs<V>& a, uint64_t tile, V* xs, V* zs) {
@@ -172,7 +201,21 @@ __device__ void fwd_tile(const StatelessArgs<V>& a, uint64_t tile, V* xs, V* zs)
 #pragma unroll
   for (int r = 0; r < R; ++r) zs[p * (R + 1) + r] = acc[r];
   __syncthreads();
-  for (int o = p; o < len; o += P) a.y[t0 + o] = zs[o + o / R];
+  if (!a.target) {
+    for (int o = p; o < len; o += P) a.y[t0 + o] = zs[o + o / R];
+  } else {
+    using S = typename Cx<V>::S;
+    S e2 = 0;
+    for (int o = p; o < len; o += P) {
+      const V y = zs[o + o / R], t = a.target[t0 + o];
+      const V d = Cx<V>::make(y.x - t.x, y.y - t.y);
+      a.y[t0 + o] = d;
+      e2 = Cx<V>::fm(d.x, d.x, Cx<V>::fm(d.y, d.y, e2));
+    }
+    __shared__ V red[32];
+    const V sum = block_sum(Cx<V>::make(e2, 0), red);
+    if (threadIdx.x == 0) a.loss_partial[tile] = sum.x;
+  }
   __syncthreads();
 }
 
@@ -191,26 +234,6 @@ __global__ void __launch_bounds__(kStatelessP) k_dpd_fwd(StatelessArgs<V> a) {
       default: break;
     }
   }
-}
-
-// Deterministic block sum of one value per thread (thread 0 gets the result).
-template <class V> __device__ V block_sum(V v, V* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  V s = czero<V>();
-  if (threadIdx.x == 0)
-    for (int w = 0; w < nw; ++w) {
-      s.x += red[w].x;
-      s.y += red[w].y;
-    }
-  __syncthreads();
-  return s;
 }
 
 template <class V, int R, int MC>
@@ -236,11 +259,15 @@ __device__ void bwd_tile(const StatelessArgs<V>& a, uint64_t tile, V* xs, V* zs,
   const uint64_t t0 = tile * T;
   const int len = (int)min(T, a.n - t0);
   const int W = (int)T + MT - 1;
+  const S gsc = a.gscale ? a.gmult * a.gscale[0] : S(1);
   for (int v = p; v < W; v += P) {
     const int64_t pos = (int64_t)t0 - (MT - 1) + v;
     xs[v] = (pos >= 0 && pos < (int64_t)(t0 + len)) ? a.x[pos] : czero<V>();
     const uint64_t gp = t0 + v;       // g window [t0, t0 + T + MT - 1), zero beyond n
-    gs[v + v / R] = gp < a.n ? a.gy[gp] : czero<V>();
+    V gv = gp < a.n ? a.gy[gp] : czero<V>();
+    gv.x *= gsc;
+    gv.y *= gsc;
+    gs[v + v / R] = gv;
   }
   __syncthreads();
   V gr[R], gx[R];
@@ -352,6 +379,25 @@ __global__ void __launch_bounds__(kGhThreads) k_gh_final(const V* partial, uint6
   }
 }
 
+// loss = (sum of the tile sums in a fixed order) / n: thread j sums tiles j,
+// j + 256, .. in ascending order, then the 256 sums by a tree of fixed shape.
+template <class S>
+__global__ void __launch_bounds__(kGhThreads) k_loss_final(const S* partial, uint64_t n_tiles, uint64_t n,
+                                                           S* loss) {
+  S v = 0;
+  for (uint64_t t = threadIdx.x; t < n_tiles; t += kGhThreads) v += partial[t];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __shared__ S ws[kGhThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S t = ws[0];
+    for (int w = 1; w < kGhThreads / 32; ++w) t += ws[w];
+    *loss = n ? t / (S)n : S(0);
+  }
+}
+
 // Resident CTAs of the stateless kernels: 16 per SM of the current device.
 uint64_t stateless_grid_cap() {
   int dev = 0, n_sm = 0;
@@ -379,13 +425,20 @@ cudaError_t stateless_common(StatelessArgs<V>& a, const V* h, int K, int M, cons
 
 template <class V>
 cudaError_t forward_impl(const V* x, uint64_t n, const V* h, int K, int M, const int* orders, V* y,
-                         cudaStream_t s) {
+                         cudaStream_t s, const V* target = nullptr, typename Cx<V>::S* loss = nullptr,
+                         typename Cx<V>::S* loss_partial = nullptr) {
   StatelessArgs<V> a{};
   a.x = x;
   a.y = y;
   a.n = n;
+  a.target = target;
+  a.loss_partial = loss_partial;
   cudaError_t e = stateless_common(a, h, K, M, orders);
-  if (e != cudaSuccess || n == 0) return e;
+  if (e != cudaSuccess) return e;
+  if (n == 0) {
+    if (target) k_loss_final<typename Cx<V>::S><<<1, kGhThreads, 0, s>>>(loss_partial, 0, 0, loss);
+    return cudaGetLastError();
+  }
   const uint64_t T = (uint64_t)kStatelessR * kStatelessP;
   const size_t W = T + a.MT;
   const size_t smem = (W + W + W / kStatelessR + 2) * sizeof(V);
@@ -393,15 +446,19 @@ cudaError_t forward_impl(const V* x, uint64_t n, const V* h, int K, int M, const
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)std::min<uint64_t>(stateless_tiles(n), stateless_grid_cap());
   k_dpd_fwd<V, kStatelessR><<<grid, kStatelessP, smem, s>>>(a);
+  if (target) k_loss_final<typename Cx<V>::S><<<1, kGhThreads, 0, s>>>(loss_partial, stateless_tiles(n), n, loss);
   return cudaGetLastError();
 }
 
 template <class V>
 cudaError_t backward_impl(const V* x, uint64_t n, const V* h, int K, int M, const int* orders, const V* gy, V* gx,
-                          V* gh, V* scratch, size_t scratch_elems, cudaStream_t s) {
+                          V* gh, V* scratch, size_t scratch_elems, cudaStream_t s,
+                          const typename Cx<V>::S* gscale = nullptr, typename Cx<V>::S gmult = 1) {
   StatelessArgs<V> a{};
   a.x = x;
   a.gy = gy;
+  a.gscale = gscale;
+  a.gmult = gmult;
   a.y = gx;
   a.gh = gh;
   a.n = n;
@@ -449,6 +506,30 @@ cudaError_t dpd_backward_stateless_f64(const double2* x, uint64_t n, const doubl
                                        const int* orders, const double2* gy, double2* gx, double2* gh,
                                        double2* scratch, size_t scratch_elems, cudaStream_t s) {
   return backward_impl<double2>(x, n, h, K, M, orders, gy, gx, gh, scratch, scratch_elems, s);
+}
+
+size_t dpd_mse_partial_elems(uint64_t n) { return std::max<uint64_t>(1, stateless_tiles(n)); }
+
+cudaError_t dpd_mse_forward(const float2* x, uint64_t n, const float2* h, int K, int M, const int* orders,
+                            const float2* target, float2* resid, float* loss, float* partial, cudaStream_t s) {
+  return forward_impl<float2>(x, n, h, K, M, orders, resid, s, target, loss, partial);
+}
+cudaError_t dpd_mse_forward_f64(const double2* x, uint64_t n, const double2* h, int K, int M, const int* orders,
+                                const double2* target, double2* resid, double* loss, double* partial,
+                                cudaStream_t s) {
+  return forward_impl<double2>(x, n, h, K, M, orders, resid, s, target, loss, partial);
+}
+cudaError_t dpd_mse_backward(const float2* x, uint64_t n, const float2* h, int K, int M, const int* orders,
+                             const float2* resid, const float* grad_loss, float2* gh, float2* scratch,
+                             size_t scratch_elems, cudaStream_t s) {
+  return backward_impl<float2>(x, n, h, K, M, orders, resid, nullptr, gh, scratch, scratch_elems, s, grad_loss,
+                               n ? 2.0f / (float)n : 0.0f);
+}
+cudaError_t dpd_mse_backward_f64(const double2* x, uint64_t n, const double2* h, int K, int M, const int* orders,
+                                 const double2* resid, const double* grad_loss, double2* gh, double2* scratch,
+                                 size_t scratch_elems, cudaStream_t s) {
+  return backward_impl<double2>(x, n, h, K, M, orders, resid, nullptr, gh, scratch, scratch_elems, s, grad_loss,
+                                n ? 2.0 / (double)n : 0.0);
 }
 
 }  // namespace dfg

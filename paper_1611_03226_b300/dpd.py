@@ -85,28 +85,51 @@ def dpd(x, h, orders):
 
 
 class DPDMSEFunction(torch.autograd.Function):
-    """loss = mean |P_h(u) - target|^2 with the residual kept for the backward:
-    dL/dy = 2 (y - target) / n (PyTorch's complex convention) goes straight into
-    the adjoint, so the loss adds one subtraction, one dot product and one
-    scale to the forward and one scale to the backward."""
+    """loss = mean |P_h(u) - target|^2 in the engine's kernels: the forward
+    writes the residual and the loss (df_dpd_mse_forward), the backward gives
+    grad_h with dL/dy = 2 (y - target) g / n formed inside the adjoint
+    (df_dpd_mse_backward), g the upstream gradient of the loss."""
 
     @staticmethod
     def forward(ctx, u, h, target, orders):
         if u.requires_grad or target.requires_grad:
             raise ValueError("dpd_mse is differentiable in h only: u and target must not require grad")
-        y = dpd_forward(u, h, orders)
-        d = (y - target).contiguous()
-        dr = torch.view_as_real(d).reshape(-1)
-        loss = torch.dot(dr, dr) / d.numel()
-        ctx.save_for_backward(u, h, d)
+        _check_inputs(u, h)
+        if target.dtype != u.dtype or not target.is_cuda or target.shape != u.shape:
+            raise ValueError("target must be a CUDA tensor of u's dtype and shape")
+        u = u.contiguous()
+        h = h.contiguous()
+        target = target.contiguous()
+        K, M = h.shape
+        f64 = u.dtype == torch.complex128
+        real = torch.float64 if f64 else torch.float32
+        resid = torch.empty_like(u)
+        loss = torch.empty((), dtype=real, device=u.device)
+        n_part = L.lib.df_dpd_mse_partial_elems(u.numel())
+        partial = torch.empty(n_part, dtype=real, device=u.device)
+        stream = torch.cuda.current_stream(u.device).cuda_stream
+        fn = L.lib.df_dpd_mse_forward_f64 if f64 else L.lib.df_dpd_mse_forward
+        L.check(fn(C.c_void_p(u.data_ptr()), u.numel(), C.c_void_p(h.data_ptr()), K, M, _orders(orders),
+                   C.c_void_p(target.data_ptr()), C.c_void_p(resid.data_ptr()), C.c_void_p(loss.data_ptr()),
+                   C.c_void_p(partial.data_ptr()), n_part, C.c_void_p(stream)), "df_dpd_mse_forward")
+        ctx.save_for_backward(u, h, resid)
         ctx.orders = tuple(orders)
         return loss
 
     @staticmethod
     def backward(ctx, g):
-        u, h, d = ctx.saved_tensors
-        grad_y = d * (g * (2.0 / d.numel()))
-        _, gh = dpd_backward(u, h, ctx.orders, grad_y, need_x=False)
+        u, h, resid = ctx.saved_tensors
+        K, M = h.shape
+        f64 = u.dtype == torch.complex128
+        g = g.reshape(()).to(torch.float64 if f64 else torch.float32).contiguous()
+        gh = torch.empty_like(h)
+        n_scratch = L.lib.df_dpd_backward_scratch_elems(u.numel(), K, M)
+        scratch = torch.empty(n_scratch, dtype=u.dtype, device=u.device)
+        stream = torch.cuda.current_stream(u.device).cuda_stream
+        fn = L.lib.df_dpd_mse_backward_f64 if f64 else L.lib.df_dpd_mse_backward
+        L.check(fn(C.c_void_p(u.data_ptr()), u.numel(), C.c_void_p(h.data_ptr()), K, M, _orders(ctx.orders),
+                   C.c_void_p(resid.data_ptr()), C.c_void_p(g.data_ptr()), C.c_void_p(gh.data_ptr()),
+                   C.c_void_p(scratch.data_ptr()), n_scratch, C.c_void_p(stream)), "df_dpd_mse_backward")
         return None, gh, None, None
 
 

@@ -135,3 +135,27 @@ def test_fused_mse_matches_plain_torch_loss():
     l2.backward()
     assert abs(l1.item() - l2.item()) <= 1e-5 * l2.item()
     assert torch.linalg.norm(h1.grad - h2.grad) <= 1e-4 * torch.linalg.norm(h2.grad)
+
+
+@pytest.mark.parametrize("n,K,M", [(700, 3, 5), (3000, 4, 10)])
+def test_fused_mse_float64_gradcheck_and_upstream_scale(n, K, M):
+    """The fused loss in float64: gradcheck of the taps at default tolerances
+    (one and several tiles of 1024, a ragged last tile), and an upstream
+    gradient other than 1 (3 * loss) scales the taps' gradient by 3."""
+    import torch
+    from paper_1611_03226_b300.dpd import dpd_mse
+    rng = np.random.default_rng(n + 7)
+    orders = (1, 3, 5, 7)[:K]
+    u = torch.tensor(rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n), dtype=torch.complex128, device="cuda")
+    t = torch.tensor(rng.normal(0, .3, n) + 1j * rng.normal(0, .3, n), dtype=torch.complex128, device="cuda")
+    h = torch.tensor(rng.normal(0, .2, (K, M)) + 1j * rng.normal(0, .2, (K, M)), dtype=torch.complex128,
+                     device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda b: dpd_mse(u, b, t, orders), (h,), nondet_tol=0.0)
+    l1 = dpd_mse(u, h, t, orders)
+    g1, = torch.autograd.grad(l1, h)
+    g3, = torch.autograd.grad(3 * dpd_mse(u, h, t, orders), h)
+    assert torch.linalg.norm(g3 - 3 * g1) <= 1e-12 * torch.linalg.norm(g1)
+    # the loss itself against its definition on the float64 forward
+    from paper_1611_03226_b300.dpd import dpd
+    want = (dpd(u, h.detach(), orders) - t).abs().pow(2).mean()
+    assert abs(l1.item() - want.item()) <= 1e-12 * want.item()
