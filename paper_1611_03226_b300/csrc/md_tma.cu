@@ -147,7 +147,22 @@ struct PairState {
   uint32_t hb1, hb2, he1, he2, cn_all, cn_lo;
 };
 
-// kTRows consecutive walked rows of one frame pair, from shared memory.
+// The 16-byte words of kTRows consecutive walked rows a lane reads from a
+// stage: per row, frame A's previous frame, frame A and frame B.
+struct StageRows {
+  uint4 v[kTRows][3];
+};
+__device__ __forceinline__ void load_rows(const uint8_t* st, int step, int slot, StageRows& r) {
+#pragma unroll
+  for (int rr = 0; rr < kTRows; ++rr) {
+    const uint8_t* row = st + rr * step;             // rows in walk order
+    r.v[rr][0] = *reinterpret_cast<const uint4*>(row);
+    r.v[rr][1] = *reinterpret_cast<const uint4*>(row + slot);
+    r.v[rr][2] = *reinterpret_cast<const uint4*>(row + 2 * slot);
+  }
+}
+
+// kTRows consecutive walked rows of one frame pair, from registers.
 //   ROWS   the unit reaches outside the image vertically: per-row range tests
 //   COLS   some lane's tile column is outside the image: lane masks
 //   W0     walk row of the group's first row when it is below 4, else 4: the
@@ -156,15 +171,11 @@ struct PairState {
 // Outside the image every pixel counts as motion for the erosion and as no
 // motion for the dilation.
 template <bool HI, bool ROWS, bool COLS, int W0>
-__device__ __forceinline__ void pair_rows(const uint8_t* st, int step, int slot, int y_start, int dir,
-                                          int H, bool col_in, uint32_t add4, uint32_t mul,
-                                          PairState& p) {
+__device__ __forceinline__ void pair_rows(const StageRows& r, int y_start, int dir, int H, bool col_in,
+                                          uint32_t add4, uint32_t mul, PairState& p) {
 #pragma unroll
   for (int rr = 0; rr < kTRows; ++rr) {
-    const uint8_t* row = st + rr * step;             // rows in walk order
-    const uint4 pv = *reinterpret_cast<const uint4*>(row);
-    const uint4 av = *reinterpret_cast<const uint4*>(row + slot);
-    const uint4 bv = *reinterpret_cast<const uint4*>(row + 2 * slot);
+    const uint4 pv = r.v[rr][0], av = r.v[rr][1], bv = r.v[rr][2];
     const int y = y_start + dir * rr;
     uint32_t b = pair_bits32<HI>(av, pv, bv, add4);
     if (COLS && !col_in) b = 0xffffffffu;
@@ -194,15 +205,15 @@ __device__ __forceinline__ void pair_rows(const uint8_t* st, int step, int slot,
 }
 
 template <bool HI, int W0>
-__device__ __forceinline__ void pair_rows_any(bool rows, bool cols, const uint8_t* st, int step,
-                                              int slot, int y_start, int dir, int H, bool col_in,
-                                              uint32_t add4, uint32_t mul, PairState& p) {
+__device__ __forceinline__ void pair_rows_any(bool rows, bool cols, const StageRows& r, int y_start,
+                                              int dir, int H, bool col_in, uint32_t add4, uint32_t mul,
+                                              PairState& p) {
   if (rows) {
-    if (cols) pair_rows<HI, true, true, W0>(st, step, slot, y_start, dir, H, col_in, add4, mul, p);
-    else pair_rows<HI, true, false, W0>(st, step, slot, y_start, dir, H, col_in, add4, mul, p);
+    if (cols) pair_rows<HI, true, true, W0>(r, y_start, dir, H, col_in, add4, mul, p);
+    else pair_rows<HI, true, false, W0>(r, y_start, dir, H, col_in, add4, mul, p);
   } else {
-    if (cols) pair_rows<HI, false, true, W0>(st, step, slot, y_start, dir, H, col_in, add4, mul, p);
-    else pair_rows<HI, false, false, W0>(st, step, slot, y_start, dir, H, col_in, add4, mul, p);
+    if (cols) pair_rows<HI, false, true, W0>(r, y_start, dir, H, col_in, add4, mul, p);
+    else pair_rows<HI, false, false, W0>(r, y_start, dir, H, col_in, add4, mul, p);
   }
 }
 
@@ -361,30 +372,36 @@ __global__ void __launch_bounds__(kTThreads)
         if (lane == 0) set_status(a.eng, DF_ETIMEOUT, kWhereMdPipe);
         return;
       }
+      // The lane's words of the stage go to registers first and the stage is
+      // handed back to the producer before the per-pixel work, so that the
+      // copies of the next groups are in flight while it runs.
+      StageRows r;
       if (active) {
         // the first row of this group in walk order, and the step between rows
         const uint8_t* st = stages + s * stage_bytes + (2 * q) * slot_bytes + lane_off +
                             (up ? (kTRows - 1) * pitch : 0);
+        load_rows(st, up ? -pitch : pitch, slot_bytes, r);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8 * s);
+      if (active) {
         const int y_start = up ? ys + kMdWalk - 3 - grp * kTRows : ys - 2 + grp * kTRows;
         // 10-bit count field of the tile row these dilation rows fall in
         const int tr = max(grp * kTRows - 4, 0) >> 4;
         uint32_t mul;                                  // 1 << (10 * field)
         asm("mov.b32 %0, %1;" : "=r"(mul) : "r"(1u << (10 * (up ? kMdTileRows - 1 - tr : tr))));
-        const int step = up ? -pitch : pitch;
         const int w0 = grp * kTRows;                   // walk row of the group's first row
         if (w0 >= 4)
-          pair_rows_any<HI, 4>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
+          pair_rows_any<HI, 4>(edge_rows, edge_cols, r, y_start, dir, a.H, col_in, add4, mul, p);
         else if (w0 == 0)
-          pair_rows_any<HI, 0>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
+          pair_rows_any<HI, 0>(edge_rows, edge_cols, r, y_start, dir, a.H, col_in, add4, mul, p);
         else if (w0 == 2 && kTRows <= 2)
-          pair_rows_any<HI, 2>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
+          pair_rows_any<HI, 2>(edge_rows, edge_cols, r, y_start, dir, a.H, col_in, add4, mul, p);
         else if (w0 == 1 && kTRows == 1)
-          pair_rows_any<HI, 1>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
+          pair_rows_any<HI, 1>(edge_rows, edge_cols, r, y_start, dir, a.H, col_in, add4, mul, p);
         else if (kTRows == 1)
-          pair_rows_any<HI, 3>(edge_rows, edge_cols, st, step, slot_bytes, y_start, dir, a.H, col_in, add4, mul, p);
+          pair_rows_any<HI, 3>(edge_rows, edge_cols, r, y_start, dir, a.H, col_in, add4, mul, p);
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(empty0 + 8 * s);
     }
     if (active) {
       store_counts(a, t.j0 + 2 * q, p.cn_all - p.cn_lo, t.strip, col, owned);

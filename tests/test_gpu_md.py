@@ -23,7 +23,8 @@ def stream_both(Net, frames, cap, chunk, rec_capacity=None, separate=False, prev
     enet, ei = EN.motion_fused(Net, H, W, cap, rec_capacity, t=t, prev_init=prev_init,
                                separate_prev_source=separate)
     ro, co, re_, ce = [], [], [], []
-    i, idle = 0, 0
+    i, idle, n_step = 0, 0, 0
+    cycle = flags if isinstance(flags, (list, tuple)) else [flags]
     while True:
         free = min(onet.channels[oi["ch_cur"]].free, onet.channels[oi["ch_prev"]].free)
         k = min(chunk, T - i, free)
@@ -33,7 +34,8 @@ def stream_both(Net, frames, cap, chunk, rec_capacity=None, separate=False, prev
             if separate:
                 enet.push(ei["src_prev"], np.ascontiguousarray(frames[i:i + k]))
             i += k
-        fo, fe = onet.run(1), enet.run(1, flags)
+        fo, fe = onet.run(1), enet.run(1, cycle[n_step % len(cycle)])
+        n_step += 1
         assert fo == fe
         for key in ("ch_cur", "ch_prev", "ch_rec", "ch_cnt"):
             assert onet.counters(oi[key]) == enet.counters(ei[key]), key
@@ -138,5 +140,20 @@ def test_motion_persistent_mode(Net, separate):
     w = synth.motion(n_frames=7, height=72, width=96)
     f = w.frames()
     ro, co, re_, ce = stream_both(Net, f, 3, 2, separate=separate, flags=L.DF_RUN_PERSISTENT)
+    np.testing.assert_array_equal(ce, co)
+    np.testing.assert_array_equal(re_, ro)
+
+
+@pytest.mark.parametrize("H,W", [(72, 96), (1080, 1920)])
+def test_motion_launch_modes_alternate(Net, H, W):
+    """Steps launched eagerly, from a graph and as the persistent kernel in
+    turn (the TMA main kernel at these widths, the register-staged one inside
+    the persistent kernel): every step's counters, records and count tokens
+    equal the oracle's."""
+    from paper_1611_03226_b300 import _lib as L
+    w = synth.motion(n_frames=13, height=H, width=W)
+    f = w.frames()
+    modes = [0, L.DF_RUN_GRAPH, L.DF_RUN_PERSISTENT, L.DF_RUN_GRAPH, 0, L.DF_RUN_PERSISTENT | L.DF_RUN_GRAPH]
+    ro, co, re_, ce = stream_both(Net, f, 4, 3, flags=modes)
     np.testing.assert_array_equal(ce, co)
     np.testing.assert_array_equal(re_, ro)
