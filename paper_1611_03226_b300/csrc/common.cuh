@@ -167,7 +167,7 @@ struct DpdArgs {            // one per predistorter actor, stored in device memo
   uint32_t L;               // samples per block
   uint32_t n_max;           // capacity of the per-firing arrays
   int orders[kMaxBranches];
-  const float2* h;          // K * MT taps (zero padded beyond M)
+  const float4* h;          // K * MT taps {hx, hx, hy, hy} (zero padded beyond M)
   DpdPlanHdr* plan;
   uint32_t* masks;          // [n_max]
   uint32_t* rank;           // [K][n_max]: active firings of branch k before firing i

@@ -187,15 +187,16 @@ __device__ inline void dpd_hist_dev(const DpdArgs& a) {
 // outside it) is staged by cp.async into one half of a double buffer while
 // the previous item computes.  Per active branch k, in ascending k:
 //   z-pass: lane l forms z = |x|^(o_k - 1) x for window positions l, l + 32,
-//           ..., stored as {zx, zx, zy, zy} (the first MT-1 positions of a
-//           block's first chunk come from branch k's own history instead:
-//           the previous block in which k was active, or the persisted
-//           history);
-//   FIR:    lane l accumulates outputs l*R .. l*R + R-1 with the taps
-//           {hx, hy} of branch k in registers, two-lane FMAs
-//           P += {hx, hy} * {zx, zx} and Q += {hx, hy} * {zy, zy}, so that
-//           y = (P.x - Q.y, P.y + Q.x) is the complex sum over taps and
-//           branches (the Adder), formed once at the end.
+//           ..., stored as {zx, zy} (the first MT-1 positions of a block's
+//           first chunk come from branch k's own history instead: the
+//           previous block in which k was active, or the persisted history);
+//   FIR:    lane l loads its R + MT - 1 window positions of z into registers
+//           and accumulates outputs l*R .. l*R + R-1 tap by tap, each tap
+//           {hx, hx, hy, hy} one 16-byte shared load at the same address in
+//           every lane, with two-lane FMAs P += {zx, zy} * {hx, hx} and
+//           Q += {zx, zy} * {hy, hy}, so that y = (P.x - Q.y, P.y + Q.x) is
+//           the complex sum over taps and branches (the Adder), formed once
+//           at the end.
 __device__ __forceinline__ float2 hist_sample(const DpdArgs& a, const DpdPlanHdr& pl, uint32_t i,
                                               int k, int s) {
   const int H1 = a.MT - 1;
@@ -224,19 +225,19 @@ __device__ __forceinline__ const uint8_t* slot_at(const ChanDesc& c, uint64_t sl
 
 // Shared memory of one warp (R outputs per lane, taps padded to at most MTMAX):
 //   xw[2][XW] float2  x window, double buffered (XW >= 32 (R + 1) and >= 32R + MTMAX - 1, even)
-//   zw[ZW]    float4  branch signal {zx, zx, zy, zy}; position v at v + v / R,
-//                     so that lanes reading at a stride of R positions hit
-//                     distinct banks
-//   hw[kMaxBranches * MTMAX + 8] float2  taps {hx, hy} of the warp's current
-//                     actor, then its branch orders (int32)
+//   zw[ZW]    float2  branch signal {zx, zy}; position v at v + v / R, so
+//                     that the 16 lanes of a half-warp reading at a stride of
+//                     R positions hit distinct banks
+//   hw[kMaxBranches * MTMAX] float4  taps {hx, hx, hy, hy} of the warp's
+//                     current actor, then its branch orders (int32)
 //   mw[2] u32         control masks of the two buffered items (staged with x)
 template <int R, int MTMAX>
 struct WarpSmem {
   static constexpr int XW = 32 * (R + 1) > 32 * R + MTMAX - 1 ? 32 * (R + 1) : ((32 * R + MTMAX) & ~1);
-  static constexpr int ZW = XW + XW / R + 1;
+  static constexpr int ZW = (XW + XW / R + 2) & ~1;
   static constexpr size_t x_bytes = 2 * (size_t)XW * sizeof(float2);
-  static constexpr size_t z_bytes = (size_t)ZW * sizeof(float4);
-  static constexpr size_t h_bytes = ((size_t)kMaxBranches * MTMAX + kMaxBranches / 2) * sizeof(float2);
+  static constexpr size_t z_bytes = (size_t)ZW * sizeof(float2);
+  static constexpr size_t h_bytes = (size_t)kMaxBranches * MTMAX * sizeof(float4) + kMaxBranches * sizeof(int32_t);
   static constexpr size_t m_bytes = 16;     // control masks of the two buffered items
   static constexpr size_t bytes = x_bytes + z_bytes + h_bytes + m_bytes;
 };
@@ -353,25 +354,21 @@ __device__ __forceinline__ void prefetch_w(const DpdArgs& a, WItem& it, float2* 
   }
 }
 
-__device__ __forceinline__ void zstore(float4* zw, int v, int R, float2 x, float p) {
-  const float zx = p * x.x, zy = p * x.y;
-  zw[v + v / R] = make_float4(zx, zx, zy, zy);
+__device__ __forceinline__ void zstore(float2* zw, int v, int R, float2 x, float p) {
+  zw[v + v / R] = make_float2(p * x.x, p * x.y);
 }
 
-// z = u^Q x over the window positions lane, lane + 32, ... < W (W <= 32 (R+1)).
-// Position lane + 32 j of the padded buffer sits at lane + lane / R + j (32 + 32 / R)
-// (R divides 32), so every access is a fixed offset from one per-lane base.
 // z = u^q x over all 32 (R + 1) window positions lane, lane + 32, ...; the x
 // and z buffers hold that many, positions >= W hold stale x and are never
-// read by the FIR, so the pass is straight-line code: all loads, then the
+// used by the FIR, so the pass is straight-line code: all loads, then the
 // arithmetic, then all stores.  Position lane + 32 j of the padded z buffer
 // sits at lane + lane / R + j (32 + 32 / R) (R divides 32): fixed offsets from
 // one per-lane base.  u^q is assembled from u, u^2 and u^4 by the bits of q
 // (q < 8, orders up to 15), by repeated products otherwise.
 template <int R>
-__device__ __forceinline__ void zpass_w(const float2* __restrict__ xs, float4* __restrict__ zw, int lane, int q) {
+__device__ __forceinline__ void zpass_w(const float2* __restrict__ xs, float2* __restrict__ zw, int lane, int q) {
   const float2* xb = xs + lane;
-  float4* zb = zw + lane + lane / R;
+  float2* zb = zw + lane + lane / R;
   float2 x[R + 1];
 #pragma unroll
   for (int j = 0; j <= R; ++j) x[j] = xb[32 * j];
@@ -397,8 +394,7 @@ __device__ __forceinline__ void zpass_w(const float2* __restrict__ xs, float4* _
   }
 #pragma unroll
   for (int j = 0; j <= R; ++j) {
-    const float zx = p[j] * x[j].x, zy = p[j] * x[j].y;
-    zb[j * (32 + 32 / R)] = make_float4(zx, zx, zy, zy);
+    zb[j * (32 + 32 / R)] = make_float2(p[j] * x[j].x, p[j] * x[j].y);
   }
 }
 
@@ -416,25 +412,22 @@ __device__ __forceinline__ float2 unpack_b64(unsigned long long v) {
 }
 
 // One branch's FIR into the accumulators of this lane's R outputs:
-// P[r] += {hx, hy} * {zx, zx}, Q[r] += {hx, hy} * {zy, zy} over the MT taps.
+// P[r] += {zx, zy} * {hx, hx}, Q[r] += {zx, zy} * {hy, hy} over the MT taps.
 template <int R, int MT>
 __device__ __forceinline__ void fir_w(unsigned long long (&P)[R], unsigned long long (&Q)[R],
-                                      const float4* __restrict__ zw, int lane, const float2* __restrict__ hk) {
-  unsigned long long h[MT];
-  const unsigned long long* hk64 = reinterpret_cast<const unsigned long long*>(hk);
+                                      const float2* __restrict__ zw, int lane, const ulonglong2* __restrict__ hk) {
+  // the lane's R + MT - 1 window positions {zx, zy}, then tap by tap
+  const unsigned long long* zb = reinterpret_cast<const unsigned long long*>(zw) + lane * (R + 1);
+  unsigned long long z[R + MT - 1];
 #pragma unroll
-  for (int m = 0; m < MT; ++m) h[m] = hk64[m];
-  const ulonglong2* zb = reinterpret_cast<const ulonglong2*>(zw) + lane * (R + 1);
+  for (int s = 0; s < R + MT - 1; ++s) z[s] = zb[s + s / R];
 #pragma unroll
-  for (int s = 0; s < R + MT - 1; ++s) {
-    const ulonglong2 z = zb[s + s / R];        // {zx, zx}, {zy, zy}
+  for (int m = 0; m < MT; ++m) {
+    const ulonglong2 h = hk[m];                // {hx, hx}, {hy, hy}: one address for the warp
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int m = r + MT - 1 - s;
-      if (m >= 0 && m < MT) {
-        ffma2_b64(P[r], h[m], z.x);
-        ffma2_b64(Q[r], h[m], z.y);
-      }
+      ffma2_b64(P[r], z[r + MT - 1 - m], h.x);
+      ffma2_b64(Q[r], z[r + MT - 1 - m], h.y);
     }
   }
 }
@@ -469,7 +462,7 @@ __device__ __forceinline__ void store_w(float2* yb, int len, int lane, const flo
 // them from several earlier firings (hist_sample).
 template <int R, int MT>
 __device__ __noinline__ void dpd_item_w(const DpdArgs& a, const WItem& it, uint32_t mask, const float2* xs,
-                                        float4* zw, const float2* hw, int lane) {
+                                        float2* zw, const ulonglong2* hw, int lane) {
   const DpdPlanHdr& pl = *a.plan;
   float2* yb = reinterpret_cast<float2*>(const_cast<uint8_t*>(slot_at(a.out, pl.slot_out0, it.i))) + it.t0;
   unsigned long long P[R], Q[R];              // pairs of floats, +0.0f each
@@ -559,8 +552,8 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
   const uint64_t total = carry;
   uint8_t* wb = reinterpret_cast<uint8_t*>(smem_raw) + dpd_body_off_bytes(G) + (size_t)wid * S::bytes;
   float2* xw = reinterpret_cast<float2*>(wb);
-  float4* zw = reinterpret_cast<float4*>(wb + S::x_bytes);
-  float2* hw = reinterpret_cast<float2*>(wb + S::x_bytes + S::z_bytes);
+  float2* zw = reinterpret_cast<float2*>(wb + S::x_bytes);
+  ulonglong2* hw = reinterpret_cast<ulonglong2*>(wb + S::x_bytes + S::z_bytes);
   uint32_t* mw = reinterpret_cast<uint32_t*>(wb + S::x_bytes + S::z_bytes + S::h_bytes);
   // Items are dealt to warps in runs of kRun consecutive items (a warp keeps
   // its actor's taps for a run): run r of global warp gw holds items
@@ -585,7 +578,7 @@ __device__ inline void dpd_body_dev(const DpdArgs* __restrict__ args, const uint
     if (cur.g != taps_of) {
       // taps {hx, hy} of every branch, then the branch orders, by asynchronous
       // copies waited for together with this item's x window
-      for (int e = lane; e < a.K * a.MT; e += 32) cp_async8(hw + e, a.h + e, true);
+      for (int e = lane; e < a.K * a.MT; e += 32) cp_async16(hw + e, a.h + e);
       if (lane < a.K) {
         const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(
             reinterpret_cast<int32_t*>(hw + a.K * a.MT) + lane));

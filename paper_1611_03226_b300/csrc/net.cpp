@@ -741,7 +741,7 @@ df_status df_net_finalize(df_net* net) {
       q.cnt = take(4ull * K);
       q.hist = take(8ull * 2 * K * std::max(1, MT - 1));
       q.parity = take(4);
-      q.h = take(8ull * K * MT);
+      q.h = take(16ull * K * MT);
       net->dpd_index[a] = (int)dp.size();
       dp.push_back(q);
     } else if (A.kind == DF_MD) {
@@ -815,7 +815,7 @@ df_status df_net_finalize(df_net* net) {
   }
   // ---- per-actor device state and the step program ----
   net->dpd_host.assign(dp.size(), DpdArgs{});
-  std::vector<std::vector<float2>> hpad(dp.size());
+  std::vector<std::vector<float4>> hpad(dp.size());
   net->d_dpd = reinterpret_cast<DpdArgs*>(base + p_dpd_args.off);
   for (int a = 0; a < (int)net->actors.size(); ++a) {
     const ActorH& A = net->actors[a];
@@ -850,16 +850,19 @@ df_status df_net_finalize(df_net* net) {
       d.cnt = reinterpret_cast<uint32_t*>(base + q.cnt.off);
       d.hist = reinterpret_cast<float2*>(base + q.hist.off);
       d.parity = reinterpret_cast<uint32_t*>(base + q.parity.off);
-      float2* hd = reinterpret_cast<float2*>(base + q.h.off);
+      // taps as {hx, hx, hy, hy}: the body's two-lane FMAs take {hx, hx} and
+      // {hy, hy} straight from one 16-byte load
+      float4* hd = reinterpret_cast<float4*>(base + q.h.off);
       d.h = hd;
-      hpad[i].assign((size_t)d.K * d.MT, make_float2(0.f, 0.f));
+      hpad[i].assign((size_t)d.K * d.MT, make_float4(0.f, 0.f, 0.f, 0.f));
       for (int k = 0; k < d.K; ++k) {
         const size_t row = fir ? (size_t)A.dpd.branch : (size_t)k;
-        for (int m = 0; m < d.M; ++m)
-          hpad[i][(size_t)k * d.MT + m] =
-              make_float2(A.h[2 * (row * d.M + m)], A.h[2 * (row * d.M + m) + 1]);
+        for (int m = 0; m < d.M; ++m) {
+          const float hx = A.h[2 * (row * d.M + m)], hy = A.h[2 * (row * d.M + m) + 1];
+          hpad[i][(size_t)k * d.MT + m] = make_float4(hx, hx, hy, hy);
+        }
       }
-      DF_CUDA(cudaMemcpyAsync(hd, hpad[i].data(), hpad[i].size() * sizeof(float2),
+      DF_CUDA(cudaMemcpyAsync(hd, hpad[i].data(), hpad[i].size() * sizeof(float4),
                               cudaMemcpyHostToDevice, s));
     }
   }
