@@ -3,11 +3,15 @@
 #include "dpd_dev.cuh"
 
 namespace dfg {
+// Padded tap count of the kernel instantiation for M taps (the padding taps
+// are zero).  Between 8 and 16 an odd count takes the next even one: fewer
+// code variants when actors of many tap counts share a launch, for one zero
+// tap.
 int dpd_supported_mt(int M) {
   if (M < 1 || M > 32) return 0;
   if (M <= 4) return 4;
   if (M <= 8) return 8;
-  if (M <= 16) return M;
+  if (M <= 16) return (M + 1) & ~1;
   return 32;
 }
 
